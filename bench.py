@@ -1,0 +1,358 @@
+"""Benchmark: NESA matrix-vector products per second on the r = 3 sphere workload.
+
+Workload: PEC sphere of radius 3 wavelengths, icosphere subdivision 6 (81,920
+triangles, 122,880 RWG unknowns), octree of 6 levels with 0.25-wavelength leaves,
+one right-hand side, FP64 throughout.  One step = one full operator application
+(near field + radiation, source transfer, translation, potential transfer, reception)
+through the library's C ABI.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line on rank 0.  ``--impl reference`` times the CPU oracle instead:
+each step is a stage-wise sample of one product (see ``oracle_sampled_product``).
+Under torchrun (N > 1) every rank runs an independent replica of the workload
+(the product of one operator does not shard without a halo exchange, which is not
+built); ``value`` counts the products of all ranks.
+"""
+import os
+
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+os.environ.setdefault("OMP_NUM_THREADS", "1")
+os.environ.setdefault("MKL_NUM_THREADS", "1")
+
+import argparse  # noqa: E402
+import json  # noqa: E402
+import subprocess  # noqa: E402
+import sys  # noqa: E402
+import threading  # noqa: E402
+import time  # noqa: E402
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from workloads import get_config, random_coefficients  # noqa: E402
+
+CONFIG = "C2"
+METRIC = "nesa_matvec_per_s"
+UNIT = "matvec/s"
+# FP64 peak of one GB300: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2070 MHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+SPEC = ("PEC sphere r=3 wavelengths, icosphere subdiv 6 (81,920 triangles, 122,880 RWG), "
+        "6-level octree, leaf 0.25 wavelength, 1 RHS, FP64")
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def oracle_sampled_product(o, x, n_leaves=12, n_boxes=12, n_rows=48, seed=0):
+    """Seconds the oracle needs for one full product, estimated stage by stage on a
+    bounded sample: every stage (channel sources, near rows, radiation, source
+    transfer, translation per level, reception, testing) is timed on a random subset
+    of its units (leaves, boxes or rows) and scaled by the number of units.  Inputs of
+    the sampled stages are the true ones where cheap, else random vectors of the right
+    shape (the cost of a stage does not depend on the values)."""
+    rng = np.random.default_rng(seed)
+    t = o.tree
+    L, l0 = o.L, o.l0
+    total = 0.0
+    parts = {}
+
+    def pick(seq, k):
+        seq = list(seq)
+        idx = rng.choice(len(seq), size=min(k, len(seq)), replace=False)
+        return [seq[i] for i in idx]
+
+    t0 = time.perf_counter()
+    J = o.sources(x)
+    parts["sources"] = time.perf_counter() - t0
+    rows = np.sort(rng.choice(o.n, size=min(n_rows, o.n), replace=False))
+    t0 = time.perf_counter()
+    _ = o.near_rows(rows) @ x
+    parts["near"] = (time.perf_counter() - t0) * o.n / len(rows)
+    leaves = t.boxes[L]
+    sample = pick(leaves, n_leaves)
+    t0 = time.perf_counter()
+    for b in sample:
+        o.radiate(J, b)
+    parts["radiation"] = (time.perf_counter() - t0) * len(leaves) / len(sample)
+    up = 0.0
+    for l in range(L, l0, -1):
+        sample = pick(t.boxes[l], n_boxes)
+        s = rng.standard_normal((o.Q[l], 4)) + 0j
+        t0 = time.perf_counter()
+        for b in sample:
+            o.source_transfer(l, b, s)
+        up += (time.perf_counter() - t0) * len(t.boxes[l]) / len(sample)
+    parts["source_transfer"] = up
+    tr = 0.0
+    for l in range(l0, L + 1):
+        sample = pick(t.boxes[l], n_boxes)
+        srcs = {b for a in sample for b in t.interaction_list(l, a)}
+        s = {b: rng.standard_normal((o.Q[l], 4)) + 0j for b in srcs}
+        op = rng.standard_normal((o.Q[l - 1], 4)) + 0j if l > l0 else None
+        o._D = {}
+        t0 = time.perf_counter()
+        for a in sample:
+            o.translate(l, a, s, op)
+        tr += (time.perf_counter() - t0) * len(t.boxes[l]) / len(sample)
+        o._D = {}
+    parts["translation"] = tr
+    sample = pick(leaves, n_leaves)
+    oL = rng.standard_normal((o.Q[L], 4)) + 0j
+    t0 = time.perf_counter()
+    for b in sample:
+        o.receive(b, oL)
+    parts["reception"] = (time.perf_counter() - t0) * len(leaves) / len(sample)
+    F = np.zeros((len(t.points), 4), np.complex128)
+    t0 = time.perf_counter()
+    o.test(F, rows)
+    parts["testing"] = (time.perf_counter() - t0) * o.n / len(rows)
+    total = sum(parts.values())
+    desc = ("stage-wise sample of one product: %d of %d leaves (radiation, reception), %d boxes per level "
+            "(source transfer, translation with D built on the fly), %d of %d rows (near field, testing); "
+            "each stage scaled by its unit count" % (min(n_leaves, len(leaves)), len(leaves), n_boxes,
+                                                   len(rows), o.n))
+    return total, parts, desc
+
+
+def build_oracle(cfg):
+    from oracle.nesa import NesaOracle
+    return NesaOracle(cfg["vertices"], cfg["triangles"], cfg["k"], cfg["leaf_size"], cfg["n_levels"])
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    cfg = get_config(CONFIG)
+    o = build_oracle(cfg)
+    x = random_coefficients(o.n, 1, seed=2024)[0]
+    for _ in range(args.warmup):
+        oracle_sampled_product(o, x, seed=1)
+    est, walls = [], []
+    for s in range(args.steps):
+        t0 = time.perf_counter()
+        sec, parts, desc = oracle_sampled_product(o, x, seed=100 + s)
+        walls.append(time.perf_counter() - t0)
+        est.append(sec)
+    value = 1.0 / float(np.mean(est))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * float(np.mean(walls)), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": "%s: %s" % (CONFIG, SPEC), "parallelism": "single process, host cores"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    import paper_1801_03589_gb300 as nesa
+
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    cfg = get_config(CONFIG)
+    g = nesa.Nesa(cfg["vertices"], cfg["triangles"], cfg["k"], leaf_size=cfg["leaf_size"], n_levels=cfg["n_levels"])
+    info = g.info()
+    stream = torch.cuda.Stream()
+    g.set_stream(stream)
+    n = g.n
+    nrhs = 1
+    x = torch.from_numpy(random_coefficients(n, nrhs, seed=2024 + rank)).cuda()
+    y = torch.empty_like(x)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(3, args.warmup)):
+            g.matvec(x, y)
+    stream.synchronize()
+    g.profile_enable(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            ev0.record(stream)
+            for _ in range(args.steps):
+                g.matvec(x, y)
+            ev1.record(stream)
+        stream.synchronize()
+        torch.cuda.synchronize()
+        barrier()
+    prof = g.profile_read()
+    g.profile_enable(False)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if pg is not None:
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * nrhs * 1e3 / ms_max
+
+    # end to end through the host-pointer entry point: H2D of x, product, D2H of y
+    xh = torch.from_numpy(random_coefficients(n, nrhs, seed=7 + rank)).pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    for _ in range(2):
+        g.matvec_host_ptr(xh.data_ptr(), yh.data_ptr(), nrhs)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        g.matvec_host_ptr(xh.data_ptr(), yh.data_ptr(), nrhs)
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+    if pg is not None:
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    e2e_ms = float(t.item())
+
+    if rank != 0:
+        if pg is not None:
+            pg.destroy_process_group()
+        return 0
+
+    # roofline of the dominant stage (largest device time)
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    d = prof[dom]
+    achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
+    stages = {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps,
+                  "tflops": (v["flops"] / (v["ms"] * 1e-3) / 1e12) if v["ms"] > 0 else None,
+                  "gbs": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
+              for k, v in prof.items()}
+    launches = sum(v["launches"] for v in prof.values())
+    peaks = _peaks()
+
+    # CPU oracle on the host cores, on a bounded stage-wise sample
+    cpu = None
+    if not args.no_cpu_baseline:
+        o = build_oracle(cfg)
+        xo = random_coefficients(n, 1, seed=2024)[0]
+        sec, parts, desc = oracle_sampled_product(o, xo, seed=3)
+        cpu = {"value": 1.0 / sec, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
+               "seconds_per_matvec": sec, "stage_seconds": parts}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "%s: %s" % (CONFIG, SPEC), "nrhs": nrhs, "n_unknowns": n,
+                   "levels": info["n_levels"], "l0": info["l0"], "q": info["q"][info["l0"]:],
+                   "near_nnz": info["near_nnz"], "device_gb": info["device_bytes"] / 1e9,
+                   "build_s": info["build_seconds"],
+                   "l2": "operator data %.1f GB per product > 129 MB L2 (no flush needed)" % (
+                       sum(v["bytes"] for v in prof.values()) / args.steps / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "clocks": clk.summary(),
+        "e2e": {"value": world * nrhs * 1e3 / e2e_ms, "unit": UNIT, "h2d_bytes_per_step": 16 * n * nrhs,
+                "d2h_bytes_per_step": 16 * n * nrhs, "ms_per_step": e2e_ms},
+        "gpu_launches": launches,
+        "roofline": {"kernel": "k_translate" if dom == "translation" else dom, "stage": dom, "bound": "alu",
+                     "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "peak_note": "FP64: 152 SMs x 4 flop/clk x 2070 MHz (derived; no measured FP64 peak in "
+                                  "MEASURED_PEAKS.json, hbm %s GB/s)" % peaks.get("hbm_gbs")},
+        "stages": stages,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    if pg is not None:
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    return run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,208 @@
+/*
+ * nesa.h - C ABI of the GB300 NESA/EFIE library (libnesa.so).
+ *
+ * The library solves the electric-field integral equation for the surface current of
+ * a perfectly conducting body, Z j = b (arxiv 1801.03589, Sec. 2, Eq. 2 and Eq. 3),
+ * with the matrix-vector product Z x evaluated by the nested equivalent source
+ * approximation: a near-field sparse product (Sec. 3, Eq. 9) plus the five far-field
+ * stages radiation, source transfer, translation, potential transfer and reception
+ * (Sec. 3, Eqs. 10-14; the nested factorisation is Sec. 2, Eqs. 4-7).  Every stage of
+ * the product runs in the library's own CUDA kernels on one GPU.
+ *
+ * Conventions shared by all entry points
+ *   - Lengths are in the same unit as 1/k (k = wavenumber); the medium is free space
+ *     (impedance eta = mu0 c).  Time convention exp(+i w t): g = exp(-i k R)/(4 pi R).
+ *   - Unknowns are RWG functions, one per interior mesh edge (an edge shared by exactly
+ *     two triangles), numbered in lexicographic order of (smaller vertex id, larger
+ *     vertex id).  The function is l/(2A+)(r - v+) on T+ (the adjacent triangle with the
+ *     smaller index) and l/(2A-)(v- - r) on T-.
+ *   - Complex numbers are interleaved (re, im) doubles.  A block of nrhs vectors of
+ *     length N is column-major: element n of vector r is at [r * N + n].
+ *   - "dev" pointers are CUDA device pointers owned by the caller; "host" pointers are
+ *     host memory owned by the caller.  The library never frees caller memory.
+ *   - Every call returns NESA_OK (0) or a negative status; nothing throws across the
+ *     ABI.  nesa_status_str() names a status.  On error, outputs are unspecified unless
+ *     stated otherwise.
+ *   - Device work is ordered on the context's stream (default: the legacy default
+ *     stream; see nesa_set_stream).  Calls that return device results do not
+ *     synchronise unless stated.  A context is used by one host thread at a time.
+ */
+#ifndef NESA_H
+#define NESA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define NESA_OK 0
+#define NESA_ERR_INVALID_ARG (-1)   /* null pointer, size out of range, bad parameter */
+#define NESA_ERR_MESH (-2)          /* non-manifold edge, degenerate triangle, bad index,
+                                       triangles too large for the leaf size */
+#define NESA_ERR_CUDA (-3)          /* a CUDA runtime or library call failed */
+#define NESA_ERR_OOM (-4)           /* device or host allocation failed */
+#define NESA_ERR_NOT_CONVERGED (-5) /* solver stopped at its iteration limit; x and info are filled */
+#define NESA_ERR_TIMEOUT (-6)       /* a bounded device wait ran out */
+#define NESA_ERR_NUMERIC (-7)       /* NaN/Inf met, or a breakdown */
+
+/* precision of the far-field stages (nesa_params.precision) */
+#define NESA_FP64 0
+
+/* rule for the number of equivalent sources per level (nesa_params.q_mode) */
+#define NESA_Q_FIXED 0 /* Q = q_fixed in every group (the paper's choice, Sec. 3) */
+#define NESA_Q_AUTO 1  /* Q_l = max(q_fixed, (n_l+1)^2), n_l = ceil(kR + 1.8 d^(2/3) (kR)^(1/3)) */
+
+/* parts of the operator applied by nesa_matvec_parts */
+#define NESA_PART_NEAR 1 /* near field, Eq. 9 */
+#define NESA_PART_FAR 2  /* far field, Eqs. 10-14 */
+#define NESA_PART_ALL 3
+
+typedef struct nesa_ctx nesa_ctx; /* opaque; owns all device memory of one operator */
+
+typedef struct {
+  double re, im;
+} nesa_c128;
+
+typedef struct {
+  int64_t n_vertices;
+  int64_t n_triangles;
+  const double *vertices;   /* host, [n_vertices][3] */
+  const int32_t *triangles; /* host, [n_triangles][3] vertex ids, counter-clockwise seen from outside */
+} nesa_mesh;
+
+/*
+ * Octree and equivalent-source parameters (Sec. 2 and Sec. 3).
+ *   leaf_size   side of a leaf box; the root cube has side leaf_size * 2^(n_levels-1)
+ *               and is centred on the centre of the vertex bounding box
+ *   n_levels    number of octree levels (root = level 0, leaves = level n_levels-1), 1..20
+ *   q_mode      NESA_Q_FIXED or NESA_Q_AUTO
+ *   q_fixed     Q for NESA_Q_FIXED; lower bound of Q_l for NESA_Q_AUTO
+ *   q_digits    d of the NESA_Q_AUTO rule
+ *   rho_eq      radius of the equivalent-source sphere / box circumradius
+ *   rho_test    radius of the test sphere / box circumradius
+ *   pinv_eps    Tikhonov parameter of the equivalent-source fit, relative to the
+ *               Frobenius norm of the fitted matrix
+ *   precision   NESA_FP64
+ */
+typedef struct {
+  double leaf_size;
+  int32_t n_levels;
+  int32_t q_mode;
+  int32_t q_fixed;
+  int32_t precision;
+  double q_digits;
+  double rho_eq;
+  double rho_test;
+  double pinv_eps;
+} nesa_params;
+
+/* Sizes of a built operator (host struct filled by nesa_get_info). */
+#define NESA_MAX_LEVELS 20
+typedef struct {
+  int64_t n_unknowns;               /* N */
+  int64_t n_triangles;
+  int64_t n_points;                 /* 7 * n_triangles quadrature points (sources) */
+  int32_t n_levels;                 /* L + 1 */
+  int32_t l0;                       /* coarsest far level */
+  int32_t q[NESA_MAX_LEVELS];       /* Q_l (0 above l0) */
+  int64_t n_boxes[NESA_MAX_LEVELS]; /* occupied boxes per level */
+  int64_t n_interactions[NESA_MAX_LEVELS]; /* interaction-list pairs per level */
+  int64_t n_offsets[NESA_MAX_LEVELS];      /* distinct translation offsets per level */
+  int64_t near_nnz;                 /* stored near-field entries */
+  int64_t near_tri_pairs;           /* triangle pairs with a near part */
+  int64_t v_columns;                /* sum over leaves of the RWG columns of V */
+  int64_t device_bytes;             /* device memory held by the context */
+  double build_seconds;             /* wall time of nesa_build */
+} nesa_info;
+
+/* Default parameters: leaf 0.25, 3 levels, NESA_Q_AUTO, q_fixed 100, q_digits 5,
+   rho_eq 1, rho_test (2 - sqrt3/2)/(sqrt3/2), pinv_eps 1e-9, NESA_FP64. */
+void nesa_default_params(nesa_params *p);
+
+/*
+ * Build the operator of a mesh at wavenumber k (> 0).  Copies the mesh, builds the RWG
+ * functions, the octree and its lists, and fills the near-field matrix and the
+ * radiation, transfer and translation operators on the current CUDA device.  On
+ * success *out owns everything; release it with nesa_destroy.  Synchronous.
+ * Errors: INVALID_ARG, MESH, CUDA, OOM.
+ */
+int nesa_build(const nesa_mesh *mesh, double k, const nesa_params *params, nesa_ctx **out);
+
+/* Use cuda_stream (a cudaStream_t, may be NULL for the legacy stream) for all later
+   device work of the context. */
+int nesa_set_stream(nesa_ctx *ctx, void *cuda_stream);
+
+int nesa_num_unknowns(const nesa_ctx *ctx, int64_t *n);
+int nesa_get_info(const nesa_ctx *ctx, nesa_info *info);
+
+/*
+ * y = Z~ x for nrhs column-major vectors (dev, complex128, N x nrhs each; x and y must
+ * not overlap).  Z~ is the NESA approximation of the EFIE matrix: the near part exactly
+ * as Eq. 3 (point pairs in touching leaves, singular pairs by extraction) plus the five
+ * far stages.  1 <= nrhs <= 64.  Asynchronous on the context's stream.
+ */
+int nesa_matvec(nesa_ctx *ctx, const nesa_c128 *x_dev, nesa_c128 *y_dev, int nrhs);
+
+/* As nesa_matvec, applying only the parts selected by NESA_PART_* bits. */
+int nesa_matvec_parts(nesa_ctx *ctx, const nesa_c128 *x_dev, nesa_c128 *y_dev, int nrhs, int parts);
+
+/*
+ * End-to-end product from host memory: copies x (host, N x nrhs) to the device,
+ * applies nesa_matvec and copies y back to host memory.  Synchronous.  Uses device
+ * buffers held by the context (grown on demand).
+ */
+int nesa_matvec_host(nesa_ctx *ctx, const nesa_c128 *x_host, nesa_c128 *y_host, int nrhs);
+
+/*
+ * Plane-wave excitation b_m = -int E^i . phi_m with E^i = pol_r exp(-i k khat_r . r)
+ * (Sec. 2, Eq. 2; 7-point rule per triangle).  khat: host [nrhs][3] unit vectors;
+ * pol: host [nrhs][3] complex; b_dev: dev, N x nrhs.  Asynchronous.
+ */
+int nesa_rhs_planewave(nesa_ctx *ctx, const double *khat, const nesa_c128 *pol, int nrhs, nesa_c128 *b_dev);
+
+/*
+ * Export internal arrays for tests and tools (host copies).
+ *   NESA_EXPORT_POINT_LEAF  int32 [n_points][3]  integer leaf coordinates of each
+ *                           quadrature point (point 7t+i = node i of triangle t)
+ *   NESA_EXPORT_RWG         int32 [N][4]  (vertex a, vertex b, T+, T-)
+ * bytes must equal the array size.  Synchronous.
+ */
+#define NESA_EXPORT_POINT_LEAF 1
+#define NESA_EXPORT_RWG 2
+int nesa_export(const nesa_ctx *ctx, int which, void *host_buf, size_t bytes);
+
+/*
+ * Per-stage device timing of the product (for benchmarks).  When enabled, every kernel
+ * launch of nesa_matvec* is bracketed by CUDA events on the context's stream.
+ * nesa_profile_read synchronises the stream, adds the elapsed times of all launches
+ * since the last read to the totals and returns them.  Stages:
+ *   0 radiation (Eq. 10)   1 source transfer (Eq. 11)
+ *   2 translation + potential transfer (Eqs. 12-13)   3 near field + reception (Eqs. 9, 14)
+ * flops and bytes are the algorithmic FP64 flops (8 per complex multiply-add) and the
+ * bytes of operator data and vectors each launch must touch at least once.
+ */
+#define NESA_STAGES 4
+typedef struct {
+  int64_t launches[NESA_STAGES];
+  double ms[NESA_STAGES];
+  double flops[NESA_STAGES];
+  double bytes[NESA_STAGES];
+} nesa_profile;
+int nesa_profile_enable(nesa_ctx *ctx, int enable); /* also resets the totals */
+int nesa_profile_read(nesa_ctx *ctx, nesa_profile *out);
+
+/* Release all memory of the context (NULL is allowed). */
+void nesa_destroy(nesa_ctx *ctx);
+
+const char *nesa_status_str(int status);
+
+/* Message of the last failed nesa_build on this host thread ("" if none). */
+const char *nesa_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NESA_H */

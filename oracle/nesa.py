@@ -164,52 +164,64 @@ class NesaOracle:
         return self._near
 
     # ---------------------------------------------------------------- far field
+    def radiate(self, J, leaf):
+        """Eq. 10 for one leaf: s = K_L G(T_L + c, X_leaf) J_leaf  (Q_L x 4)."""
+        t = self.tree
+        idx = t.leaf_points[leaf]
+        c = t.box_center(self.L, leaf)
+        return self.K[self.L] @ (green(self.k, self.T[self.L] + c, t.points[idx]) @ J[idx])
+
+    def source_transfer(self, level, child, s_child):
+        """Eq. 11 for one child at ``level``: contribution C_l(octant) s_child to its parent."""
+        oct_ = (child[0] & 1, child[1] & 1, child[2] & 1)
+        return self.C(level, oct_) @ s_child
+
+    def translate(self, level, box, s, o_parent):
+        """Eqs. 13 and 12 for one box: o = C_l(octant)^T o_parent + sum_{b in IL} D_l(box - b) s_b."""
+        acc = np.zeros((self.Q[level], 4), np.complex128)
+        if o_parent is not None:
+            oct_ = (box[0] & 1, box[1] & 1, box[2] & 1)
+            acc += self.C(level, oct_).T @ o_parent
+        for b in self.tree.interaction_list(level, box):
+            off = (box[0] - b[0], box[1] - b[1], box[2] - b[2])
+            acc += self.D(level, off) @ s[b]
+        return acc
+
+    def receive(self, leaf, o_leaf):
+        """Eq. 14 for one leaf: field G(X_leaf, T_L + c) K_L^T o at the leaf's points."""
+        t = self.tree
+        idx = t.leaf_points[leaf]
+        c = t.box_center(self.L, leaf)
+        return idx, green(self.k, t.points[idx], self.T[self.L] + c) @ (self.K[self.L].T @ o_leaf)
+
     def far_fields(self, x, needed_leaves=None):
         """Five far-field stages (Eqs. 10-14).  Returns F [npts, 4] at the points of
         ``needed_leaves`` (all leaves by default)."""
         t = self.tree
         L, l0 = self.L, self.l0
-        X = t.points
         J = self.sources(x)
-        # Radiation (Eq. 10): s_beta = V_beta q_beta
         s = {l: {} for l in range(l0, L + 1)}
         for b in t.boxes[L]:
-            idx = t.leaf_points[b]
-            c = t.box_center(L, b)
-            s[L][b] = self.K[L] @ (green(self.k, self.T[L] + c, X[idx]) @ J[idx])
-        # Source transfer (Eq. 11), finest to coarsest
+            s[L][b] = self.radiate(J, b)
         for l in range(L, l0, -1):
             for b in t.boxes[l]:
                 p = t.parent(b)
-                oct_ = (b[0] & 1, b[1] & 1, b[2] & 1)
-                s[l - 1][p] = s[l - 1].get(p, 0) + self.C(l, oct_) @ s[l][b]
-        # boxes whose incoming field is needed
+                s[l - 1][p] = s[l - 1].get(p, 0) + self.source_transfer(l, b, s[l][b])
         if needed_leaves is None:
             need = {l: list(t.boxes[l]) for l in range(l0, L + 1)}
         else:
             need = {L: sorted(set(needed_leaves))}
             for l in range(L - 1, l0 - 1, -1):
                 need[l] = sorted({t.parent(b) for b in need[l + 1]})
-        # Translation (Eq. 12) and potential transfer (Eq. 13), coarsest to finest
         o = {l: {} for l in range(l0, L + 1)}
         for l in range(l0, L + 1):
             for a in need[l]:
-                acc = np.zeros((self.Q[l], 4), np.complex128)
-                if l > l0:
-                    p = t.parent(a)
-                    oct_ = (a[0] & 1, a[1] & 1, a[2] & 1)
-                    acc += self.C(l, oct_).T @ o[l - 1][p]
-                for b in t.interaction_list(l, a):
-                    off = (a[0] - b[0], a[1] - b[1], a[2] - b[2])
-                    acc += self.D(l, off) @ s[l][b]
-                o[l][a] = acc
+                o[l][a] = self.translate(l, a, s[l], o[l - 1][t.parent(a)] if l > l0 else None)
             self._D = {key: v for key, v in self._D.items() if key[0] != l}
-        # Reception (Eq. 14): field at the points of each needed leaf
-        F = np.zeros((len(X), 4), np.complex128)
+        F = np.zeros((len(t.points), 4), np.complex128)
         for a in need[L]:
-            idx = t.leaf_points[a]
-            c = t.box_center(L, a)
-            F[idx] = green(self.k, X[idx], self.T[L] + c) @ (self.K[L].T @ o[L][a])
+            idx, f = self.receive(a, o[L][a])
+            F[idx] = f
         return F
 
     def far_rows(self, x, rows=None):

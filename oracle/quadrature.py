@@ -22,9 +22,12 @@ WEIGHTS = np.array([9.0 / 40.0, _W1, _W1, _W1, _W2, _W2, _W2])
 
 
 def triangle_points(vertices, triangles):
-    """Quadrature nodes ``[nt, 7, 3]`` of every triangle."""
-    v = vertices[triangles]  # [nt, 3, 3]
-    return np.einsum("pc,tcx->tpx", BARY, v)
+    """Quadrature nodes ``[nt, 7, 3]`` of every triangle, evaluated as
+    (l0 v0 + l1 v1) + l2 v2 with separately rounded products and sums, so that a node
+    lying exactly on a box face is reproducible."""
+    v = np.asarray(vertices, np.float64)[np.asarray(triangles)]  # [nt, 3, 3]
+    B = BARY[None, :, :, None]
+    return (B[:, :, 0] * v[:, None, 0, :] + B[:, :, 1] * v[:, None, 1, :]) + B[:, :, 2] * v[:, None, 2, :]
 
 
 def triangle_areas(vertices, triangles):

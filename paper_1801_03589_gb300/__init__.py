@@ -1,0 +1,228 @@
+"""Python binding of libnesa (the GB300 NESA/EFIE library).
+
+Argument marshalling only: every stage of the product and of the solver runs in the
+library's CUDA kernels.  Device vectors are torch tensors (complex128, shape
+``[nrhs, N]``, contiguous, on the CUDA device of the context), passed by pointer.
+If ``libnesa.so`` is missing or cannot be loaded every call raises; there is no
+fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libnesa.so")
+
+OK = 0
+ERR_INVALID_ARG, ERR_MESH, ERR_CUDA, ERR_OOM, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_NUMERIC = -1, -2, -3, -4, -5, -6, -7
+FP64 = 0
+Q_FIXED, Q_AUTO = 0, 1
+PART_NEAR, PART_FAR, PART_ALL = 1, 2, 3
+EXPORT_POINT_LEAF, EXPORT_RWG = 1, 2
+MAX_LEVELS = 20
+
+
+class NesaError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        super().__init__("libnesa status %d (%s)%s" % (status, _status_str(status), (": " + what) if what else ""))
+
+
+class Mesh(ctypes.Structure):
+    _fields_ = [("n_vertices", ctypes.c_int64), ("n_triangles", ctypes.c_int64),
+                ("vertices", ctypes.c_void_p), ("triangles", ctypes.c_void_p)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("leaf_size", ctypes.c_double), ("n_levels", ctypes.c_int32), ("q_mode", ctypes.c_int32),
+                ("q_fixed", ctypes.c_int32), ("precision", ctypes.c_int32), ("q_digits", ctypes.c_double),
+                ("rho_eq", ctypes.c_double), ("rho_test", ctypes.c_double), ("pinv_eps", ctypes.c_double)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n_unknowns", ctypes.c_int64), ("n_triangles", ctypes.c_int64), ("n_points", ctypes.c_int64),
+                ("n_levels", ctypes.c_int32), ("l0", ctypes.c_int32), ("q", ctypes.c_int32 * MAX_LEVELS),
+                ("n_boxes", ctypes.c_int64 * MAX_LEVELS), ("n_interactions", ctypes.c_int64 * MAX_LEVELS),
+                ("n_offsets", ctypes.c_int64 * MAX_LEVELS), ("near_nnz", ctypes.c_int64),
+                ("near_tri_pairs", ctypes.c_int64), ("v_columns", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("build_seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        nl = self.n_levels
+        return dict(n_unknowns=self.n_unknowns, n_triangles=self.n_triangles, n_points=self.n_points,
+                    n_levels=nl, l0=self.l0, q=list(self.q[:nl]), n_boxes=list(self.n_boxes[:nl]),
+                    n_interactions=list(self.n_interactions[:nl]), n_offsets=list(self.n_offsets[:nl]),
+                    near_nnz=self.near_nnz, near_tri_pairs=self.near_tri_pairs, v_columns=self.v_columns,
+                    device_bytes=self.device_bytes, build_seconds=self.build_seconds)
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64 * 4), ("ms", ctypes.c_double * 4), ("flops", ctypes.c_double * 4),
+                ("bytes", ctypes.c_double * 4)]
+
+
+STAGES = ("radiation", "source_transfer", "translation", "near_reception")
+
+_lib = None
+
+
+def lib():
+    """Load libnesa.so (raises if it is missing: the library has no CPU fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libnesa.so not built: run paper_1801_03589_gb300/build.py (or __graft_entry__.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, I64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+        sig = {
+            "nesa_default_params": (None, [P]),
+            "nesa_build": (I, [P, D, P, P]),
+            "nesa_set_stream": (I, [P, P]),
+            "nesa_num_unknowns": (I, [P, P]),
+            "nesa_get_info": (I, [P, P]),
+            "nesa_matvec": (I, [P, P, P, I]),
+            "nesa_matvec_parts": (I, [P, P, P, I, I]),
+            "nesa_matvec_host": (I, [P, P, P, I]),
+            "nesa_rhs_planewave": (I, [P, P, P, I, P]),
+            "nesa_export": (I, [P, I, P, ctypes.c_size_t]),
+            "nesa_destroy": (None, [P]),
+            "nesa_status_str": (ctypes.c_char_p, [I]),
+            "nesa_last_error": (ctypes.c_char_p, []),
+            "nesa_profile_enable": (I, [P, I]),
+            "nesa_profile_read": (I, [P, P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _status_str(s):
+    try:
+        return lib().nesa_status_str(s).decode()
+    except Exception:  # noqa: BLE001 - only used to format an error
+        return "?"
+
+
+def _check(status):
+    if status != OK:
+        what = lib().nesa_last_error().decode()
+        raise NesaError(status, what)
+
+
+def default_params(**overrides):
+    p = Params()
+    lib().nesa_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise TypeError("unknown parameter %s" % k)
+        setattr(p, k, v)
+    return p
+
+
+def _dev_ptr(t, n, what):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.complex128 or not t.is_contiguous():
+        raise TypeError("%s must be a contiguous complex128 CUDA tensor" % what)
+    if t.dim() == 1:
+        t = t.view(1, -1)
+    if t.shape[-1] != n:
+        raise ValueError("%s has %d columns, expected %d" % (what, t.shape[-1], n))
+    return t, t.data_ptr(), t.shape[0]
+
+
+class Nesa:
+    """One built operator (owns its device memory)."""
+
+    def __init__(self, vertices, triangles, k, **params):
+        v = np.ascontiguousarray(vertices, dtype=np.float64)
+        t = np.ascontiguousarray(triangles, dtype=np.int32)
+        mesh = Mesh(len(v), len(t), v.ctypes.data, t.ctypes.data)
+        self.params = default_params(**params)
+        h = ctypes.c_void_p()
+        _check(lib().nesa_build(ctypes.byref(mesh), float(k), ctypes.byref(self.params), ctypes.byref(h)))
+        self._h = h
+        self.k = float(k)
+        n = ctypes.c_int64()
+        _check(lib().nesa_num_unknowns(h, ctypes.byref(n)))
+        self.n = n.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().nesa_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+    def info(self):
+        i = Info()
+        _check(lib().nesa_get_info(self._h, ctypes.byref(i)))
+        return i.as_dict()
+
+    def set_stream(self, stream):
+        """Order the context's device work on a torch.cuda.Stream (or a raw handle)."""
+        handle = getattr(stream, "cuda_stream", stream)
+        _check(lib().nesa_set_stream(self._h, ctypes.c_void_p(handle)))
+
+    def matvec(self, x, y=None, parts=PART_ALL):
+        """y = Z~ x for x of shape [nrhs, N] (complex128, CUDA).  Asynchronous."""
+        import torch
+        x, px, nrhs = _dev_ptr(x, self.n, "x")
+        if y is None:
+            y = torch.empty_like(x)
+        y, py, nr2 = _dev_ptr(y, self.n, "y")
+        if nr2 != nrhs:
+            raise ValueError("x and y differ in nrhs")
+        _check(lib().nesa_matvec_parts(self._h, px, py, nrhs, parts))
+        return y
+
+    def matvec_host(self, x):
+        """End to end from host memory: x numpy or CPU tensor [nrhs, N] complex128."""
+        xa = np.ascontiguousarray(np.atleast_2d(np.asarray(x)), dtype=np.complex128)
+        y = np.empty_like(xa)
+        _check(lib().nesa_matvec_host(self._h, xa.ctypes.data, y.ctypes.data, xa.shape[0]))
+        return y
+
+    def matvec_host_ptr(self, x_ptr, y_ptr, nrhs):
+        """End to end product between two host buffers given by address (e.g. pinned tensors)."""
+        _check(lib().nesa_matvec_host(self._h, ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr), int(nrhs)))
+
+    def rhs_planewave(self, khat, pol, out=None):
+        import torch
+        kh = np.ascontiguousarray(np.atleast_2d(khat), dtype=np.float64)
+        pl = np.ascontiguousarray(np.atleast_2d(pol), dtype=np.complex128)
+        nrhs = kh.shape[0]
+        if out is None:
+            out = torch.empty((nrhs, self.n), dtype=torch.complex128, device="cuda")
+        out, po, nr2 = _dev_ptr(out, self.n, "out")
+        if nr2 != nrhs or pl.shape != (nrhs, 3):
+            raise ValueError("khat, pol and out disagree in nrhs")
+        _check(lib().nesa_rhs_planewave(self._h, kh.ctypes.data, pl.ctypes.data, nrhs, po))
+        return out
+
+    def profile_enable(self, on=True):
+        _check(lib().nesa_profile_enable(self._h, 1 if on else 0))
+
+    def profile_read(self):
+        """Per-stage totals since profile_enable: launches, device ms, algorithmic flops and bytes."""
+        p = Profile()
+        _check(lib().nesa_profile_read(self._h, ctypes.byref(p)))
+        return {name: dict(launches=p.launches[i], ms=p.ms[i], flops=p.flops[i], bytes=p.bytes[i])
+                for i, name in enumerate(STAGES)}
+
+    def export_point_leaf(self):
+        a = np.empty((self.info()["n_points"], 3), np.int32)
+        _check(lib().nesa_export(self._h, EXPORT_POINT_LEAF, a.ctypes.data, a.nbytes))
+        return a
+
+    def export_rwg(self):
+        a = np.empty((self.n, 4), np.int32)
+        _check(lib().nesa_export(self._h, EXPORT_RWG, a.ctypes.data, a.nbytes))
+        return a

@@ -1,0 +1,112 @@
+// Device-side types and helpers shared by the libnesa kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "nesa_internal.h"
+
+namespace nesa {
+
+typedef double2 cplx;  // (re, im)
+
+__host__ __device__ inline cplx cmk(double re, double im) { return make_double2(re, im); }
+__host__ __device__ inline cplx cadd(cplx a, cplx b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline cplx cmul(cplx a, cplx b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__host__ __device__ inline cplx cscale(cplx a, double s) { return make_double2(a.x * s, a.y * s); }
+// acc += a * b with four fused multiply-adds
+__device__ __forceinline__ void cfma(cplx &acc, cplx a, cplx b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+
+// free-space Green's function exp(-i k R)/(4 pi R) (time convention exp(+i w t))
+__device__ __forceinline__ cplx green(double k, double R) {
+  double s, c;
+  sincos(k * R, &s, &c);
+  double f = 0.07957747154594767 / R;  // 1/(4 pi R)
+  return make_double2(c * f, -s * f);
+}
+
+// Distances between points given as separate coordinates.
+__device__ __forceinline__ double dist3(double ax, double ay, double az, double bx, double by, double bz) {
+  double dx = ax - bx, dy = ay - by, dz = az - bz;
+  return sqrt(dx * dx + dy * dy + dz * dz);
+}
+
+// Per-level device arrays of the far-field structure.
+struct DevLevel {
+  int q = 0;           // Q_l
+  int64_t nbox = 0;
+  int64_t nil = 0;     // interaction pairs
+  int64_t noff = 0;    // distinct offsets
+  double width = 0.0;
+  int32_t *parent = nullptr, *octant = nullptr, *child_ptr = nullptr;
+  int32_t *il_ptr = nullptr, *il_src = nullptr, *il_slot = nullptr;
+  cplx *D = nullptr;   // [noff][q][q] column-major per offset
+  cplx *C = nullptr;   // [8][q_{l-1}][q] column-major (rows: parent's sources)
+  cplx *Ct = nullptr;  // [8][q][q_{l-1}] column-major (transpose of C)
+  cplx *K = nullptr;   // [q][2q] column-major
+  cplx *s = nullptr;   // workspace [nbox][4*nrhs][q] outgoing equivalent sources
+  cplx *o = nullptr;   // workspace [nbox][4*nrhs][q] incoming field at the equivalent points
+};
+
+}  // namespace nesa
+
+// The context behind the opaque ABI handle.
+struct nesa_ctx {
+  nesa::HostModel h;
+  cudaStream_t stream = nullptr;
+  double k = 0.0, eta = 0.0;
+  int64_t n = 0, nt = 0, np = 0, nleaf = 0;
+  int L = 0, l0 = 0;
+  nesa_info info{};
+  // mesh and basis on the device
+  double *d_pts = nullptr;       // [np][3]
+  double *d_verts = nullptr;     // [nv][3]
+  int32_t *d_tris = nullptr;     // [nt][3]
+  int32_t *d_tri_rwg = nullptr;  // [nt][3]
+  double *d_tri_sl = nullptr;    // [nt][3]
+  int32_t *d_rwg_tri = nullptr;  // [n][2]
+  int32_t *d_rwg_free = nullptr; // [n][2]
+  // radiation / reception
+  int32_t *d_vc_ptr = nullptr, *d_vc_rwg = nullptr, *d_vc_leaf = nullptr;
+  int32_t *d_rx_ptr = nullptr, *d_rx_col = nullptr;
+  nesa::cplx *d_V = nullptr;     // [ncol][4][q_L]
+  // near field (CSR by RWG row)
+  int64_t *d_nz_ptr = nullptr;
+  int32_t *d_nz_col = nullptr;
+  nesa::cplx *d_nz_val = nullptr;
+  // levels
+  nesa::DevLevel lev[NESA_MAX_LEVELS];
+  int nrhs_cap = 0;              // capacity of the s/o workspaces
+  int max_leaf_cols = 0;         // largest number of V columns of one leaf
+  // host-pointer product buffers
+  nesa::cplx *d_hx = nullptr, *d_hy = nullptr;
+  int hbuf_cap = 0;
+  size_t device_bytes = 0;
+  // stage timing (nesa_profile_enable)
+  bool profiling = false;
+  struct Pending {
+    int stage;
+    cudaEvent_t a, b;
+    double flops, bytes;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> event_pool;
+  nesa_profile prof{};
+  std::vector<void *> allocs;    // every device allocation owned by the context
+};
+
+namespace nesa {
+// device allocation with accounting; throws Error on failure
+void *dalloc(nesa_ctx *c, size_t bytes);
+void dfree(nesa_ctx *c, void *p);
+void check_cuda(cudaError_t e, const char *what);
+void launch_matvec(nesa_ctx *c, const cplx *x, cplx *y, int nrhs, int parts);
+int ensure_workspace(nesa_ctx *c, int nrhs);
+}  // namespace nesa

@@ -1,0 +1,424 @@
+// The NESA matrix-vector product y = Z~ x on the device (FP64).
+//
+// Stages (paper Sec. 3), one kernel launch each (per level where the stage is per level):
+//   k_radiate     s_beta = V_beta x_beta                      (Eq. 10)
+//   k_upward      s_P   += C_l(octant) s_child, l = L..l0+1    (Eq. 11)
+//   k_translate   o_a    = C_l(octant)^T o_P(a) + sum_{b in IL(a)} D_l(a - b) s_b
+//                                                             (Eq. 13 and Eq. 12, l = l0..L)
+//   k_near_receive y_m   = sum_n Z^near_mn x_n                 (Eq. 9)
+//                        + (-i eta k) sum_ch gamma_ch V^T o    (Eq. 14; U = V^T)
+// Every output element is owned by one thread or one warp (no atomics), so the
+// product is deterministic.  All four kernels are bound by the FP64 pipe: a complex
+// multiply-add is four FP64 FMAs and the matrices are read from L2/HBM at well below
+// its bandwidth.
+//
+// Workspace layout per level l >= l0: s_l, o_l = [nbox][4*nrhs][Q_l], column 4r + ch
+// holds channel ch (x, y, z, rho) of right-hand side r.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "nesa_device.cuh"
+
+namespace nesa {
+
+void dfree(nesa_ctx *c, void *p) {
+  if (!p) return;
+  auto it = std::find(c->allocs.begin(), c->allocs.end(), p);
+  if (it != c->allocs.end()) c->allocs.erase(it);
+  cudaFree(p);
+}
+
+int ensure_workspace(nesa_ctx *c, int nrhs) {
+  if (nrhs <= c->nrhs_cap) return NESA_OK;
+  for (int l = c->l0; l <= c->L; ++l) {
+    DevLevel &d = c->lev[l];
+    dfree(c, d.s);
+    dfree(c, d.o);
+    d.s = d.o = nullptr;
+    size_t bytes = sizeof(cplx) * (size_t)d.nbox * 4 * nrhs * d.q;
+    d.s = (cplx *)dalloc(c, bytes);
+    d.o = (cplx *)dalloc(c, bytes);
+  }
+  c->nrhs_cap = nrhs;
+  return NESA_OK;
+}
+
+// Row tiling of a (Q rows x 4 channels) block: ntile tiles of tr rows, 4*tr threads.
+struct Tiling {
+  int ntile, tr, threads;
+};
+static Tiling tiling(int q) {
+  const int maxt = 512;
+  int ntile = (4 * q + maxt - 1) / maxt;
+  int tr = (q + ntile - 1) / ntile;
+  int threads = ((4 * tr + 31) / 32) * 32;
+  return {ntile, tr, threads};
+}
+
+// ------------------------------------------------------------------ radiation (Eq. 10)
+__global__ void __launch_bounds__(512) k_radiate(cplx *__restrict__ s, const cplx *__restrict__ V,
+                                                 const int32_t *__restrict__ vc_ptr, const int32_t *__restrict__ vc_rwg,
+                                                 const cplx *__restrict__ x, int64_t n, int nrhs, int q, int tr) {
+  extern __shared__ cplx xs[];
+  const int32_t b = blockIdx.x;
+  const int tile = blockIdx.y;
+  const int ch = threadIdx.x / tr;
+  const int i = tile * tr + threadIdx.x % tr;
+  const bool active = ch < 4 && i < q;
+  const int32_t g0 = vc_ptr[b], ns = vc_ptr[b + 1] - g0;
+  const cplx *Vb = V + (int64_t)4 * g0 * q;
+  for (int r = 0; r < nrhs; ++r) {
+    __syncthreads();
+    for (int j = threadIdx.x; j < ns; j += blockDim.x) xs[j] = x[(int64_t)r * n + vc_rwg[g0 + j]];
+    __syncthreads();
+    if (!active) continue;
+    cplx acc = {0.0, 0.0};
+    const cplx *vp = Vb + (int64_t)ch * q + i;
+#pragma unroll 4
+    for (int j = 0; j < ns; ++j) cfma(acc, vp[(int64_t)4 * j * q], xs[j]);
+    s[((int64_t)b * 4 * nrhs + 4 * r + ch) * q + i] = acc;
+  }
+}
+
+// ------------------------------------------------------------------ source transfer (Eq. 11)
+// parent P at level l-1 (rows qp) gathers its children at level l (rows q)
+__global__ void __launch_bounds__(512) k_upward(cplx *__restrict__ sp, const cplx *__restrict__ sc,
+                                                const cplx *__restrict__ C, const int32_t *__restrict__ child_ptr,
+                                                const int32_t *__restrict__ octant, int nrhs, int qp, int q, int tr) {
+  extern __shared__ cplx col[];  // [4][q]
+  const int32_t P = blockIdx.x;
+  const int tile = blockIdx.y;
+  const int ch = threadIdx.x / tr;
+  const int i = tile * tr + threadIdx.x % tr;
+  const bool active = ch < 4 && i < qp;
+  const int32_t c0 = child_ptr[P], c1 = child_ptr[P + 1];
+  for (int r = 0; r < nrhs; ++r) {
+    cplx acc = {0.0, 0.0};
+    for (int32_t cb = c0; cb < c1; ++cb) {
+      __syncthreads();
+      const cplx *src = sc + ((int64_t)cb * 4 * nrhs + 4 * r) * q;
+      for (int j = threadIdx.x; j < 4 * q; j += blockDim.x) col[j] = src[j];
+      __syncthreads();
+      if (!active) continue;
+      const cplx *Cm = C + (int64_t)octant[cb] * qp * q + i;
+      const cplx *cs = col + ch * q;
+#pragma unroll 4
+      for (int j = 0; j < q; ++j) cfma(acc, Cm[(int64_t)j * qp], cs[j]);
+    }
+    if (active) sp[((int64_t)P * 4 * nrhs + 4 * r + ch) * qp + i] = acc;
+  }
+}
+
+// ------------------------------------------------------------------ translation + potential transfer
+__global__ void __launch_bounds__(512) k_translate(cplx *__restrict__ o, const cplx *__restrict__ s,
+                                                   const cplx *__restrict__ D, const int32_t *__restrict__ il_ptr,
+                                                   const int32_t *__restrict__ il_src,
+                                                   const int32_t *__restrict__ il_slot, const cplx *__restrict__ op,
+                                                   const cplx *__restrict__ Ct, const int32_t *__restrict__ parent,
+                                                   const int32_t *__restrict__ octant, int nrhs, int q, int qp,
+                                                   int tr) {
+  extern __shared__ cplx col[];  // [4][max(q, qp)]
+  const int32_t a = blockIdx.x;
+  const int tile = blockIdx.y;
+  const int ch = threadIdx.x / tr;
+  const int i = tile * tr + threadIdx.x % tr;
+  const bool active = ch < 4 && i < q;
+  const int32_t e0 = il_ptr[a], e1 = il_ptr[a + 1];
+  for (int r = 0; r < nrhs; ++r) {
+    cplx acc = {0.0, 0.0};
+    if (op) {  // potential transfer from the parent (Eq. 13): o_a += C^T o_P
+      __syncthreads();
+      const int32_t P = parent[a];
+      const cplx *src = op + ((int64_t)P * 4 * nrhs + 4 * r) * qp;
+      for (int j = threadIdx.x; j < 4 * qp; j += blockDim.x) col[j] = src[j];
+      __syncthreads();
+      if (active) {
+        const cplx *Bm = Ct + (int64_t)octant[a] * q * qp + i;
+        const cplx *cs = col + ch * qp;
+#pragma unroll 4
+        for (int j = 0; j < qp; ++j) cfma(acc, Bm[(int64_t)j * q], cs[j]);
+      }
+    }
+    for (int32_t e = e0; e < e1; ++e) {  // translations (Eq. 12)
+      __syncthreads();
+      const cplx *src = s + ((int64_t)il_src[e] * 4 * nrhs + 4 * r) * q;
+      for (int j = threadIdx.x; j < 4 * q; j += blockDim.x) col[j] = src[j];
+      __syncthreads();
+      if (!active) continue;
+      const cplx *Dm = D + (int64_t)il_slot[e] * q * q + i;
+      const cplx *cs = col + ch * q;
+#pragma unroll 4
+      for (int j = 0; j < q; ++j) cfma(acc, Dm[(int64_t)j * q], cs[j]);
+    }
+    if (active) o[((int64_t)a * 4 * nrhs + 4 * r + ch) * q + i] = acc;
+  }
+}
+
+// ------------------------------------------------------------------ near field + reception
+__global__ void __launch_bounds__(256) k_near_receive(cplx *__restrict__ y, const cplx *__restrict__ x, int64_t n,
+                                                      int nrhs, const int64_t *__restrict__ nz_ptr,
+                                                      const int32_t *__restrict__ nz_col,
+                                                      const cplx *__restrict__ nz_val, const int32_t *__restrict__ rx_ptr,
+                                                      const int32_t *__restrict__ rx_col,
+                                                      const int32_t *__restrict__ vc_leaf, const cplx *__restrict__ V,
+                                                      const cplx *__restrict__ oL, int q, double eta_k, double inv_k2,
+                                                      int parts) {
+  const int64_t m = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (m >= n) return;
+  for (int r = 0; r < nrhs; ++r) {
+    cplx near = {0.0, 0.0}, far = {0.0, 0.0};
+    if (parts & NESA_PART_NEAR) {
+      const cplx *xr = x + (int64_t)r * n;
+      for (int64_t e = nz_ptr[m] + lane; e < nz_ptr[m + 1]; e += 32) cfma(near, nz_val[e], xr[nz_col[e]]);
+    }
+    if (parts & NESA_PART_FAR) {
+      for (int32_t e = rx_ptr[m]; e < rx_ptr[m + 1]; ++e) {
+        const int32_t g = rx_col[e];
+        const int32_t lf = vc_leaf[g];
+        const cplx *vg = V + (int64_t)4 * g * q;
+        const cplx *ol = oL + ((int64_t)lf * 4 * nrhs + 4 * r) * q;
+        for (int ch = 0; ch < 4; ++ch) {
+          cplx t = {0.0, 0.0};
+          for (int i = lane; i < q; i += 32) cfma(t, vg[ch * q + i], ol[ch * q + i]);
+          const double gam = ch < 3 ? 1.0 : -inv_k2;
+          far.x = fma(gam, t.x, far.x);
+          far.y = fma(gam, t.y, far.y);
+        }
+      }
+    }
+    // -i eta k * far
+    cplx v = make_double2(near.x + eta_k * far.y, near.y - eta_k * far.x);
+    for (int off = 16; off > 0; off >>= 1) {
+      v.x += __shfl_down_sync(0xffffffffu, v.x, off);
+      v.y += __shfl_down_sync(0xffffffffu, v.y, off);
+    }
+    if (lane == 0) y[(int64_t)r * n + m] = v;
+  }
+}
+
+static inline unsigned grid_for(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+// Stage timing: an event before and after a launch when profiling is on.
+static cudaEvent_t take_event(nesa_ctx *c) {
+  if (!c->event_pool.empty()) {
+    cudaEvent_t e = c->event_pool.back();
+    c->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  check_cuda(cudaEventCreate(&e), "event");
+  return e;
+}
+struct StageScope {
+  nesa_ctx *c;
+  int stage;
+  double flops, bytes;
+  cudaEvent_t a = nullptr;
+  StageScope(nesa_ctx *c_, int s, double f, double b) : c(c_), stage(s), flops(f), bytes(b) {
+    if (c->profiling) {
+      a = take_event(c);
+      cudaEventRecord(a, c->stream);
+    }
+  }
+  ~StageScope() {
+    if (!c->profiling) return;
+    cudaEvent_t b = take_event(c);
+    cudaEventRecord(b, c->stream);
+    c->pending.push_back({stage, a, b, flops, bytes});
+  }
+};
+
+// Launch the product on the context's stream.
+void launch_matvec(nesa_ctx *c, const cplx *x, cplx *y, int nrhs, int parts) {
+  cudaStream_t st = c->stream;
+  const int L = c->L, l0 = c->l0;
+  const double B = sizeof(cplx);
+  const double ncol = (double)c->info.v_columns;
+  if (parts & NESA_PART_FAR) {
+    {  // radiation
+      DevLevel &d = c->lev[L];
+      Tiling t = tiling(d.q);
+      const int maxs = c->max_leaf_cols;
+      size_t smem = sizeof(cplx) * (size_t)std::max(1, maxs);
+      StageScope sc(c, 0, 32.0 * nrhs * ncol * d.q, B * (4.0 * ncol * d.q + nrhs * (c->n + 4.0 * d.nbox * d.q)));
+      k_radiate<<<dim3((unsigned)d.nbox, t.ntile), t.threads, smem, st>>>(d.s, c->d_V, c->d_vc_ptr, c->d_vc_rwg, x,
+                                                                          c->n, nrhs, d.q, t.tr);
+    }
+    for (int l = L; l > l0; --l) {  // source transfer
+      DevLevel &d = c->lev[l], &p = c->lev[l - 1];
+      Tiling t = tiling(p.q);
+      size_t smem = sizeof(cplx) * 4 * (size_t)d.q;
+      StageScope sc(c, 1, 32.0 * nrhs * d.nbox * (double)p.q * d.q,
+                    B * (8.0 * p.q * d.q + 4.0 * nrhs * ((double)d.nbox * d.q + (double)p.nbox * p.q)));
+      k_upward<<<dim3((unsigned)p.nbox, t.ntile), t.threads, smem, st>>>(p.s, d.s, d.C, p.child_ptr, d.octant, nrhs,
+                                                                         p.q, d.q, t.tr);
+    }
+    for (int l = l0; l <= L; ++l) {  // translation and potential transfer
+      DevLevel &d = c->lev[l];
+      Tiling t = tiling(d.q);
+      const bool down = l > l0;
+      const int qp = down ? c->lev[l - 1].q : 0;
+      size_t smem = sizeof(cplx) * 4 * (size_t)std::max(d.q, qp);
+      double fl = 32.0 * nrhs * ((double)d.nil * d.q * d.q + (down ? (double)d.nbox * d.q * qp : 0.0));
+      double by = B * ((double)d.noff * d.q * d.q + (down ? 8.0 * d.q * qp : 0.0) +
+                       4.0 * nrhs * (2.0 * d.nbox * d.q + (down ? (double)c->lev[l - 1].nbox * qp : 0.0)));
+      StageScope sc(c, 2, fl, by);
+      k_translate<<<dim3((unsigned)d.nbox, t.ntile), t.threads, smem, st>>>(
+          d.o, d.s, d.D, d.il_ptr, d.il_src, d.il_slot, down ? c->lev[l - 1].o : nullptr, down ? d.Ct : nullptr,
+          d.parent, d.octant, nrhs, d.q, qp, t.tr);
+    }
+  }
+  const DevLevel &dL = c->lev[L];
+  const double nnz = (double)c->info.near_nnz;
+  double fl = ((parts & NESA_PART_NEAR) ? 8.0 * nrhs * nnz : 0.0) +
+              ((parts & NESA_PART_FAR) ? 32.0 * nrhs * ncol * dL.q : 0.0);
+  double by = ((parts & NESA_PART_NEAR) ? (B + 4.0) * nnz + 8.0 * (c->n + 1) : 0.0) +
+              ((parts & NESA_PART_FAR) ? B * 4.0 * ncol * dL.q + B * 4.0 * nrhs * dL.nbox * dL.q : 0.0) +
+              B * 2.0 * nrhs * c->n;
+  StageScope sc(c, 3, fl, by);
+  k_near_receive<<<grid_for(c->n * 32, 256), 256, 0, st>>>(y, x, c->n, nrhs, c->d_nz_ptr, c->d_nz_col, c->d_nz_val,
+                                                          c->d_rx_ptr, c->d_rx_col, c->d_vc_leaf, c->d_V, dL.o, dL.q,
+                                                          c->eta * c->k, 1.0 / (c->k * c->k), parts);
+}
+
+// ------------------------------------------------------------------ plane-wave excitation
+// b_m = -sum_{T in supp m} sum_p w_p sl (r_p - v)/2 . pol exp(-i k khat.r_p)
+__global__ void k_rhs_planewave(cplx *b, int64_t n, int nrhs, const double *khat, const cplx *pol,
+                                const int32_t *rwg_tri, const int32_t *rwg_free, const int32_t *tris,
+                                const double *verts, const double *tri_sl, const double *pts, const double *w7,
+                                double k) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= n * nrhs) return;
+  int64_t m = idx % n;
+  int r = (int)(idx / n);
+  const double *kh = khat + 3 * r;
+  const cplx *pl = pol + 3 * r;
+  cplx acc = {0.0, 0.0};
+  for (int s = 0; s < 2; ++s) {
+    int32_t t = rwg_tri[2 * m + s];
+    int fr = rwg_free[2 * m + s];
+    double sl = tri_sl[3 * t + fr];
+    const double *v = verts + 3 * (int64_t)tris[3 * t + fr];
+    for (int p = 0; p < 7; ++p) {
+      const double *rp = pts + 3 * (7 * (int64_t)t + p);
+      double ph = -k * (kh[0] * rp[0] + kh[1] * rp[1] + kh[2] * rp[2]);
+      double sn, cs;
+      sincos(ph, &sn, &cs);
+      double f = 0.5 * w7[p] * sl;
+      cplx dp = {0.0, 0.0};
+      for (int x = 0; x < 3; ++x) {
+        double a = f * (rp[x] - v[x]);
+        dp.x += a * pl[x].x;
+        dp.y += a * pl[x].y;
+      }
+      acc = cadd(acc, cmul(dp, make_double2(cs, sn)));
+    }
+  }
+  b[(int64_t)r * n + m] = make_double2(-acc.x, -acc.y);
+}
+
+}  // namespace nesa
+
+using namespace nesa;
+
+extern "C" {
+
+int nesa_matvec_parts(nesa_ctx *c, const nesa_c128 *x, nesa_c128 *y, int nrhs, int parts) {
+  if (!c || !x || !y || nrhs < 1 || nrhs > 64 || parts < 1 || parts > NESA_PART_ALL) return NESA_ERR_INVALID_ARG;
+  try {
+    ensure_workspace(c, nrhs);
+    launch_matvec(c, (const cplx *)x, (cplx *)y, nrhs, parts);
+    check_cuda(cudaGetLastError(), "matvec launch");
+  } catch (const Error &e) {
+    return e.status;
+  }
+  return NESA_OK;
+}
+
+int nesa_profile_enable(nesa_ctx *c, int enable) {
+  if (!c) return NESA_ERR_INVALID_ARG;
+  cudaStreamSynchronize(c->stream);
+  for (auto &p : c->pending) {
+    c->event_pool.push_back(p.a);
+    c->event_pool.push_back(p.b);
+  }
+  c->pending.clear();
+  c->prof = nesa_profile{};
+  c->profiling = enable != 0;
+  return NESA_OK;
+}
+
+int nesa_profile_read(nesa_ctx *c, nesa_profile *out) {
+  if (!c || !out) return NESA_ERR_INVALID_ARG;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return NESA_ERR_CUDA;
+  for (auto &p : c->pending) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) != cudaSuccess) return NESA_ERR_CUDA;
+    c->prof.launches[p.stage] += 1;
+    c->prof.ms[p.stage] += ms;
+    c->prof.flops[p.stage] += p.flops;
+    c->prof.bytes[p.stage] += p.bytes;
+    c->event_pool.push_back(p.a);
+    c->event_pool.push_back(p.b);
+  }
+  c->pending.clear();
+  *out = c->prof;
+  return NESA_OK;
+}
+
+int nesa_matvec(nesa_ctx *c, const nesa_c128 *x, nesa_c128 *y, int nrhs) {
+  return nesa_matvec_parts(c, x, y, nrhs, NESA_PART_ALL);
+}
+
+int nesa_matvec_host(nesa_ctx *c, const nesa_c128 *xh, nesa_c128 *yh, int nrhs) {
+  if (!c || !xh || !yh || nrhs < 1 || nrhs > 64) return NESA_ERR_INVALID_ARG;
+  try {
+    if (nrhs > c->hbuf_cap) {
+      dfree(c, c->d_hx);
+      dfree(c, c->d_hy);
+      c->d_hx = (cplx *)dalloc(c, sizeof(cplx) * (size_t)c->n * nrhs);
+      c->d_hy = (cplx *)dalloc(c, sizeof(cplx) * (size_t)c->n * nrhs);
+      c->hbuf_cap = nrhs;
+    }
+    size_t bytes = sizeof(cplx) * (size_t)c->n * nrhs;
+    check_cuda(cudaMemcpyAsync(c->d_hx, xh, bytes, cudaMemcpyHostToDevice, c->stream), "H2D");
+    ensure_workspace(c, nrhs);
+    launch_matvec(c, c->d_hx, c->d_hy, nrhs, NESA_PART_ALL);
+    check_cuda(cudaGetLastError(), "matvec launch");
+    check_cuda(cudaMemcpyAsync(yh, c->d_hy, bytes, cudaMemcpyDeviceToHost, c->stream), "D2H");
+    check_cuda(cudaStreamSynchronize(c->stream), "sync");
+  } catch (const Error &e) {
+    return e.status;
+  }
+  return NESA_OK;
+}
+
+int nesa_rhs_planewave(nesa_ctx *c, const double *khat, const nesa_c128 *pol, int nrhs, nesa_c128 *b) {
+  if (!c || !khat || !pol || !b || nrhs < 1 || nrhs > 4096) return NESA_ERR_INVALID_ARG;
+  try {
+    // one device buffer: polarisations first (16-byte aligned complex), then the
+    // directions and the 7 rule weights (doubles)
+    const double s15 = std::sqrt(15.0);
+    std::vector<double> buf(6 * (size_t)nrhs + 3 * (size_t)nrhs + 7);
+    std::memcpy(buf.data(), pol, sizeof(nesa_c128) * 3 * nrhs);
+    std::copy(khat, khat + 3 * nrhs, buf.begin() + 6 * nrhs);
+    double w[7] = {9.0 / 40.0, (155.0 + s15) / 1200.0, (155.0 + s15) / 1200.0, (155.0 + s15) / 1200.0,
+                   (155.0 - s15) / 1200.0, (155.0 - s15) / 1200.0, (155.0 - s15) / 1200.0};
+    std::copy(w, w + 7, buf.begin() + 9 * nrhs);
+    double *d = (double *)dalloc(c, sizeof(double) * buf.size());
+    check_cuda(cudaMemcpyAsync(d, buf.data(), sizeof(double) * buf.size(), cudaMemcpyHostToDevice, c->stream), "H2D");
+    k_rhs_planewave<<<grid_for(c->n * nrhs, 256), 256, 0, c->stream>>>(
+        (cplx *)b, c->n, nrhs, d + 6 * nrhs, (const cplx *)d, c->d_rwg_tri, c->d_rwg_free, c->d_tris, c->d_verts,
+        c->d_tri_sl, c->d_pts, d + 9 * nrhs, c->k);
+    check_cuda(cudaGetLastError(), "rhs launch");
+    check_cuda(cudaStreamSynchronize(c->stream), "rhs");
+    dfree(c, d);
+  } catch (const Error &e) {
+    return e.status;
+  }
+  return NESA_OK;
+}
+
+}  // extern "C"
