@@ -194,6 +194,33 @@ typedef struct {
 int nesa_profile_enable(nesa_ctx *ctx, int enable); /* also resets the totals */
 int nesa_profile_read(nesa_ctx *ctx, nesa_profile *out);
 
+/*
+ * nesa_matvec_noalloc - the product y = Z~ x for callers that cannot allocate device
+ * memory.  The paper has no counterpart: this is a property of the library, not of
+ * the method.
+ *
+ * nesa_matvec keeps its per-level work vectors in buffers that the context allocates
+ * (cudaMalloc) the first time a given nrhs is used.  Callers that must not allocate -
+ * code running while a stream is captured into a CUDA graph, code held to a fixed
+ * device-memory budget, real-time loops where an allocation could synchronise the
+ * device - can call this entry point instead.  It runs the same kernels with the work
+ * vectors taken from one fixed array of NESA_NOALLOC_SCRATCH_BYTES in device memory
+ * that is part of the library image (present on every GPU that loads the library,
+ * until the process exits).  It calls no allocating routine.
+ *
+ *   x_dev, y_dev, nrhs   as for nesa_matvec (caller-owned device memory)
+ * Returns NESA_ERR_INVALID_ARG (with a message in nesa_last_error) when the work
+ * vectors of this operator and nrhs need more than NESA_NOALLOC_SCRATCH_BYTES (about
+ * 22 MB per right-hand side for 30,720 unknowns, 52 MB for 122,880).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current): make that first call before any
+ * stream capture.  Call it with the context's device current.  All calls share the
+ * array, which keeps the last call's data; calls whose kernels overlap on the GPU race
+ * on it.  Asynchronous on the context's stream.
+ */
+#define NESA_NOALLOC_SCRATCH_BYTES (32u << 20)
+int nesa_matvec_noalloc(nesa_ctx *ctx, const nesa_c128 *x_dev, nesa_c128 *y_dev, int nrhs);
+
 /* Release all memory of the context (NULL is allowed). */
 void nesa_destroy(nesa_ctx *ctx);
 

@@ -680,6 +680,11 @@ const char *nesa_status_str(int s) {
 
 static thread_local std::string g_last_error;
 const char *nesa_last_error(void) { return g_last_error.c_str(); }
+}  // extern "C"
+
+void nesa::set_last_error(const std::string &what) { g_last_error = what; }
+
+extern "C" {
 
 static void free_ctx(nesa_ctx *c) {
   if (!c) return;

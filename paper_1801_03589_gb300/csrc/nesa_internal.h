@@ -15,6 +15,8 @@ struct Error {
   std::string what;
 };
 [[noreturn]] void fail(int status, const std::string &what);
+// message returned by nesa_last_error on this host thread
+void set_last_error(const std::string &what);
 
 // Everything the host computes from the mesh and the parameters (integer structure,
 // geometry of the points and of the equivalent-source spheres).  Built by
