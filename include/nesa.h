@@ -164,6 +164,38 @@ int nesa_matvec_host(nesa_ctx *ctx, const nesa_c128 *x_host, nesa_c128 *y_host, 
 int nesa_rhs_planewave(nesa_ctx *ctx, const double *khat, const nesa_c128 *pol, int nrhs, nesa_c128 *b_dev);
 
 /*
+ * Solve Z~ x = b by restarted GMRES(m) on the device (Sec. 2 names GMRES as the
+ * iterative solver; Saad & Schultz 1986).  x0 = 0; Arnoldi by classical Gram-Schmidt
+ * applied twice; Givens rotations; a right-hand side stops when its residual estimate
+ * |g_{j+1}|/||b|| <= tol; the true residual b - Z~ x is recomputed at every restart and
+ * at the end.  The nrhs right-hand sides advance in lock step (one product of nrhs
+ * columns per Arnoldi step) with separate Krylov spaces.
+ *   b_dev  dev, N x nrhs (read);  x_dev  dev, N x nrhs (written);  1 <= nrhs <= 64
+ *   opts   NULL for defaults (restart 50, max_iters 1000)
+ *   info   may be NULL; filled also when the solve does not converge
+ * Returns NESA_OK when every true relative residual is <= tol, NESA_ERR_NOT_CONVERGED
+ * when max_iters was reached first (x holds the last iterate), NESA_ERR_NUMERIC on
+ * NaN/Inf.  Synchronous (the host reads one status word per Arnoldi step).
+ * Device workspace: (restart + 3) * N * nrhs complex values, kept by the context.
+ */
+typedef struct {
+  int32_t restart;   /* Krylov dimension m of a cycle */
+  int32_t max_iters; /* total Arnoldi steps */
+  int32_t reserved[6];
+} nesa_solve_opts;
+typedef struct {
+  int32_t iterations;      /* Arnoldi steps taken */
+  int32_t restarts;        /* completed cycles before the last one */
+  int32_t converged;       /* right-hand sides whose true residual met tol */
+  int32_t matvecs;         /* products of nrhs columns */
+  double rel_residual[64]; /* final true ||b - Z~ x|| / ||b|| per right-hand side */
+  double seconds;          /* wall time of the call */
+} nesa_solve_info;
+void nesa_default_solve_opts(nesa_solve_opts *opts);
+int nesa_solve(nesa_ctx *ctx, const nesa_c128 *b_dev, nesa_c128 *x_dev, int nrhs, double tol,
+               const nesa_solve_opts *opts, nesa_solve_info *info);
+
+/*
  * Export internal arrays for tests and tools (host copies).
  *   NESA_EXPORT_POINT_LEAF  int32 [n_points][3]  integer leaf coordinates of each
  *                           quadrature point (point 7t+i = node i of triangle t)

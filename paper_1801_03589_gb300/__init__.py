@@ -64,6 +64,15 @@ class Profile(ctypes.Structure):
 
 STAGES = ("radiation", "source_transfer", "translation", "near_reception")
 
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("restart", ctypes.c_int32), ("max_iters", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("restarts", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("matvecs", ctypes.c_int32), ("rel_residual", ctypes.c_double * 64), ("seconds", ctypes.c_double)]
+
 _lib = None
 
 
@@ -91,6 +100,8 @@ def lib():
             "nesa_last_error": (ctypes.c_char_p, []),
             "nesa_profile_enable": (I, [P, I]),
             "nesa_profile_read": (I, [P, P]),
+            "nesa_default_solve_opts": (None, [P]),
+            "nesa_solve": (I, [P, P, P, I, D, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -206,6 +217,26 @@ class Nesa:
             raise ValueError("khat, pol and out disagree in nrhs")
         _check(lib().nesa_rhs_planewave(self._h, kh.ctypes.data, pl.ctypes.data, nrhs, po))
         return out
+
+    def solve(self, b, tol, x=None, restart=50, max_iters=1000, check=True):
+        """Restarted GMRES on the device for Z~ x = b (b: [nrhs, N] complex128 CUDA).
+        Returns (x, info dict).  With check=False a non-converged solve returns instead
+        of raising (info['status'] holds the library status)."""
+        import torch
+        b, pb, nrhs = _dev_ptr(b, self.n, "b")
+        if x is None:
+            x = torch.empty_like(b)
+        x, px, nr2 = _dev_ptr(x, self.n, "x")
+        o = SolveOpts()
+        lib().nesa_default_solve_opts(ctypes.byref(o))
+        o.restart, o.max_iters = int(restart), int(max_iters)
+        i = SolveInfo()
+        st = lib().nesa_solve(self._h, pb, px, nrhs, float(tol), ctypes.byref(o), ctypes.byref(i))
+        info = dict(status=st, iterations=i.iterations, restarts=i.restarts, converged=i.converged,
+                    matvecs=i.matvecs, rel_residual=list(i.rel_residual[:nrhs]), seconds=i.seconds)
+        if check and st != OK:
+            raise NesaError(st, str(info))
+        return x, info
 
     def profile_enable(self, on=True):
         _check(lib().nesa_profile_enable(self._h, 1 if on else 0))

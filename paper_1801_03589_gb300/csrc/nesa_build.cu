@@ -688,6 +688,7 @@ extern "C" {
 
 static void free_ctx(nesa_ctx *c) {
   if (!c) return;
+  nesa_free_solve_work(c);
   for (void *p : c->allocs) cudaFree(p);
   for (auto &p : c->pending) {
     cudaEventDestroy(p.a);

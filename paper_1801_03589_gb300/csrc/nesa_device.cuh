@@ -99,6 +99,7 @@ struct nesa_ctx {
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> event_pool;
   nesa_profile prof{};
+  void *solve_work = nullptr;    // GMRES workspace (nesa_solve.cu)
   std::vector<void *> allocs;    // every device allocation owned by the context
 };
 
@@ -109,4 +110,7 @@ void dfree(nesa_ctx *c, void *p);
 void check_cuda(cudaError_t e, const char *what);
 void launch_matvec(nesa_ctx *c, const cplx *x, cplx *y, int nrhs, int parts);
 int ensure_workspace(nesa_ctx *c, int nrhs);
+}  // namespace nesa
+void nesa_free_solve_work(nesa_ctx *c);
+namespace nesa {
 }  // namespace nesa

@@ -1,0 +1,439 @@
+// nesa_solve: restarted GMRES(m) on the device for Z~ x = b (paper Sec. 2 names GMRES
+// as the iterative solver; the algorithm is Saad & Schultz 1986).
+//
+// Readings: x0 = 0; Arnoldi with classical Gram-Schmidt applied twice (CGS2), which
+// keeps the basis orthogonal to working precision with two reductions per step;
+// Givens rotations on the Hessenberg column; stop when the relative residual estimate
+// |g_{j+1}| / ||b|| <= tol, and recompute the true residual b - Z~ x at every restart.
+// Right-hand sides advance in lock step (one product of nrhs columns per step) but
+// keep their own Krylov spaces; a column that has converged stops updating its
+// Hessenberg column and its step count.
+//
+// Every step of the iteration runs in kernels; the host only launches them and reads
+// back one flag per right-hand side after each Arnoldi step.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "nesa_device.cuh"
+
+namespace nesa {
+
+// Solver workspace of a context (grown on demand).
+struct SolveWork {
+  int m = 0, nrhs = 0;
+  cplx *V = nullptr;     // [m+1][nrhs][n] basis
+  cplx *w = nullptr;     // [nrhs][n]
+  cplx *r = nullptr;     // [nrhs][n]
+  cplx *H = nullptr;     // [nrhs][m+1][m] Hessenberg (column-major per rhs: H[(r*(m+1)) + i + j*(m+1)])
+  cplx *h = nullptr;     // [nrhs][m+1] projections of the current step
+  cplx *cs = nullptr;    // [nrhs][m]
+  cplx *sn = nullptr;    // [nrhs][m]
+  cplx *g = nullptr;     // [nrhs][m+1]
+  cplx *y = nullptr;     // [nrhs][m]
+  double *part = nullptr;  // partial sums [nrhs][m+1][nchunk] (complex as 2 doubles)
+  double *nrm = nullptr;   // [nrhs] norms
+  double *bnorm = nullptr; // [nrhs]
+  int *steps = nullptr;    // [nrhs] Arnoldi steps in this cycle
+  int *state = nullptr;    // [nrhs] 0 running, 1 converged, 2 breakdown (lucky), 3 numeric
+  double *est = nullptr;   // [nrhs] residual estimate
+  int *h_state = nullptr;  // pinned host mirror of state
+  double *h_est = nullptr; // pinned host mirror of est
+};
+
+static const int kChunk = 2048;  // vector elements per partial-sum block
+
+// part[(r*(jmax) + i)*nchunk + c] = sum over chunk c of conj(V_i[r]) w[r]   (i < ni)
+__global__ void k_dots(double2 *part, const cplx *V, const cplx *w, int ni, int64_t n, int nrhs, int nchunk) {
+  const int c = blockIdx.x, r = blockIdx.y;
+  const int64_t lo = (int64_t)c * kChunk, hi = min(n, lo + kChunk);
+  __shared__ double sre[32], sim[32];
+  const cplx *wr = w + (int64_t)r * n;
+  for (int i = 0; i < ni; ++i) {
+    const cplx *vi = V + ((int64_t)i * nrhs + r) * n;
+    double re = 0.0, im = 0.0;
+    for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+      cplx a = vi[e], b = wr[e];
+      re = fma(a.x, b.x, re);
+      re = fma(a.y, b.y, re);
+      im = fma(a.x, b.y, im);
+      im = fma(-a.y, b.x, im);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      re += __shfl_down_sync(0xffffffffu, re, off);
+      im += __shfl_down_sync(0xffffffffu, im, off);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+      sre[wid] = re;
+      sim[wid] = im;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double a = 0.0, b = 0.0;
+      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+        a += sre[k];
+        b += sim[k];
+      }
+      part[((int64_t)r * ni + i) * nchunk + c] = make_double2(a, b);
+    }
+    __syncthreads();
+  }
+}
+
+// h[r][i] (+)= sum_c part  (accumulate when add != 0)
+__global__ void k_dots_reduce(cplx *h, int ldh, const double2 *part, int ni, int nchunk, int add) {
+  const int i = blockIdx.x, r = blockIdx.y;
+  double re = 0.0, im = 0.0;
+  for (int c = threadIdx.x; c < nchunk; c += blockDim.x) {
+    double2 v = part[((int64_t)r * ni + i) * nchunk + c];
+    re += v.x;
+    im += v.y;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    re += __shfl_down_sync(0xffffffffu, re, off);
+    im += __shfl_down_sync(0xffffffffu, im, off);
+  }
+  if (threadIdx.x == 0) {
+    cplx &o = h[(int64_t)r * ldh + i];
+    if (add) {
+      o.x += re;
+      o.y += im;
+    } else {
+      o = make_double2(re, im);
+    }
+  }
+}
+
+// w[r] -= sum_{i<ni} V_i[r] * coef[r][i]
+__global__ void k_subtract(cplx *w, const cplx *V, const cplx *coef, int ldc, int ni, int64_t n, int nrhs) {
+  const int r = blockIdx.y;
+  const cplx *cr = coef + (int64_t)r * ldc;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    cplx acc = w[(int64_t)r * n + e];
+    for (int i = 0; i < ni; ++i) {
+      cplx v = V[((int64_t)i * nrhs + r) * n + e];
+      cplx c = cr[i];
+      acc.x -= v.x * c.x - v.y * c.y;
+      acc.y -= v.x * c.y + v.y * c.x;
+    }
+    w[(int64_t)r * n + e] = acc;
+  }
+}
+
+// x[r] += sum_{i<k_r} V_i[r] y[r][i]
+__global__ void k_update_x(cplx *x, const cplx *V, const cplx *y, int ldy, const int *steps, int64_t n, int nrhs) {
+  const int r = blockIdx.y;
+  const int k = steps[r];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    cplx acc = x[(int64_t)r * n + e];
+    for (int i = 0; i < k; ++i) cfma(acc, V[((int64_t)i * nrhs + r) * n + e], y[(int64_t)r * ldy + i]);
+    x[(int64_t)r * n + e] = acc;
+  }
+}
+
+// partial sums of |v|^2 per column
+__global__ void k_norm2(double2 *part, const cplx *v, int64_t n, int nchunk) {
+  const int c = blockIdx.x, r = blockIdx.y;
+  const int64_t lo = (int64_t)c * kChunk, hi = min(n, lo + kChunk);
+  double s = 0.0;
+  for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+    cplx a = v[(int64_t)r * n + e];
+    s = fma(a.x, a.x, s);
+    s = fma(a.y, a.y, s);
+  }
+  __shared__ double sh[32];
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += sh[k];
+    part[(int64_t)r * nchunk + c] = make_double2(t, 0.0);
+  }
+}
+
+__global__ void k_norm_reduce(double *out, const double2 *part, int nchunk) {
+  const int r = blockIdx.x;
+  double s = 0.0;
+  for (int c = threadIdx.x; c < nchunk; c += blockDim.x) s += part[(int64_t)r * nchunk + c].x;
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if (threadIdx.x == 0) out[r] = sqrt(s);
+}
+
+// dst[r] = a * src[r] / scale[r]   (scale NULL: 1)
+__global__ void k_scale(cplx *dst, const cplx *src, const double *scale, int64_t n, int nrhs) {
+  const int r = blockIdx.y;
+  const double f = scale ? (scale[r] > 0.0 ? 1.0 / scale[r] : 0.0) : 1.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    cplx a = src[(int64_t)r * n + e];
+    dst[(int64_t)r * n + e] = make_double2(a.x * f, a.y * f);
+  }
+}
+
+// r = b - r   (r holds Z~ x on entry)
+__global__ void k_residual(cplx *r, const cplx *b, int64_t total) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    cplx z = r[e], bb = b[e];
+    r[e] = make_double2(bb.x - z.x, bb.y - z.y);
+  }
+}
+
+// start of a cycle: g = (beta, 0, ...), steps = 0, state from beta
+__global__ void k_cycle_start(cplx *g, int m, const double *beta, const double *bnorm, int *steps, int *state,
+                              double *est, double tol, int nrhs) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrhs) return;
+  for (int i = 0; i <= m; ++i) g[(int64_t)r * (m + 1) + i] = make_double2(i == 0 ? beta[r] : 0.0, 0.0);
+  steps[r] = 0;
+  const double e = bnorm[r] > 0.0 ? beta[r] / bnorm[r] : 0.0;
+  est[r] = e;
+  state[r] = (e <= tol) ? 1 : (isfinite(e) ? 0 : 3);
+}
+
+// Arnoldi step j: Hessenberg column from h (projections) and hn (norm of the
+// orthogonalised vector); previous rotations, new rotation, residual estimate.
+__global__ void k_givens(cplx *H, const cplx *h, const double *hn, cplx *cs, cplx *sn, cplx *g, int *steps,
+                         int *state, double *est, const double *bnorm, int j, int m, double tol, int nrhs) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrhs || state[r] != 0) return;
+  cplx *Hr = H + (int64_t)r * (m + 1) * m;
+  cplx *col = Hr + (int64_t)j * (m + 1);
+  for (int i = 0; i <= j; ++i) col[i] = h[(int64_t)r * (m + 1) + i];
+  col[j + 1] = make_double2(hn[r], 0.0);
+  cplx *c = cs + (int64_t)r * m, *s = sn + (int64_t)r * m, *gr = g + (int64_t)r * (m + 1);
+  for (int i = 0; i < j; ++i) {
+    // [c s; -conj(s) c] with c real
+    cplx a = col[i], b = col[i + 1];
+    double ci = c[i].x;
+    cplx si = s[i];
+    col[i] = make_double2(ci * a.x + si.x * b.x - si.y * b.y, ci * a.y + si.x * b.y + si.y * b.x);
+    col[i + 1] = make_double2(-(si.x * a.x + si.y * a.y) + ci * b.x, -(si.x * a.y - si.y * a.x) + ci * b.y);
+  }
+  cplx a = col[j], b = col[j + 1];
+  double na = hypot(a.x, a.y), nb = hypot(b.x, b.y);
+  double den = hypot(na, nb);
+  double cj;
+  cplx sj;
+  if (den == 0.0 || !isfinite(den)) {
+    state[r] = 3;
+    return;
+  }
+  if (na == 0.0) {
+    cj = 0.0;
+    sj = make_double2(b.x / nb, -b.y / nb);  // conj(b)/|b|
+  } else {
+    cj = na / den;
+    // (a/|a|) conj(b) / den
+    cplx ua = make_double2(a.x / na, a.y / na);
+    sj = make_double2((ua.x * b.x + ua.y * b.y) / den, (ua.y * b.x - ua.x * b.y) / den);
+  }
+  c[j] = make_double2(cj, 0.0);
+  s[j] = sj;
+  col[j] = make_double2(cj * a.x + sj.x * b.x - sj.y * b.y, cj * a.y + sj.x * b.y + sj.y * b.x);
+  col[j + 1] = make_double2(0.0, 0.0);
+  cplx gj = gr[j];
+  gr[j + 1] = make_double2(-(sj.x * gj.x + sj.y * gj.y), -(sj.x * gj.y - sj.y * gj.x));
+  gr[j] = make_double2(cj * gj.x, cj * gj.y);
+  steps[r] = j + 1;
+  const double e = hypot(gr[j + 1].x, gr[j + 1].y) / bnorm[r];
+  est[r] = e;
+  if (!isfinite(e))
+    state[r] = 3;
+  else if (e <= tol)
+    state[r] = 1;
+  else if (hn[r] == 0.0)
+    state[r] = 2;  // the Krylov space is invariant: the solution is exact in it
+}
+
+// y = R^-1 g (upper triangular R = rotated H, size steps[r])
+__global__ void k_backsolve(cplx *y, const cplx *H, const cplx *g, const int *steps, int m, int nrhs) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrhs) return;
+  const int k = steps[r];
+  const cplx *Hr = H + (int64_t)r * (m + 1) * m;
+  const cplx *gr = g + (int64_t)r * (m + 1);
+  cplx *yr = y + (int64_t)r * m;
+  for (int i = k - 1; i >= 0; --i) {
+    cplx acc = gr[i];
+    for (int t = i + 1; t < k; ++t) {
+      cplx hv = Hr[i + (int64_t)t * (m + 1)], yv = yr[t];
+      acc.x -= hv.x * yv.x - hv.y * yv.y;
+      acc.y -= hv.x * yv.y + hv.y * yv.x;
+    }
+    cplx d = Hr[i + (int64_t)i * (m + 1)];
+    double dd = d.x * d.x + d.y * d.y;
+    yr[i] = make_double2((acc.x * d.x + acc.y * d.y) / dd, (acc.y * d.x - acc.x * d.y) / dd);
+  }
+}
+
+static inline unsigned blocks_for(int64_t n, int bs, int cap) {
+  int64_t b = (n + bs - 1) / bs;
+  return (unsigned)(b < cap ? b : cap);
+}
+
+}  // namespace nesa
+
+using namespace nesa;
+
+static SolveWork *get_work(nesa_ctx *c, int m, int nrhs) {
+  static_assert(sizeof(SolveWork) > 0, "");
+  if (!c->solve_work) c->solve_work = new SolveWork();
+  SolveWork *W = (SolveWork *)c->solve_work;
+  if (W->m >= m && W->nrhs >= nrhs) return W;
+  void *old[] = {W->V, W->w, W->r, W->H, W->h, W->cs, W->sn, W->g, W->y, W->part, W->nrm, W->bnorm, W->steps,
+                 W->state, W->est};
+  for (void *p : old) dfree(c, p);
+  if (W->h_state) cudaFreeHost(W->h_state);
+  if (W->h_est) cudaFreeHost(W->h_est);
+  *W = SolveWork();
+  const int64_t n = c->n;
+  const int nchunk = (int)((n + kChunk - 1) / kChunk);
+  W->m = m;
+  W->nrhs = nrhs;
+  W->V = (cplx *)dalloc(c, sizeof(cplx) * (size_t)(m + 1) * nrhs * n);
+  W->w = (cplx *)dalloc(c, sizeof(cplx) * (size_t)nrhs * n);
+  W->r = (cplx *)dalloc(c, sizeof(cplx) * (size_t)nrhs * n);
+  W->H = (cplx *)dalloc(c, sizeof(cplx) * (size_t)nrhs * (m + 1) * m);
+  W->h = (cplx *)dalloc(c, sizeof(cplx) * (size_t)nrhs * (m + 1));
+  W->cs = (cplx *)dalloc(c, sizeof(cplx) * (size_t)nrhs * m);
+  W->sn = (cplx *)dalloc(c, sizeof(cplx) * (size_t)nrhs * m);
+  W->g = (cplx *)dalloc(c, sizeof(cplx) * (size_t)nrhs * (m + 1));
+  W->y = (cplx *)dalloc(c, sizeof(cplx) * (size_t)nrhs * m);
+  W->part = (double *)dalloc(c, sizeof(double2) * (size_t)nrhs * (m + 1) * nchunk);
+  W->nrm = (double *)dalloc(c, sizeof(double) * nrhs);
+  W->bnorm = (double *)dalloc(c, sizeof(double) * nrhs);
+  W->steps = (int *)dalloc(c, sizeof(int) * nrhs);
+  W->state = (int *)dalloc(c, sizeof(int) * nrhs);
+  W->est = (double *)dalloc(c, sizeof(double) * nrhs);
+  check_cuda(cudaMallocHost(&W->h_state, sizeof(int) * nrhs), "pinned");
+  check_cuda(cudaMallocHost(&W->h_est, sizeof(double) * nrhs), "pinned");
+  return W;
+}
+
+void nesa_free_solve_work(nesa_ctx *c) {
+  SolveWork *W = (SolveWork *)c->solve_work;
+  if (!W) return;
+  if (W->h_state) cudaFreeHost(W->h_state);
+  if (W->h_est) cudaFreeHost(W->h_est);
+  delete W;
+  c->solve_work = nullptr;
+}
+
+extern "C" {
+
+void nesa_default_solve_opts(nesa_solve_opts *o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->restart = 50;
+  o->max_iters = 1000;
+}
+
+int nesa_solve(nesa_ctx *c, const nesa_c128 *b_dev, nesa_c128 *x_dev, int nrhs, double tol,
+               const nesa_solve_opts *opts, nesa_solve_info *info) {
+  if (!c || !b_dev || !x_dev || nrhs < 1 || nrhs > 64 || !(tol > 0.0)) return NESA_ERR_INVALID_ARG;
+  nesa_solve_opts o;
+  nesa_default_solve_opts(&o);
+  if (opts) o = *opts;
+  if (o.restart < 1 || o.restart > 1000 || o.max_iters < 1) return NESA_ERR_INVALID_ARG;
+  auto t0 = std::chrono::steady_clock::now();
+  nesa_solve_info I;
+  std::memset(&I, 0, sizeof(I));
+  int status = NESA_OK;
+  try {
+    const int m = o.restart;
+    SolveWork *W = get_work(c, m, nrhs);
+    ensure_workspace(c, nrhs);
+    cudaStream_t st = c->stream;
+    const int64_t n = c->n;
+    const int nchunk = (int)((n + kChunk - 1) / kChunk);
+    const cplx *b = (const cplx *)b_dev;
+    cplx *x = (cplx *)x_dev;
+    const dim3 vgrid(blocks_for(n, 256, 4096), nrhs);
+    auto norms = [&](const cplx *v, double *out) {
+      k_norm2<<<dim3(nchunk, nrhs), 256, 0, st>>>((double2 *)W->part, v, n, nchunk);
+      k_norm_reduce<<<nrhs, 32, 0, st>>>(out, (const double2 *)W->part, nchunk);
+    };
+    norms(b, W->bnorm);
+    check_cuda(cudaMemsetAsync(x, 0, sizeof(cplx) * (size_t)nrhs * n, st), "x0");
+    check_cuda(cudaMemcpyAsync(W->r, b, sizeof(cplx) * (size_t)nrhs * n, cudaMemcpyDeviceToDevice, st), "r0");
+    int total = 0;
+    while (true) {
+      // r holds the residual; start a cycle
+      norms(W->r, W->nrm);
+      k_cycle_start<<<(nrhs + 63) / 64, 64, 0, st>>>(W->g, m, W->nrm, W->bnorm, W->steps, W->state, W->est, tol,
+                                                     nrhs);
+      k_scale<<<vgrid, 256, 0, st>>>(W->V, W->r, W->nrm, n, nrhs);
+      check_cuda(cudaMemcpyAsync(W->h_state, W->state, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st), "state");
+      check_cuda(cudaMemcpyAsync(W->h_est, W->est, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st), "est");
+      check_cuda(cudaStreamSynchronize(st), "cycle start");
+      bool running = false;
+      for (int r = 0; r < nrhs; ++r) running |= W->h_state[r] == 0;
+      for (int r = 0; r < nrhs; ++r)
+        if (W->h_state[r] == 3) status = NESA_ERR_NUMERIC;
+      if (!running || status != NESA_OK || total >= o.max_iters) break;
+      I.restarts += total > 0;
+      int j = 0;
+      for (; j < m && total < o.max_iters; ++j) {
+        cplx *Vj = W->V + (size_t)j * nrhs * n;
+        cplx *Vn = W->V + (size_t)(j + 1) * nrhs * n;
+        launch_matvec(c, Vj, W->w, nrhs, NESA_PART_ALL);
+        I.matvecs += 1;
+        // CGS2: two rounds of projection onto V_0..V_j
+        for (int pass = 0; pass < 2; ++pass) {
+          k_dots<<<dim3(nchunk, nrhs), 256, 0, st>>>((double2 *)W->part, W->V, W->w, j + 1, n, nrhs, nchunk);
+          k_dots_reduce<<<dim3(j + 1, nrhs), 32, 0, st>>>(W->h + 0, m + 1, (const double2 *)W->part, j + 1, nchunk,
+                                                           pass);
+          // subtract with this pass's coefficients: use y as scratch for them
+          k_dots_reduce<<<dim3(j + 1, nrhs), 32, 0, st>>>(W->y, m, (const double2 *)W->part, j + 1, nchunk, 0);
+          k_subtract<<<vgrid, 256, 0, st>>>(W->w, W->V, W->y, m, j + 1, n, nrhs);
+        }
+        norms(W->w, W->nrm);
+        k_givens<<<(nrhs + 63) / 64, 64, 0, st>>>(W->H, W->h, W->nrm, W->cs, W->sn, W->g, W->steps, W->state, W->est,
+                                                  W->bnorm, j, m, tol, nrhs);
+        k_scale<<<vgrid, 256, 0, st>>>(Vn, W->w, W->nrm, n, nrhs);
+        ++total;
+        check_cuda(cudaMemcpyAsync(W->h_state, W->state, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st), "state");
+        check_cuda(cudaStreamSynchronize(st), "arnoldi step");
+        bool any = false;
+        for (int r = 0; r < nrhs; ++r) any |= W->h_state[r] == 0;
+        if (!any) break;
+      }
+      // x += V y for the steps each column took in this cycle
+      k_backsolve<<<(nrhs + 63) / 64, 64, 0, st>>>(W->y, W->H, W->g, W->steps, m, nrhs);
+      k_update_x<<<vgrid, 256, 0, st>>>(x, W->V, W->y, m, W->steps, n, nrhs);
+      // true residual
+      launch_matvec(c, x, W->r, nrhs, NESA_PART_ALL);
+      I.matvecs += 1;
+      k_residual<<<blocks_for((int64_t)nrhs * n, 256, 4096), 256, 0, st>>>(W->r, b, (int64_t)nrhs * n);
+      check_cuda(cudaGetLastError(), "gmres launch");
+      if (total >= o.max_iters) {
+        norms(W->r, W->nrm);
+        break;
+      }
+    }
+    // final true residuals
+    norms(W->r, W->nrm);
+    std::vector<double> rn(nrhs), bn(nrhs);
+    check_cuda(cudaMemcpyAsync(rn.data(), W->nrm, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st), "res");
+    check_cuda(cudaMemcpyAsync(bn.data(), W->bnorm, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st), "bn");
+    check_cuda(cudaStreamSynchronize(st), "solve");
+    I.iterations = total;
+    for (int r = 0; r < nrhs; ++r) {
+      double rr = bn[r] > 0.0 ? rn[r] / bn[r] : 0.0;
+      I.rel_residual[r] = rr;
+      if (!std::isfinite(rr)) status = NESA_ERR_NUMERIC;
+      // the true residual decides convergence (the estimate can be slightly optimistic)
+      if (rr <= tol * (1.0 + 1e-6)) I.converged += 1;
+    }
+    if (status == NESA_OK && I.converged < nrhs) status = NESA_ERR_NOT_CONVERGED;
+  } catch (const Error &e) {
+    status = e.status;
+    set_last_error(e.what);
+  }
+  I.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (info) *info = I;
+  return status;
+}
+
+}  // extern "C"
