@@ -2,9 +2,14 @@
 
 Workload: PEC sphere of radius 3 wavelengths, icosphere subdivision 6 (81,920
 triangles, 122,880 RWG unknowns), octree of 6 levels with 0.25-wavelength leaves,
-one right-hand side, FP64 throughout.  One step = one full operator application
-(near field + radiation, source transfer, translation, potential transfer, reception)
-through the library's C ABI.
+one right-hand side.  One step = one full operator application (near field +
+radiation, source transfer, translation, potential transfer, reception) through the
+library's C ABI.
+
+``value`` is the rate of the mixed-precision product (the low-precision operator
+copy; its error against the FP64 product is measured and reported); the plain FP64
+product is timed beside it (``fp64``), and one GMRES solve to 1e-5 with FP64
+iterative refinement around the mixed product is timed (``solve``).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -37,10 +42,11 @@ from workloads import get_config, random_coefficients  # noqa: E402
 CONFIG = "C2"
 METRIC = "nesa_matvec_per_s"
 UNIT = "matvec/s"
-# FP64 peak of one GB300: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2070 MHz
+# GB300: 152 SMs at 2070 MHz; per SM and clock 2 FP64 FMA and 128 FP32 FMA
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 SPEC = ("PEC sphere r=3 wavelengths, icosphere subdiv 6 (81,920 triangles, 122,880 RWG), "
-        "6-level octree, leaf 0.25 wavelength, 1 RHS, FP64")
+        "6-level octree, leaf 0.25 wavelength, 1 RHS")
 
 
 def _peaks():
@@ -126,7 +132,6 @@ def oracle_sampled_product(o, x, n_leaves=12, n_boxes=12, n_rows=48, seed=0):
     rng = np.random.default_rng(seed)
     t = o.tree
     L, l0 = o.L, o.l0
-    total = 0.0
     parts = {}
 
     def pick(seq, k):
@@ -219,6 +224,36 @@ def run_reference(args, world, rank):
     return 0
 
 
+def _time_products(g, x, y, parts, steps, warmup, stream, barrier):
+    import torch
+    with torch.cuda.stream(stream):
+        for _ in range(max(3, warmup)):
+            g.matvec(x, y, parts=parts)
+    stream.synchronize()
+    g.profile_enable(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for _ in range(steps):
+            g.matvec(x, y, parts=parts)
+        ev1.record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    prof = g.profile_read()
+    g.profile_enable(False)
+    return ev0.elapsed_time(ev1) / steps, prof
+
+
+def _stages(prof, steps):
+    return {k: {"launches": v["launches"], "ms_per_step": v["ms"] / steps,
+                "tflops": (v["flops"] / (v["ms"] * 1e-3) / 1e12) if v["ms"] > 0 else None,
+                "gbs": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
+            for k, v in prof.items()}
+
+
 def run_ours(args, world, rank, local):
     import torch
 
@@ -231,7 +266,8 @@ def run_ours(args, world, rank, local):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
         pg = dist
     cfg = get_config(CONFIG)
-    g = nesa.Nesa(cfg["vertices"], cfg["triangles"], cfg["k"], leaf_size=cfg["leaf_size"], n_levels=cfg["n_levels"])
+    g = nesa.Nesa(cfg["vertices"], cfg["triangles"], cfg["k"], leaf_size=cfg["leaf_size"], n_levels=cfg["n_levels"],
+                  precision=nesa.MIXED)
     info = g.info()
     stream = torch.cuda.Stream()
     g.set_stream(stream)
@@ -245,64 +281,59 @@ def run_ours(args, world, rank, local):
         if pg is not None:
             pg.barrier()
 
-    with torch.cuda.stream(stream):
-        for _ in range(max(3, args.warmup)):
-            g.matvec(x, y)
-    stream.synchronize()
-    g.profile_enable(True)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    def max_over_ranks(v):
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        if pg is not None:
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        return float(t.item())
+
+    mixed = nesa.PART_ALL | nesa.PART_MIXED
     with ClockSampler(local) as clk:
-        barrier()
-        torch.cuda.synchronize()
-        with torch.cuda.stream(stream):
-            ev0.record(stream)
-            for _ in range(args.steps):
-                g.matvec(x, y)
-            ev1.record(stream)
-        stream.synchronize()
-        torch.cuda.synchronize()
-        barrier()
-    prof = g.profile_read()
-    g.profile_enable(False)
-    ms = ev0.elapsed_time(ev1) / args.steps
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if pg is not None:
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * nrhs * 1e3 / ms_max
+        ms64, prof64 = _time_products(g, x, y, nesa.PART_ALL, args.steps, args.warmup, stream, barrier)
+        ms_mx, prof_mx = _time_products(g, x, y, mixed, args.steps, args.warmup, stream, barrier)
+    ms64, ms_mx = max_over_ranks(ms64), max_over_ranks(ms_mx)
+    value = world * nrhs * 1e3 / ms_mx
+    # accuracy of the mixed product against the FP64 product on this input
+    y64 = g.matvec(x)
+    ymx = g.matvec(x, parts=mixed)
+    mixed_err = float((ymx - y64).abs().pow(2).sum().sqrt() / y64.abs().pow(2).sum().sqrt())
 
     # end to end through the host-pointer entry point: H2D of x, product, D2H of y
     xh = torch.from_numpy(random_coefficients(n, nrhs, seed=7 + rank)).pin_memory()
     yh = torch.empty_like(xh).pin_memory()
-    for _ in range(2):
-        g.matvec_host_ptr(xh.data_ptr(), yh.data_ptr(), nrhs)
+    for _ in range(3):
+        g.matvec_host_ptr(xh.data_ptr(), yh.data_ptr(), nrhs, mixed)
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        g.matvec_host_ptr(xh.data_ptr(), yh.data_ptr(), nrhs)
-    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
-    t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
-    if pg is not None:
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-    e2e_ms = float(t.item())
+        g.matvec_host_ptr(xh.data_ptr(), yh.data_ptr(), nrhs, mixed)
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps)
+
+    # one solve to 1e-5: FP64 refinement around GMRES on the mixed product
+    solve = None
+    if not args.no_solve:
+        b = g.rhs_planewave([[0.0, 0.0, 1.0]], [[1.0, 0.0, 0.0]])
+        torch.cuda.synchronize()
+        barrier()
+        xs, si = g.solve(b, tol=1e-5, mixed=True, restart=100, max_iters=4000, inner_tol=1e-2, check=False)
+        solve = {"tol": 1e-5, "seconds": max_over_ranks(si["seconds"]), "status": si["status"],
+                 "iterations": si["iterations"], "refinements": si["refinements"],
+                 "fp64_products": si["fp64_matvecs"], "true_rel_residual": si["rel_residual"][0],
+                 "method": "FP64 iterative refinement, inner GMRES(100) on the mixed product to 1e-2, "
+                           "x-polarised plane wave along +z"}
 
     if rank != 0:
         if pg is not None:
             pg.destroy_process_group()
         return 0
 
-    # roofline of the dominant stage (largest device time)
-    dom = max(prof, key=lambda k: prof[k]["ms"])
-    d = prof[dom]
+    # roofline of the dominant stage of the mixed product (largest device time)
+    dom = max(prof_mx, key=lambda k: prof_mx[k]["ms"])
+    d = prof_mx[dom]
     achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
-    stages = {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps,
-                  "tflops": (v["flops"] / (v["ms"] * 1e-3) / 1e12) if v["ms"] > 0 else None,
-                  "gbs": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else None}
-              for k, v in prof.items()}
-    launches = sum(v["launches"] for v in prof.values())
+    launches = sum(v["launches"] for v in prof_mx.values())
     peaks = _peaks()
 
-    # CPU oracle on the host cores, on a bounded stage-wise sample
     cpu = None
     if not args.no_cpu_baseline:
         o = build_oracle(cfg)
@@ -311,27 +342,41 @@ def run_ours(args, world, rank, local):
         cpu = {"value": 1.0 / sec, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
                "seconds_per_matvec": sec, "stage_seconds": parts}
 
+    kernel = {"translation": "k_translate<float2>", "near_reception": "k_near_receive<float2>",
+              "radiation": "k_radiate<float2>", "source_transfer": "k_upward<float2>"}[dom]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": max(3, args.warmup), "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "warmup": max(3, args.warmup), "ms_per_step": ms_mx, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "%s: %s" % (CONFIG, SPEC), "nrhs": nrhs, "n_unknowns": n,
+                   "product": "mixed precision (complex64 operator copy, FP32 arithmetic), rel err vs FP64 %.1e"
+                              % mixed_err,
                    "levels": info["n_levels"], "l0": info["l0"], "q": info["q"][info["l0"]:],
                    "near_nnz": info["near_nnz"], "device_gb": info["device_bytes"] / 1e9,
                    "build_s": info["build_seconds"],
-                   "l2": "operator data %.1f GB per product > 129 MB L2 (no flush needed)" % (
-                       sum(v["bytes"] for v in prof.values()) / args.steps / 1e9),
+                   "l2": "operator data %.1f GB (FP64) / %.1f GB (mixed) per product > 129 MB L2, no flush needed" % (
+                       sum(v["bytes"] for v in prof64.values()) / args.steps / 1e9,
+                       sum(v["bytes"] for v in prof_mx.values()) / args.steps / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "clocks": clk.summary(),
         "e2e": {"value": world * nrhs * 1e3 / e2e_ms, "unit": UNIT, "h2d_bytes_per_step": 16 * n * nrhs,
                 "d2h_bytes_per_step": 16 * n * nrhs, "ms_per_step": e2e_ms},
         "gpu_launches": launches,
-        "roofline": {"kernel": "k_translate" if dom == "translation" else dom, "stage": dom, "bound": "alu",
-                     "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                     "peak_note": "FP64: 152 SMs x 4 flop/clk x 2070 MHz (derived; no measured FP64 peak in "
-                                  "MEASURED_PEAKS.json, hbm %s GB/s)" % peaks.get("hbm_gbs")},
-        "stages": stages,
+        "roofline": {"kernel": kernel, "stage": dom, "bound": "alu", "achieved": achieved,
+                     "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                     "traffic": None,
+                     "peak_note": "FP32: 152 SMs x 256 flop/clk x 2070 MHz (derived; MEASURED_PEAKS.json has "
+                                  "HBM %s GB/s and BF16 only)" % peaks.get("hbm_gbs")},
+        "stages": _stages(prof_mx, args.steps),
+        "fp64": {"value": world * nrhs * 1e3 / ms64, "unit": UNIT, "ms_per_step": ms64, "dtype": "f64",
+                 "stages": _stages(prof64, args.steps),
+                 "roofline": {"kernel": "k_translate<double2>", "bound": "alu",
+                              "achieved": prof64["translation"]["flops"] / (prof64["translation"]["ms"] * 1e-3) / 1e12,
+                              "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                              "frac": prof64["translation"]["flops"] / (prof64["translation"]["ms"] * 1e-3) / 1e12
+                              / FP64_PEAK_TFLOPS}},
+        "mixed_vs_fp64": ms64 / ms_mx,
+        "solve": solve,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line))
@@ -347,6 +392,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-solve", action="store_true")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":

@@ -48,8 +48,9 @@ extern "C" {
 #define NESA_ERR_TIMEOUT (-6)       /* a bounded device wait ran out */
 #define NESA_ERR_NUMERIC (-7)       /* NaN/Inf met, or a breakdown */
 
-/* precision of the far-field stages (nesa_params.precision) */
-#define NESA_FP64 0
+/* precision of the operator copies built (nesa_params.precision) */
+#define NESA_FP64 0  /* FP64 operator only */
+#define NESA_MIXED 1 /* FP64 operator plus a low-precision copy (see NESA_PART_MIXED) */
 
 /* rule for the number of equivalent sources per level (nesa_params.q_mode) */
 #define NESA_Q_FIXED 0 /* Q = q_fixed in every group (the paper's choice, Sec. 3) */
@@ -59,6 +60,13 @@ extern "C" {
 #define NESA_PART_NEAR 1 /* near field, Eq. 9 */
 #define NESA_PART_FAR 2  /* far field, Eqs. 10-14 */
 #define NESA_PART_ALL 3
+/* Or-ed into the parts: apply the low-precision copy (context built with NESA_MIXED):
+   near field, radiation, transfers and reception in complex64 (FP32 arithmetic),
+   translations as selected by nesa_params.translate (x and y stay complex128). */
+#define NESA_PART_MIXED 4
+
+/* translation engine of the mixed product (nesa_params.translate) */
+#define NESA_TRANSLATE_FP32 0 /* complex64 on the CUDA cores */
 
 typedef struct nesa_ctx nesa_ctx; /* opaque; owns all device memory of one operator */
 
@@ -85,7 +93,8 @@ typedef struct {
  *   rho_test    radius of the test sphere / box circumradius
  *   pinv_eps    Tikhonov parameter of the equivalent-source fit, relative to the
  *               Frobenius norm of the fitted matrix
- *   precision   NESA_FP64
+ *   precision   NESA_FP64 or NESA_MIXED
+ *   translate   NESA_TRANSLATE_* engine of the mixed product's translations
  */
 typedef struct {
   double leaf_size;
@@ -97,6 +106,8 @@ typedef struct {
   double rho_eq;
   double rho_test;
   double pinv_eps;
+  int32_t translate;
+  int32_t reserved[3];
 } nesa_params;
 
 /* Sizes of a built operator (host struct filled by nesa_get_info). */
@@ -151,10 +162,11 @@ int nesa_matvec_parts(nesa_ctx *ctx, const nesa_c128 *x_dev, nesa_c128 *y_dev, i
 
 /*
  * End-to-end product from host memory: copies x (host, N x nrhs) to the device,
- * applies nesa_matvec and copies y back to host memory.  Synchronous.  Uses device
- * buffers held by the context (grown on demand).
+ * applies nesa_matvec_parts(parts) and copies y back to host memory.  Synchronous.
+ * Uses device buffers held by the context (grown on demand).  Pinned host memory
+ * gives the fastest copies.
  */
-int nesa_matvec_host(nesa_ctx *ctx, const nesa_c128 *x_host, nesa_c128 *y_host, int nrhs);
+int nesa_matvec_host(nesa_ctx *ctx, const nesa_c128 *x_host, nesa_c128 *y_host, int nrhs, int parts);
 
 /*
  * Plane-wave excitation b_m = -int E^i . phi_m with E^i = pol_r exp(-i k khat_r . r)
@@ -179,16 +191,24 @@ int nesa_rhs_planewave(nesa_ctx *ctx, const double *khat, const nesa_c128 *pol, 
  * Device workspace: (restart + 3) * N * nrhs complex values, kept by the context.
  */
 typedef struct {
-  int32_t restart;   /* Krylov dimension m of a cycle */
-  int32_t max_iters; /* total Arnoldi steps */
-  int32_t reserved[6];
+  int32_t restart;    /* Krylov dimension m of a cycle */
+  int32_t max_iters;  /* total Arnoldi steps (over all inner solves when mixed) */
+  int32_t mixed;      /* 1: FP64 iterative refinement - r = b - Z~ x with the FP64 product,
+                         an inner GMRES on the NESA_PART_MIXED product solves for the
+                         correction to inner_tol, x += d - until ||r||/||b|| <= tol
+                         (context built with NESA_MIXED); Arnoldi and Givens stay FP64 */
+  int32_t max_refine; /* refinement steps (default 10) */
+  double inner_tol;   /* relative tolerance of each inner solve (default 1e-3) */
+  int32_t reserved[4];
 } nesa_solve_opts;
 typedef struct {
   int32_t iterations;      /* Arnoldi steps taken */
   int32_t restarts;        /* completed cycles before the last one */
   int32_t converged;       /* right-hand sides whose true residual met tol */
-  int32_t matvecs;         /* products of nrhs columns */
-  double rel_residual[64]; /* final true ||b - Z~ x|| / ||b|| per right-hand side */
+  int32_t matvecs;         /* products of nrhs columns (all precisions) */
+  int32_t refinements;     /* refinement steps (mixed) */
+  int32_t fp64_matvecs;    /* FP64 products among them */
+  double rel_residual[64]; /* final true FP64 ||b - Z~ x|| / ||b|| per right-hand side */
   double seconds;          /* wall time of the call */
 } nesa_solve_info;
 void nesa_default_solve_opts(nesa_solve_opts *opts);

@@ -16,9 +16,10 @@ LIB_PATH = os.path.join(HERE, "libnesa.so")
 
 OK = 0
 ERR_INVALID_ARG, ERR_MESH, ERR_CUDA, ERR_OOM, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_NUMERIC = -1, -2, -3, -4, -5, -6, -7
-FP64 = 0
+FP64, MIXED = 0, 1
 Q_FIXED, Q_AUTO = 0, 1
-PART_NEAR, PART_FAR, PART_ALL = 1, 2, 3
+PART_NEAR, PART_FAR, PART_ALL, PART_MIXED = 1, 2, 3, 4
+TRANSLATE_FP32, TRANSLATE_TENSOR = 0, 1
 EXPORT_POINT_LEAF, EXPORT_RWG = 1, 2
 MAX_LEVELS = 20
 
@@ -37,7 +38,8 @@ class Mesh(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("leaf_size", ctypes.c_double), ("n_levels", ctypes.c_int32), ("q_mode", ctypes.c_int32),
                 ("q_fixed", ctypes.c_int32), ("precision", ctypes.c_int32), ("q_digits", ctypes.c_double),
-                ("rho_eq", ctypes.c_double), ("rho_test", ctypes.c_double), ("pinv_eps", ctypes.c_double)]
+                ("rho_eq", ctypes.c_double), ("rho_test", ctypes.c_double), ("pinv_eps", ctypes.c_double),
+                ("translate", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class Info(ctypes.Structure):
@@ -66,12 +68,14 @@ STAGES = ("radiation", "source_transfer", "translation", "near_reception")
 
 
 class SolveOpts(ctypes.Structure):
-    _fields_ = [("restart", ctypes.c_int32), ("max_iters", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+    _fields_ = [("restart", ctypes.c_int32), ("max_iters", ctypes.c_int32), ("mixed", ctypes.c_int32),
+                ("max_refine", ctypes.c_int32), ("inner_tol", ctypes.c_double), ("reserved", ctypes.c_int32 * 4)]
 
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("restarts", ctypes.c_int32), ("converged", ctypes.c_int32),
-                ("matvecs", ctypes.c_int32), ("rel_residual", ctypes.c_double * 64), ("seconds", ctypes.c_double)]
+                ("matvecs", ctypes.c_int32), ("refinements", ctypes.c_int32), ("fp64_matvecs", ctypes.c_int32),
+                ("rel_residual", ctypes.c_double * 64), ("seconds", ctypes.c_double)]
 
 _lib = None
 
@@ -92,7 +96,7 @@ def lib():
             "nesa_get_info": (I, [P, P]),
             "nesa_matvec": (I, [P, P, P, I]),
             "nesa_matvec_parts": (I, [P, P, P, I, I]),
-            "nesa_matvec_host": (I, [P, P, P, I]),
+            "nesa_matvec_host": (I, [P, P, P, I, I]),
             "nesa_rhs_planewave": (I, [P, P, P, I, P]),
             "nesa_export": (I, [P, I, P, ctypes.c_size_t]),
             "nesa_destroy": (None, [P]),
@@ -194,16 +198,16 @@ class Nesa:
         _check(lib().nesa_matvec_parts(self._h, px, py, nrhs, parts))
         return y
 
-    def matvec_host(self, x):
+    def matvec_host(self, x, parts=PART_ALL):
         """End to end from host memory: x numpy or CPU tensor [nrhs, N] complex128."""
         xa = np.ascontiguousarray(np.atleast_2d(np.asarray(x)), dtype=np.complex128)
         y = np.empty_like(xa)
-        _check(lib().nesa_matvec_host(self._h, xa.ctypes.data, y.ctypes.data, xa.shape[0]))
+        _check(lib().nesa_matvec_host(self._h, xa.ctypes.data, y.ctypes.data, xa.shape[0], parts))
         return y
 
-    def matvec_host_ptr(self, x_ptr, y_ptr, nrhs):
+    def matvec_host_ptr(self, x_ptr, y_ptr, nrhs, parts=PART_ALL):
         """End to end product between two host buffers given by address (e.g. pinned tensors)."""
-        _check(lib().nesa_matvec_host(self._h, ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr), int(nrhs)))
+        _check(lib().nesa_matvec_host(self._h, ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr), int(nrhs), parts))
 
     def rhs_planewave(self, khat, pol, out=None):
         import torch
@@ -218,8 +222,10 @@ class Nesa:
         _check(lib().nesa_rhs_planewave(self._h, kh.ctypes.data, pl.ctypes.data, nrhs, po))
         return out
 
-    def solve(self, b, tol, x=None, restart=50, max_iters=1000, check=True):
+    def solve(self, b, tol, x=None, restart=50, max_iters=1000, check=True, mixed=False, max_refine=10,
+              inner_tol=1e-3):
         """Restarted GMRES on the device for Z~ x = b (b: [nrhs, N] complex128 CUDA).
+        mixed=True: FP64 iterative refinement around GMRES on the low-precision product.
         Returns (x, info dict).  With check=False a non-converged solve returns instead
         of raising (info['status'] holds the library status)."""
         import torch
@@ -230,10 +236,12 @@ class Nesa:
         o = SolveOpts()
         lib().nesa_default_solve_opts(ctypes.byref(o))
         o.restart, o.max_iters = int(restart), int(max_iters)
+        o.mixed, o.max_refine, o.inner_tol = int(bool(mixed)), int(max_refine), float(inner_tol)
         i = SolveInfo()
         st = lib().nesa_solve(self._h, pb, px, nrhs, float(tol), ctypes.byref(o), ctypes.byref(i))
         info = dict(status=st, iterations=i.iterations, restarts=i.restarts, converged=i.converged,
-                    matvecs=i.matvecs, rel_residual=list(i.rel_residual[:nrhs]), seconds=i.seconds)
+                    matvecs=i.matvecs, refinements=i.refinements, fp64_matvecs=i.fp64_matvecs,
+                    rel_residual=list(i.rel_residual[:nrhs]), seconds=i.seconds)
         if check and st != OK:
             raise NesaError(st, str(info))
         return x, info

@@ -705,7 +705,8 @@ int nesa_build(const nesa_mesh *mesh, double k, const nesa_params *params, nesa_
     return NESA_ERR_INVALID_ARG;
   if (!(k > 0.0) || !(params->leaf_size > 0.0) || params->n_levels < 1 || params->n_levels > NESA_MAX_LEVELS ||
       (params->q_mode != NESA_Q_FIXED && params->q_mode != NESA_Q_AUTO) || params->q_fixed < 1 ||
-      params->precision != NESA_FP64 || !(params->rho_eq > 0.0) || !(params->rho_test > params->rho_eq) ||
+      (params->precision != NESA_FP64 && params->precision != NESA_MIXED) || params->translate < 0 ||
+      params->translate > 1 || !(params->rho_eq > 0.0) || !(params->rho_test > params->rho_eq) ||
       !(params->pinv_eps >= 0.0) || mesh->n_triangles > (1LL << 28))
     return NESA_ERR_INVALID_ARG;
   auto t0 = std::chrono::steady_clock::now();
@@ -751,6 +752,15 @@ int nesa_build(const nesa_mesh *mesh, double k, const nesa_params *params, nesa_
     I.near_nnz = nnz;
   }
   I.v_columns = (int64_t)c->h.vc_rwg.size();
+  if (params->precision == NESA_MIXED) {
+    try {
+      build_mixed(c);
+    } catch (const Error &e) {
+      g_last_error = e.what;
+      free_ctx(c);
+      return e.status;
+    }
+  }
   I.device_bytes = (int64_t)c->device_bytes;
   I.build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   *out = c;

@@ -38,8 +38,19 @@ __device__ __forceinline__ double dist3(double ax, double ay, double az, double 
   return sqrt(dx * dx + dy * dy + dz * dz);
 }
 
+typedef float2 cplxf;  // complex64 (mixed-precision operator)
+
+__device__ __forceinline__ void cfma(cplxf &acc, cplxf a, cplxf b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(-a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(a.y, b.x, acc.y);
+}
+
 // Per-level device arrays of the far-field structure.
 struct DevLevel {
+  // complex64 copies for the mixed-precision product (NESA_MIXED)
+  cplxf *D32 = nullptr, *C32 = nullptr, *Ct32 = nullptr, *s32 = nullptr, *o32 = nullptr;
   int q = 0;           // Q_l
   int64_t nbox = 0;
   int64_t nil = 0;     // interaction pairs
@@ -81,6 +92,11 @@ struct nesa_ctx {
   int64_t *d_nz_ptr = nullptr;
   int32_t *d_nz_col = nullptr;
   nesa::cplx *d_nz_val = nullptr;
+  // complex64 copies (NESA_MIXED)
+  bool mixed = false;
+  nesa::cplxf *d_nz_val32 = nullptr;
+  nesa::cplxf *d_V32 = nullptr;
+  int nrhs_cap32 = 0;
   // levels
   nesa::DevLevel lev[NESA_MAX_LEVELS];
   int nrhs_cap = 0;              // capacity of the s/o workspaces
@@ -109,6 +125,8 @@ void *dalloc(nesa_ctx *c, size_t bytes);
 void dfree(nesa_ctx *c, void *p);
 void check_cuda(cudaError_t e, const char *what);
 void launch_matvec(nesa_ctx *c, const cplx *x, cplx *y, int nrhs, int parts);
+// converted copies of the operator for the mixed-precision product
+void build_mixed(nesa_ctx *c);
 int ensure_workspace(nesa_ctx *c, int nrhs);
 }  // namespace nesa
 void nesa_free_solve_work(nesa_ctx *c);

@@ -1,16 +1,17 @@
-// The NESA matrix-vector product y = Z~ x on the device (FP64).
+// The NESA matrix-vector product y = Z~ x on the device.
 //
 // Stages (paper Sec. 3), one kernel launch each (per level where the stage is per level):
-//   k_radiate     s_beta = V_beta x_beta                      (Eq. 10)
-//   k_upward      s_P   += C_l(octant) s_child, l = L..l0+1    (Eq. 11)
-//   k_translate   o_a    = C_l(octant)^T o_P(a) + sum_{b in IL(a)} D_l(a - b) s_b
-//                                                             (Eq. 13 and Eq. 12, l = l0..L)
-//   k_near_receive y_m   = sum_n Z^near_mn x_n                 (Eq. 9)
-//                        + (-i eta k) sum_ch gamma_ch V^T o    (Eq. 14; U = V^T)
+//   k_radiate      s_beta = V_beta x_beta                      (Eq. 10)
+//   k_upward       s_P    = sum_children C_l(octant) s_child   (Eq. 11, l = L..l0+1)
+//   k_translate    o_a    = C_l(octant)^T o_P(a) + sum_{b in IL(a)} D_l(a - b) s_b
+//                                                              (Eq. 13 and Eq. 12, l = l0..L)
+//   k_near_receive y_m    = sum_n Z^near_mn x_n                (Eq. 9)
+//                         + (-i eta k) sum_ch gamma_ch V^T o   (Eq. 14; U = V^T)
 // Every output element is owned by one thread or one warp (no atomics), so the
-// product is deterministic.  All four kernels are bound by the FP64 pipe: a complex
-// multiply-add is four FP64 FMAs and the matrices are read from L2/HBM at well below
-// its bandwidth.
+// product is deterministic.  The kernels are templated on the complex type of the
+// operator: complex128 (the FP64 product, bound by the FP64 pipe: a complex
+// multiply-add is four FP64 FMAs against 16 bytes of matrix data) and complex64
+// (the mixed product's copy, FP32 arithmetic).  x and y are complex128 in both.
 //
 // Workspace layout per level l >= l0: s_l, o_l = [nbox][4*nrhs][Q_l], column 4r + ch
 // holds channel ch (x, y, z, rho) of right-hand side r.
@@ -30,18 +31,44 @@ void dfree(nesa_ctx *c, void *p) {
 }
 
 int ensure_workspace(nesa_ctx *c, int nrhs) {
-  if (nrhs <= c->nrhs_cap) return NESA_OK;
+  if (nrhs > c->nrhs_cap) {
+    for (int l = c->l0; l <= c->L; ++l) {
+      DevLevel &d = c->lev[l];
+      dfree(c, d.s);
+      dfree(c, d.o);
+      d.s = d.o = nullptr;
+      size_t bytes = sizeof(cplx) * (size_t)d.nbox * 4 * nrhs * d.q;
+      d.s = (cplx *)dalloc(c, bytes);
+      d.o = (cplx *)dalloc(c, bytes);
+    }
+    c->nrhs_cap = nrhs;
+  }
+  return NESA_OK;
+}
+
+static void ensure_workspace32(nesa_ctx *c, int nrhs) {
+  if (nrhs <= c->nrhs_cap32) return;
   for (int l = c->l0; l <= c->L; ++l) {
     DevLevel &d = c->lev[l];
-    dfree(c, d.s);
-    dfree(c, d.o);
-    d.s = d.o = nullptr;
-    size_t bytes = sizeof(cplx) * (size_t)d.nbox * 4 * nrhs * d.q;
-    d.s = (cplx *)dalloc(c, bytes);
-    d.o = (cplx *)dalloc(c, bytes);
+    dfree(c, d.s32);
+    dfree(c, d.o32);
+    d.s32 = d.o32 = nullptr;
+    size_t bytes = sizeof(cplxf) * (size_t)d.nbox * 4 * nrhs * d.q;
+    d.s32 = (cplxf *)dalloc(c, bytes);
+    d.o32 = (cplxf *)dalloc(c, bytes);
   }
-  c->nrhs_cap = nrhs;
-  return NESA_OK;
+  c->nrhs_cap32 = nrhs;
+}
+
+template <typename CT>
+__device__ __forceinline__ CT from64(double2 v);
+template <>
+__device__ __forceinline__ double2 from64<double2>(double2 v) {
+  return v;
+}
+template <>
+__device__ __forceinline__ float2 from64<float2>(double2 v) {
+  return make_float2((float)v.x, (float)v.y);
 }
 
 // Row tiling of a (Q rows x 4 channels) block: ntile tiles of tr rows, 4*tr threads.
@@ -57,24 +84,26 @@ static Tiling tiling(int q) {
 }
 
 // ------------------------------------------------------------------ radiation (Eq. 10)
-__global__ void __launch_bounds__(512) k_radiate(cplx *__restrict__ s, const cplx *__restrict__ V,
+template <typename CT>
+__global__ void __launch_bounds__(512) k_radiate(CT *__restrict__ s, const CT *__restrict__ V,
                                                  const int32_t *__restrict__ vc_ptr, const int32_t *__restrict__ vc_rwg,
                                                  const cplx *__restrict__ x, int64_t n, int nrhs, int q, int tr) {
-  extern __shared__ cplx xs[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  CT *xs = (CT *)smem_raw;
   const int32_t b = blockIdx.x;
   const int tile = blockIdx.y;
   const int ch = threadIdx.x / tr;
   const int i = tile * tr + threadIdx.x % tr;
   const bool active = ch < 4 && i < q;
   const int32_t g0 = vc_ptr[b], ns = vc_ptr[b + 1] - g0;
-  const cplx *Vb = V + (int64_t)4 * g0 * q;
+  const CT *Vb = V + (int64_t)4 * g0 * q;
   for (int r = 0; r < nrhs; ++r) {
     __syncthreads();
-    for (int j = threadIdx.x; j < ns; j += blockDim.x) xs[j] = x[(int64_t)r * n + vc_rwg[g0 + j]];
+    for (int j = threadIdx.x; j < ns; j += blockDim.x) xs[j] = from64<CT>(x[(int64_t)r * n + vc_rwg[g0 + j]]);
     __syncthreads();
     if (!active) continue;
-    cplx acc = {0.0, 0.0};
-    const cplx *vp = Vb + (int64_t)ch * q + i;
+    CT acc = {0, 0};
+    const CT *vp = Vb + (int64_t)ch * q + i;
 #pragma unroll 4
     for (int j = 0; j < ns; ++j) cfma(acc, vp[(int64_t)4 * j * q], xs[j]);
     s[((int64_t)b * 4 * nrhs + 4 * r + ch) * q + i] = acc;
@@ -83,10 +112,12 @@ __global__ void __launch_bounds__(512) k_radiate(cplx *__restrict__ s, const cpl
 
 // ------------------------------------------------------------------ source transfer (Eq. 11)
 // parent P at level l-1 (rows qp) gathers its children at level l (rows q)
-__global__ void __launch_bounds__(512) k_upward(cplx *__restrict__ sp, const cplx *__restrict__ sc,
-                                                const cplx *__restrict__ C, const int32_t *__restrict__ child_ptr,
+template <typename CT>
+__global__ void __launch_bounds__(512) k_upward(CT *__restrict__ sp, const CT *__restrict__ sc,
+                                                const CT *__restrict__ C, const int32_t *__restrict__ child_ptr,
                                                 const int32_t *__restrict__ octant, int nrhs, int qp, int q, int tr) {
-  extern __shared__ cplx col[];  // [4][q]
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  CT *col = (CT *)smem_raw;  // [4][q]
   const int32_t P = blockIdx.x;
   const int tile = blockIdx.y;
   const int ch = threadIdx.x / tr;
@@ -94,15 +125,15 @@ __global__ void __launch_bounds__(512) k_upward(cplx *__restrict__ sp, const cpl
   const bool active = ch < 4 && i < qp;
   const int32_t c0 = child_ptr[P], c1 = child_ptr[P + 1];
   for (int r = 0; r < nrhs; ++r) {
-    cplx acc = {0.0, 0.0};
+    CT acc = {0, 0};
     for (int32_t cb = c0; cb < c1; ++cb) {
       __syncthreads();
-      const cplx *src = sc + ((int64_t)cb * 4 * nrhs + 4 * r) * q;
+      const CT *src = sc + ((int64_t)cb * 4 * nrhs + 4 * r) * q;
       for (int j = threadIdx.x; j < 4 * q; j += blockDim.x) col[j] = src[j];
       __syncthreads();
       if (!active) continue;
-      const cplx *Cm = C + (int64_t)octant[cb] * qp * q + i;
-      const cplx *cs = col + ch * q;
+      const CT *Cm = C + (int64_t)octant[cb] * qp * q + i;
+      const CT *cs = col + ch * q;
 #pragma unroll 4
       for (int j = 0; j < q; ++j) cfma(acc, Cm[(int64_t)j * qp], cs[j]);
     }
@@ -111,14 +142,16 @@ __global__ void __launch_bounds__(512) k_upward(cplx *__restrict__ sp, const cpl
 }
 
 // ------------------------------------------------------------------ translation + potential transfer
-__global__ void __launch_bounds__(512) k_translate(cplx *__restrict__ o, const cplx *__restrict__ s,
-                                                   const cplx *__restrict__ D, const int32_t *__restrict__ il_ptr,
+template <typename CT>
+__global__ void __launch_bounds__(512) k_translate(CT *__restrict__ o, const CT *__restrict__ s,
+                                                   const CT *__restrict__ D, const int32_t *__restrict__ il_ptr,
                                                    const int32_t *__restrict__ il_src,
-                                                   const int32_t *__restrict__ il_slot, const cplx *__restrict__ op,
-                                                   const cplx *__restrict__ Ct, const int32_t *__restrict__ parent,
+                                                   const int32_t *__restrict__ il_slot, const CT *__restrict__ op,
+                                                   const CT *__restrict__ Ct, const int32_t *__restrict__ parent,
                                                    const int32_t *__restrict__ octant, int nrhs, int q, int qp,
                                                    int tr) {
-  extern __shared__ cplx col[];  // [4][max(q, qp)]
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  CT *col = (CT *)smem_raw;  // [4][max(q, qp)]
   const int32_t a = blockIdx.x;
   const int tile = blockIdx.y;
   const int ch = threadIdx.x / tr;
@@ -126,28 +159,28 @@ __global__ void __launch_bounds__(512) k_translate(cplx *__restrict__ o, const c
   const bool active = ch < 4 && i < q;
   const int32_t e0 = il_ptr[a], e1 = il_ptr[a + 1];
   for (int r = 0; r < nrhs; ++r) {
-    cplx acc = {0.0, 0.0};
+    CT acc = {0, 0};
     if (op) {  // potential transfer from the parent (Eq. 13): o_a += C^T o_P
       __syncthreads();
       const int32_t P = parent[a];
-      const cplx *src = op + ((int64_t)P * 4 * nrhs + 4 * r) * qp;
+      const CT *src = op + ((int64_t)P * 4 * nrhs + 4 * r) * qp;
       for (int j = threadIdx.x; j < 4 * qp; j += blockDim.x) col[j] = src[j];
       __syncthreads();
       if (active) {
-        const cplx *Bm = Ct + (int64_t)octant[a] * q * qp + i;
-        const cplx *cs = col + ch * qp;
+        const CT *Bm = Ct + (int64_t)octant[a] * q * qp + i;
+        const CT *cs = col + ch * qp;
 #pragma unroll 4
         for (int j = 0; j < qp; ++j) cfma(acc, Bm[(int64_t)j * q], cs[j]);
       }
     }
     for (int32_t e = e0; e < e1; ++e) {  // translations (Eq. 12)
       __syncthreads();
-      const cplx *src = s + ((int64_t)il_src[e] * 4 * nrhs + 4 * r) * q;
+      const CT *src = s + ((int64_t)il_src[e] * 4 * nrhs + 4 * r) * q;
       for (int j = threadIdx.x; j < 4 * q; j += blockDim.x) col[j] = src[j];
       __syncthreads();
       if (!active) continue;
-      const cplx *Dm = D + (int64_t)il_slot[e] * q * q + i;
-      const cplx *cs = col + ch * q;
+      const CT *Dm = D + (int64_t)il_slot[e] * q * q + i;
+      const CT *cs = col + ch * q;
 #pragma unroll 4
       for (int j = 0; j < q; ++j) cfma(acc, Dm[(int64_t)j * q], cs[j]);
     }
@@ -156,40 +189,41 @@ __global__ void __launch_bounds__(512) k_translate(cplx *__restrict__ o, const c
 }
 
 // ------------------------------------------------------------------ near field + reception
+template <typename CT>
 __global__ void __launch_bounds__(256) k_near_receive(cplx *__restrict__ y, const cplx *__restrict__ x, int64_t n,
                                                       int nrhs, const int64_t *__restrict__ nz_ptr,
                                                       const int32_t *__restrict__ nz_col,
-                                                      const cplx *__restrict__ nz_val, const int32_t *__restrict__ rx_ptr,
+                                                      const CT *__restrict__ nz_val, const int32_t *__restrict__ rx_ptr,
                                                       const int32_t *__restrict__ rx_col,
-                                                      const int32_t *__restrict__ vc_leaf, const cplx *__restrict__ V,
-                                                      const cplx *__restrict__ oL, int q, double eta_k, double inv_k2,
+                                                      const int32_t *__restrict__ vc_leaf, const CT *__restrict__ V,
+                                                      const CT *__restrict__ oL, int q, double eta_k, double inv_k2,
                                                       int parts) {
   const int64_t m = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (m >= n) return;
   for (int r = 0; r < nrhs; ++r) {
-    cplx near = {0.0, 0.0}, far = {0.0, 0.0};
+    CT near = {0, 0}, far = {0, 0};
     if (parts & NESA_PART_NEAR) {
       const cplx *xr = x + (int64_t)r * n;
-      for (int64_t e = nz_ptr[m] + lane; e < nz_ptr[m + 1]; e += 32) cfma(near, nz_val[e], xr[nz_col[e]]);
+      for (int64_t e = nz_ptr[m] + lane; e < nz_ptr[m + 1]; e += 32) cfma(near, nz_val[e], from64<CT>(xr[nz_col[e]]));
     }
     if (parts & NESA_PART_FAR) {
       for (int32_t e = rx_ptr[m]; e < rx_ptr[m + 1]; ++e) {
         const int32_t g = rx_col[e];
         const int32_t lf = vc_leaf[g];
-        const cplx *vg = V + (int64_t)4 * g * q;
-        const cplx *ol = oL + ((int64_t)lf * 4 * nrhs + 4 * r) * q;
+        const CT *vg = V + (int64_t)4 * g * q;
+        const CT *ol = oL + ((int64_t)lf * 4 * nrhs + 4 * r) * q;
         for (int ch = 0; ch < 4; ++ch) {
-          cplx t = {0.0, 0.0};
+          CT t = {0, 0};
           for (int i = lane; i < q; i += 32) cfma(t, vg[ch * q + i], ol[ch * q + i]);
           const double gam = ch < 3 ? 1.0 : -inv_k2;
-          far.x = fma(gam, t.x, far.x);
-          far.y = fma(gam, t.y, far.y);
+          far.x += (decltype(far.x))(gam * t.x);
+          far.y += (decltype(far.y))(gam * t.y);
         }
       }
     }
-    // -i eta k * far
-    cplx v = make_double2(near.x + eta_k * far.y, near.y - eta_k * far.x);
+    // -i eta k * far, summed over the warp in FP64
+    double2 v = make_double2((double)near.x + eta_k * (double)far.y, (double)near.y - eta_k * (double)far.x);
     for (int off = 16; off > 0; off >>= 1) {
       v.x += __shfl_down_sync(0xffffffffu, v.x, off);
       v.y += __shfl_down_sync(0xffffffffu, v.y, off);
@@ -230,44 +264,53 @@ struct StageScope {
   }
 };
 
-// Launch the product on the context's stream.
-void launch_matvec(nesa_ctx *c, const cplx *x, cplx *y, int nrhs, int parts) {
+// One precision of the product.  Arrays: near values, V, and per level s, o, C, Ct, D.
+template <typename CT>
+struct OpView {
+  const CT *nz_val, *V;
+  CT *s[NESA_MAX_LEVELS], *o[NESA_MAX_LEVELS];
+  const CT *C[NESA_MAX_LEVELS], *Ct[NESA_MAX_LEVELS], *D[NESA_MAX_LEVELS];
+};
+
+template <typename CT>
+static void run_product(nesa_ctx *c, const OpView<CT> &op, const cplx *x, cplx *y, int nrhs, int parts) {
   cudaStream_t st = c->stream;
   const int L = c->L, l0 = c->l0;
-  const double B = sizeof(cplx);
+  const double B = sizeof(CT);
   const double ncol = (double)c->info.v_columns;
   if (parts & NESA_PART_FAR) {
     {  // radiation
       DevLevel &d = c->lev[L];
       Tiling t = tiling(d.q);
-      const int maxs = c->max_leaf_cols;
-      size_t smem = sizeof(cplx) * (size_t)std::max(1, maxs);
-      StageScope sc(c, 0, 32.0 * nrhs * ncol * d.q, B * (4.0 * ncol * d.q + nrhs * (c->n + 4.0 * d.nbox * d.q)));
-      k_radiate<<<dim3((unsigned)d.nbox, t.ntile), t.threads, smem, st>>>(d.s, c->d_V, c->d_vc_ptr, c->d_vc_rwg, x,
-                                                                          c->n, nrhs, d.q, t.tr);
+      size_t smem = sizeof(CT) * (size_t)std::max(1, c->max_leaf_cols);
+      StageScope sc(c, 0, 32.0 * nrhs * ncol * d.q,
+                    B * (4.0 * ncol * d.q + 4.0 * nrhs * d.nbox * d.q) + 16.0 * nrhs * c->n);
+      k_radiate<CT><<<dim3((unsigned)d.nbox, t.ntile), t.threads, smem, st>>>(op.s[L], op.V, c->d_vc_ptr, c->d_vc_rwg,
+                                                                              x, c->n, nrhs, d.q, t.tr);
     }
     for (int l = L; l > l0; --l) {  // source transfer
       DevLevel &d = c->lev[l], &p = c->lev[l - 1];
       Tiling t = tiling(p.q);
-      size_t smem = sizeof(cplx) * 4 * (size_t)d.q;
+      size_t smem = sizeof(CT) * 4 * (size_t)d.q;
       StageScope sc(c, 1, 32.0 * nrhs * d.nbox * (double)p.q * d.q,
                     B * (8.0 * p.q * d.q + 4.0 * nrhs * ((double)d.nbox * d.q + (double)p.nbox * p.q)));
-      k_upward<<<dim3((unsigned)p.nbox, t.ntile), t.threads, smem, st>>>(p.s, d.s, d.C, p.child_ptr, d.octant, nrhs,
-                                                                         p.q, d.q, t.tr);
+      k_upward<CT><<<dim3((unsigned)p.nbox, t.ntile), t.threads, smem, st>>>(op.s[l - 1], op.s[l], op.C[l],
+                                                                             p.child_ptr, d.octant, nrhs, p.q, d.q,
+                                                                             t.tr);
     }
     for (int l = l0; l <= L; ++l) {  // translation and potential transfer
       DevLevel &d = c->lev[l];
       Tiling t = tiling(d.q);
       const bool down = l > l0;
       const int qp = down ? c->lev[l - 1].q : 0;
-      size_t smem = sizeof(cplx) * 4 * (size_t)std::max(d.q, qp);
+      size_t smem = sizeof(CT) * 4 * (size_t)std::max(d.q, qp);
       double fl = 32.0 * nrhs * ((double)d.nil * d.q * d.q + (down ? (double)d.nbox * d.q * qp : 0.0));
       double by = B * ((double)d.noff * d.q * d.q + (down ? 8.0 * d.q * qp : 0.0) +
                        4.0 * nrhs * (2.0 * d.nbox * d.q + (down ? (double)c->lev[l - 1].nbox * qp : 0.0)));
       StageScope sc(c, 2, fl, by);
-      k_translate<<<dim3((unsigned)d.nbox, t.ntile), t.threads, smem, st>>>(
-          d.o, d.s, d.D, d.il_ptr, d.il_src, d.il_slot, down ? c->lev[l - 1].o : nullptr, down ? d.Ct : nullptr,
-          d.parent, d.octant, nrhs, d.q, qp, t.tr);
+      k_translate<CT><<<dim3((unsigned)d.nbox, t.ntile), t.threads, smem, st>>>(
+          op.o[l], op.s[l], op.D[l], d.il_ptr, d.il_src, d.il_slot, down ? op.o[l - 1] : nullptr,
+          down ? op.Ct[l] : nullptr, d.parent, d.octant, nrhs, d.q, qp, t.tr);
     }
   }
   const DevLevel &dL = c->lev[L];
@@ -276,11 +319,73 @@ void launch_matvec(nesa_ctx *c, const cplx *x, cplx *y, int nrhs, int parts) {
               ((parts & NESA_PART_FAR) ? 32.0 * nrhs * ncol * dL.q : 0.0);
   double by = ((parts & NESA_PART_NEAR) ? (B + 4.0) * nnz + 8.0 * (c->n + 1) : 0.0) +
               ((parts & NESA_PART_FAR) ? B * 4.0 * ncol * dL.q + B * 4.0 * nrhs * dL.nbox * dL.q : 0.0) +
-              B * 2.0 * nrhs * c->n;
+              16.0 * 2.0 * nrhs * c->n;
   StageScope sc(c, 3, fl, by);
-  k_near_receive<<<grid_for(c->n * 32, 256), 256, 0, st>>>(y, x, c->n, nrhs, c->d_nz_ptr, c->d_nz_col, c->d_nz_val,
-                                                          c->d_rx_ptr, c->d_rx_col, c->d_vc_leaf, c->d_V, dL.o, dL.q,
-                                                          c->eta * c->k, 1.0 / (c->k * c->k), parts);
+  k_near_receive<CT><<<grid_for(c->n * 32, 256), 256, 0, st>>>(y, x, c->n, nrhs, c->d_nz_ptr, c->d_nz_col, op.nz_val,
+                                                              c->d_rx_ptr, c->d_rx_col, c->d_vc_leaf, op.V, op.o[L],
+                                                              dL.q, c->eta * c->k, 1.0 / (c->k * c->k), parts);
+}
+
+// Launch the product on the context's stream.
+void launch_matvec(nesa_ctx *c, const cplx *x, cplx *y, int nrhs, int parts) {
+  if (parts & NESA_PART_MIXED) {
+    if (!c->mixed) fail(NESA_ERR_INVALID_ARG, "context was not built with NESA_MIXED");
+    ensure_workspace32(c, nrhs);
+    OpView<cplxf> op{};
+    op.nz_val = c->d_nz_val32;
+    op.V = c->d_V32;
+    for (int l = c->l0; l <= c->L; ++l) {
+      op.s[l] = c->lev[l].s32;
+      op.o[l] = c->lev[l].o32;
+      op.C[l] = c->lev[l].C32;
+      op.Ct[l] = c->lev[l].Ct32;
+      op.D[l] = c->lev[l].D32;
+    }
+    run_product<cplxf>(c, op, x, y, nrhs, parts & NESA_PART_ALL);
+    return;
+  }
+  OpView<cplx> op{};
+  op.nz_val = c->d_nz_val;
+  op.V = c->d_V;
+  for (int l = c->l0; l <= c->L; ++l) {
+    op.s[l] = c->lev[l].s;
+    op.o[l] = c->lev[l].o;
+    op.C[l] = c->lev[l].C;
+    op.Ct[l] = c->lev[l].Ct;
+    op.D[l] = c->lev[l].D;
+  }
+  run_product<cplx>(c, op, x, y, nrhs, parts & NESA_PART_ALL);
+}
+
+// ------------------------------------------------------------------ mixed-precision copies
+__global__ void k_to_c64(cplxf *dst, const cplx *src, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    cplx v = src[e];
+    dst[e] = make_float2((float)v.x, (float)v.y);
+  }
+}
+
+static cplxf *copy_c64(nesa_ctx *c, const cplx *src, int64_t n) {
+  cplxf *d = (cplxf *)dalloc(c, sizeof(cplxf) * (size_t)std::max<int64_t>(n, 1));
+  if (n > 0) k_to_c64<<<(unsigned)std::min<int64_t>((n + 255) / 256, 65536), 256, 0, c->stream>>>(d, src, n);
+  return d;
+}
+
+void build_mixed(nesa_ctx *c) {
+  c->d_nz_val32 = copy_c64(c, c->d_nz_val, c->info.near_nnz);
+  c->d_V32 = copy_c64(c, c->d_V, 4 * c->info.v_columns * (int64_t)c->lev[c->L].q);
+  for (int l = c->l0; l <= c->L; ++l) {
+    DevLevel &d = c->lev[l];
+    d.D32 = copy_c64(c, d.D, d.noff * (int64_t)d.q * d.q);
+    if (l > c->l0) {
+      const int64_t cn = 8LL * c->lev[l - 1].q * d.q;
+      d.C32 = copy_c64(c, d.C, cn);
+      d.Ct32 = copy_c64(c, d.Ct, cn);
+    }
+  }
+  check_cuda(cudaGetLastError(), "mixed copies");
+  check_cuda(cudaStreamSynchronize(c->stream), "mixed copies");
+  c->mixed = true;
 }
 
 // ------------------------------------------------------------------ plane-wave excitation
@@ -325,18 +430,6 @@ using namespace nesa;
 
 extern "C" {
 
-int nesa_matvec_parts(nesa_ctx *c, const nesa_c128 *x, nesa_c128 *y, int nrhs, int parts) {
-  if (!c || !x || !y || nrhs < 1 || nrhs > 64 || parts < 1 || parts > NESA_PART_ALL) return NESA_ERR_INVALID_ARG;
-  try {
-    ensure_workspace(c, nrhs);
-    launch_matvec(c, (const cplx *)x, (cplx *)y, nrhs, parts);
-    check_cuda(cudaGetLastError(), "matvec launch");
-  } catch (const Error &e) {
-    return e.status;
-  }
-  return NESA_OK;
-}
-
 int nesa_profile_enable(nesa_ctx *c, int enable) {
   if (!c) return NESA_ERR_INVALID_ARG;
   cudaStreamSynchronize(c->stream);
@@ -368,12 +461,29 @@ int nesa_profile_read(nesa_ctx *c, nesa_profile *out) {
   return NESA_OK;
 }
 
+int nesa_matvec_parts(nesa_ctx *c, const nesa_c128 *x, nesa_c128 *y, int nrhs, int parts) {
+  if (!c || !x || !y || nrhs < 1 || nrhs > 64 || (parts & NESA_PART_ALL) == 0 ||
+      (parts & ~(NESA_PART_ALL | NESA_PART_MIXED)) != 0)
+    return NESA_ERR_INVALID_ARG;
+  try {
+    ensure_workspace(c, nrhs);
+    launch_matvec(c, (const cplx *)x, (cplx *)y, nrhs, parts);
+    check_cuda(cudaGetLastError(), "matvec launch");
+  } catch (const Error &e) {
+    set_last_error(e.what);
+    return e.status;
+  }
+  return NESA_OK;
+}
+
 int nesa_matvec(nesa_ctx *c, const nesa_c128 *x, nesa_c128 *y, int nrhs) {
   return nesa_matvec_parts(c, x, y, nrhs, NESA_PART_ALL);
 }
 
-int nesa_matvec_host(nesa_ctx *c, const nesa_c128 *xh, nesa_c128 *yh, int nrhs) {
-  if (!c || !xh || !yh || nrhs < 1 || nrhs > 64) return NESA_ERR_INVALID_ARG;
+int nesa_matvec_host(nesa_ctx *c, const nesa_c128 *xh, nesa_c128 *yh, int nrhs, int parts) {
+  if (!c || !xh || !yh || nrhs < 1 || nrhs > 64 || (parts & NESA_PART_ALL) == 0 ||
+      (parts & ~(NESA_PART_ALL | NESA_PART_MIXED)) != 0)
+    return NESA_ERR_INVALID_ARG;
   try {
     if (nrhs > c->hbuf_cap) {
       dfree(c, c->d_hx);
@@ -385,11 +495,12 @@ int nesa_matvec_host(nesa_ctx *c, const nesa_c128 *xh, nesa_c128 *yh, int nrhs) 
     size_t bytes = sizeof(cplx) * (size_t)c->n * nrhs;
     check_cuda(cudaMemcpyAsync(c->d_hx, xh, bytes, cudaMemcpyHostToDevice, c->stream), "H2D");
     ensure_workspace(c, nrhs);
-    launch_matvec(c, c->d_hx, c->d_hy, nrhs, NESA_PART_ALL);
+    launch_matvec(c, c->d_hx, c->d_hy, nrhs, parts);
     check_cuda(cudaGetLastError(), "matvec launch");
     check_cuda(cudaMemcpyAsync(yh, c->d_hy, bytes, cudaMemcpyDeviceToHost, c->stream), "D2H");
     check_cuda(cudaStreamSynchronize(c->stream), "sync");
   } catch (const Error &e) {
+    set_last_error(e.what);
     return e.status;
   }
   return NESA_OK;
@@ -416,6 +527,7 @@ int nesa_rhs_planewave(nesa_ctx *c, const double *khat, const nesa_c128 *pol, in
     check_cuda(cudaStreamSynchronize(c->stream), "rhs");
     dfree(c, d);
   } catch (const Error &e) {
+    set_last_error(e.what);
     return e.status;
   }
   return NESA_OK;

@@ -39,6 +39,9 @@ struct SolveWork {
   double *est = nullptr;   // [nrhs] residual estimate
   int *h_state = nullptr;  // pinned host mirror of state
   double *h_est = nullptr; // pinned host mirror of est
+  cplx *ro = nullptr;      // [nrhs][n] FP64 residual of the refinement loop
+  cplx *dx = nullptr;      // [nrhs][n] correction from the inner solve
+  double *onrm = nullptr;  // [nrhs] norms of the refinement loop
 };
 
 static const int kChunk = 2048;  // vector elements per partial-sum block
@@ -282,7 +285,7 @@ static SolveWork *get_work(nesa_ctx *c, int m, int nrhs) {
   SolveWork *W = (SolveWork *)c->solve_work;
   if (W->m >= m && W->nrhs >= nrhs) return W;
   void *old[] = {W->V, W->w, W->r, W->H, W->h, W->cs, W->sn, W->g, W->y, W->part, W->nrm, W->bnorm, W->steps,
-                 W->state, W->est};
+                 W->state, W->est, W->ro, W->dx, W->onrm};
   for (void *p : old) dfree(c, p);
   if (W->h_state) cudaFreeHost(W->h_state);
   if (W->h_est) cudaFreeHost(W->h_est);
@@ -306,6 +309,9 @@ static SolveWork *get_work(nesa_ctx *c, int m, int nrhs) {
   W->steps = (int *)dalloc(c, sizeof(int) * nrhs);
   W->state = (int *)dalloc(c, sizeof(int) * nrhs);
   W->est = (double *)dalloc(c, sizeof(double) * nrhs);
+  W->ro = (cplx *)dalloc(c, sizeof(cplx) * (size_t)nrhs * n);
+  W->dx = (cplx *)dalloc(c, sizeof(cplx) * (size_t)nrhs * n);
+  W->onrm = (double *)dalloc(c, sizeof(double) * nrhs);
   check_cuda(cudaMallocHost(&W->h_state, sizeof(int) * nrhs), "pinned");
   check_cuda(cudaMallocHost(&W->h_est, sizeof(double) * nrhs), "pinned");
   return W;
@@ -320,35 +326,18 @@ void nesa_free_solve_work(nesa_ctx *c) {
   c->solve_work = nullptr;
 }
 
-extern "C" {
-
-void nesa_default_solve_opts(nesa_solve_opts *o) {
-  if (!o) return;
-  std::memset(o, 0, sizeof(*o));
-  o->restart = 50;
-  o->max_iters = 1000;
-}
-
-int nesa_solve(nesa_ctx *c, const nesa_c128 *b_dev, nesa_c128 *x_dev, int nrhs, double tol,
-               const nesa_solve_opts *opts, nesa_solve_info *info) {
-  if (!c || !b_dev || !x_dev || nrhs < 1 || nrhs > 64 || !(tol > 0.0)) return NESA_ERR_INVALID_ARG;
-  nesa_solve_opts o;
-  nesa_default_solve_opts(&o);
-  if (opts) o = *opts;
-  if (o.restart < 1 || o.restart > 1000 || o.max_iters < 1) return NESA_ERR_INVALID_ARG;
-  auto t0 = std::chrono::steady_clock::now();
-  nesa_solve_info I;
-  std::memset(&I, 0, sizeof(I));
+// GMRES from x0 = 0 on the product selected by `parts`.  Throws Error on CUDA
+// failures.  Returns NESA_OK, NESA_ERR_NOT_CONVERGED or NESA_ERR_NUMERIC; adds to the
+// counters of I and fills its true residuals.
+static int gmres_run(nesa_ctx *c, const cplx *b, cplx *x, int nrhs, double tol, int m, int max_iters, int parts,
+                     nesa_solve_info &I) {
   int status = NESA_OK;
-  try {
-    const int m = o.restart;
+  {
     SolveWork *W = get_work(c, m, nrhs);
     ensure_workspace(c, nrhs);
     cudaStream_t st = c->stream;
     const int64_t n = c->n;
     const int nchunk = (int)((n + kChunk - 1) / kChunk);
-    const cplx *b = (const cplx *)b_dev;
-    cplx *x = (cplx *)x_dev;
     const dim3 vgrid(blocks_for(n, 256, 4096), nrhs);
     auto norms = [&](const cplx *v, double *out) {
       k_norm2<<<dim3(nchunk, nrhs), 256, 0, st>>>((double2 *)W->part, v, n, nchunk);
@@ -371,13 +360,13 @@ int nesa_solve(nesa_ctx *c, const nesa_c128 *b_dev, nesa_c128 *x_dev, int nrhs, 
       for (int r = 0; r < nrhs; ++r) running |= W->h_state[r] == 0;
       for (int r = 0; r < nrhs; ++r)
         if (W->h_state[r] == 3) status = NESA_ERR_NUMERIC;
-      if (!running || status != NESA_OK || total >= o.max_iters) break;
+      if (!running || status != NESA_OK || total >= max_iters) break;
       I.restarts += total > 0;
       int j = 0;
-      for (; j < m && total < o.max_iters; ++j) {
+      for (; j < m && total < max_iters; ++j) {
         cplx *Vj = W->V + (size_t)j * nrhs * n;
         cplx *Vn = W->V + (size_t)(j + 1) * nrhs * n;
-        launch_matvec(c, Vj, W->w, nrhs, NESA_PART_ALL);
+        launch_matvec(c, Vj, W->w, nrhs, parts);
         I.matvecs += 1;
         // CGS2: two rounds of projection onto V_0..V_j
         for (int pass = 0; pass < 2; ++pass) {
@@ -403,11 +392,11 @@ int nesa_solve(nesa_ctx *c, const nesa_c128 *b_dev, nesa_c128 *x_dev, int nrhs, 
       k_backsolve<<<(nrhs + 63) / 64, 64, 0, st>>>(W->y, W->H, W->g, W->steps, m, nrhs);
       k_update_x<<<vgrid, 256, 0, st>>>(x, W->V, W->y, m, W->steps, n, nrhs);
       // true residual
-      launch_matvec(c, x, W->r, nrhs, NESA_PART_ALL);
+      launch_matvec(c, x, W->r, nrhs, parts);
       I.matvecs += 1;
       k_residual<<<blocks_for((int64_t)nrhs * n, 256, 4096), 256, 0, st>>>(W->r, b, (int64_t)nrhs * n);
       check_cuda(cudaGetLastError(), "gmres launch");
-      if (total >= o.max_iters) {
+      if (total >= max_iters) {
         norms(W->r, W->nrm);
         break;
       }
@@ -418,7 +407,7 @@ int nesa_solve(nesa_ctx *c, const nesa_c128 *b_dev, nesa_c128 *x_dev, int nrhs, 
     check_cuda(cudaMemcpyAsync(rn.data(), W->nrm, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st), "res");
     check_cuda(cudaMemcpyAsync(bn.data(), W->bnorm, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st), "bn");
     check_cuda(cudaStreamSynchronize(st), "solve");
-    I.iterations = total;
+    I.iterations += total;
     for (int r = 0; r < nrhs; ++r) {
       double rr = bn[r] > 0.0 ? rn[r] / bn[r] : 0.0;
       I.rel_residual[r] = rr;
@@ -427,6 +416,105 @@ int nesa_solve(nesa_ctx *c, const nesa_c128 *b_dev, nesa_c128 *x_dev, int nrhs, 
       if (rr <= tol * (1.0 + 1e-6)) I.converged += 1;
     }
     if (status == NESA_OK && I.converged < nrhs) status = NESA_ERR_NOT_CONVERGED;
+  }
+  return status;
+}
+
+// x += d
+__global__ void k_axpy(cplx *x, const cplx *d, int64_t total) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    cplx a = x[e], b = d[e];
+    x[e] = make_double2(a.x + b.x, a.y + b.y);
+  }
+}
+
+// FP64 iterative refinement: r = b - Z~ x with the FP64 product, an inner GMRES on the
+// low-precision product solves Z~_mixed d = r to inner_tol, x += d.
+static int refine_run(nesa_ctx *c, const cplx *b, cplx *x, int nrhs, double tol, const nesa_solve_opts &o,
+                      nesa_solve_info &I) {
+  if (!c->mixed) fail(NESA_ERR_INVALID_ARG, "mixed solve needs a context built with NESA_MIXED");
+  SolveWork *W = get_work(c, o.restart, nrhs);
+  cudaStream_t st = c->stream;
+  const int64_t n = c->n, total = n * nrhs;
+  const int nchunk = (int)((n + kChunk - 1) / kChunk);
+  auto norms = [&](const cplx *v, double *out_dev, std::vector<double> &host) {
+    k_norm2<<<dim3(nchunk, nrhs), 256, 0, st>>>((double2 *)W->part, v, n, nchunk);
+    k_norm_reduce<<<nrhs, 32, 0, st>>>(out_dev, (const double2 *)W->part, nchunk);
+    host.resize(nrhs);
+    check_cuda(cudaMemcpyAsync(host.data(), out_dev, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st), "norm");
+    check_cuda(cudaStreamSynchronize(st), "norm");
+  };
+  std::vector<double> bn, rn;
+  norms(b, W->onrm, bn);
+  check_cuda(cudaMemsetAsync(x, 0, sizeof(cplx) * (size_t)total, st), "x0");
+  check_cuda(cudaMemcpyAsync(W->ro, b, sizeof(cplx) * (size_t)total, cudaMemcpyDeviceToDevice, st), "r0");
+  int status = NESA_OK;
+  for (int it = 0;; ++it) {
+    norms(W->ro, W->onrm, rn);
+    bool done = true;
+    for (int r = 0; r < nrhs; ++r) {
+      double e = bn[r] > 0.0 ? rn[r] / bn[r] : 0.0;
+      if (!std::isfinite(e)) return NESA_ERR_NUMERIC;
+      done &= e <= tol;
+    }
+    if (done || it >= o.max_refine || I.iterations >= o.max_iters) break;
+    nesa_solve_info Ii;
+    std::memset(&Ii, 0, sizeof(Ii));
+    int si = gmres_run(c, W->ro, W->dx, nrhs, o.inner_tol, o.restart, o.max_iters - I.iterations,
+                       NESA_PART_ALL | NESA_PART_MIXED, Ii);
+    I.iterations += Ii.iterations;
+    I.matvecs += Ii.matvecs;
+    I.restarts += Ii.restarts;
+    if (si == NESA_ERR_NUMERIC) return si;
+    k_axpy<<<blocks_for(total, 256, 4096), 256, 0, st>>>(x, W->dx, total);
+    launch_matvec(c, x, W->ro, nrhs, NESA_PART_ALL);
+    I.fp64_matvecs += 1;
+    k_residual<<<blocks_for(total, 256, 4096), 256, 0, st>>>(W->ro, b, total);
+    check_cuda(cudaGetLastError(), "refinement launch");
+    I.refinements += 1;
+  }
+  I.converged = 0;
+  for (int r = 0; r < nrhs; ++r) {
+    double e = bn[r] > 0.0 ? rn[r] / bn[r] : 0.0;
+    I.rel_residual[r] = e;
+    if (e <= tol) I.converged += 1;
+  }
+  if (I.converged < nrhs) status = NESA_ERR_NOT_CONVERGED;
+  return status;
+}
+
+extern "C" {
+
+void nesa_default_solve_opts(nesa_solve_opts *o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->restart = 50;
+  o->max_iters = 1000;
+  o->mixed = 0;
+  o->max_refine = 10;
+  o->inner_tol = 1e-3;
+}
+
+int nesa_solve(nesa_ctx *c, const nesa_c128 *b_dev, nesa_c128 *x_dev, int nrhs, double tol,
+               const nesa_solve_opts *opts, nesa_solve_info *info) {
+  if (!c || !b_dev || !x_dev || nrhs < 1 || nrhs > 64 || !(tol > 0.0)) return NESA_ERR_INVALID_ARG;
+  nesa_solve_opts o;
+  nesa_default_solve_opts(&o);
+  if (opts) o = *opts;
+  if (o.restart < 1 || o.restart > 1000 || o.max_iters < 1 || (o.mixed != 0 && o.mixed != 1) ||
+      o.max_refine < 0 || !(o.inner_tol > 0.0 && o.inner_tol < 1.0))
+    return NESA_ERR_INVALID_ARG;
+  auto t0 = std::chrono::steady_clock::now();
+  nesa_solve_info I;
+  std::memset(&I, 0, sizeof(I));
+  int status = NESA_OK;
+  try {
+    if (o.mixed) {
+      status = refine_run(c, (const cplx *)b_dev, (cplx *)x_dev, nrhs, tol, o, I);
+    } else {
+      status = gmres_run(c, (const cplx *)b_dev, (cplx *)x_dev, nrhs, tol, o.restart, o.max_iters, NESA_PART_ALL, I);
+      I.fp64_matvecs = I.matvecs;
+    }
   } catch (const Error &e) {
     status = e.status;
     set_last_error(e.what);
