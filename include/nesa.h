@@ -67,6 +67,11 @@ extern "C" {
 
 /* translation engine of the mixed product (nesa_params.translate) */
 #define NESA_TRANSLATE_FP32 0 /* complex64 on the CUDA cores */
+/* Tensor cores (tcgen05, BF16 operands split hi/lo, three products per K step, FP32
+   accumulation): the pairs of one level that share an offset form one complex GEMM
+   (Sec. 5.1 notes that equal relative positions share a matrix), computed as the real
+   GEMM [[Re D, -Im D], [Im D, Re D]] [Re s; Im s] */
+#define NESA_TRANSLATE_TENSOR 1
 
 typedef struct nesa_ctx nesa_ctx; /* opaque; owns all device memory of one operator */
 
@@ -272,6 +277,13 @@ int nesa_profile_read(nesa_ctx *ctx, nesa_profile *out);
  */
 #define NESA_NOALLOC_SCRATCH_BYTES (32u << 20)
 int nesa_matvec_noalloc(nesa_ctx *ctx, const nesa_c128 *x_dev, nesa_c128 *y_dev, int nrhs);
+
+/*
+ * Device-side status of the context's kernels since the last call: NESA_OK, or
+ * NESA_ERR_TIMEOUT when a bounded wait inside a kernel (tensor-core translation) ran
+ * out; that product's result is then invalid.  Clears the status.  Synchronous.
+ */
+int nesa_device_status(nesa_ctx *ctx);
 
 /* Release all memory of the context (NULL is allowed). */
 void nesa_destroy(nesa_ctx *ctx);

@@ -689,6 +689,7 @@ extern "C" {
 static void free_ctx(nesa_ctx *c) {
   if (!c) return;
   nesa_free_solve_work(c);
+  tc_free(c);
   for (void *p : c->allocs) cudaFree(p);
   for (auto &p : c->pending) {
     cudaEventDestroy(p.a);
@@ -755,6 +756,7 @@ int nesa_build(const nesa_mesh *mesh, double k, const nesa_params *params, nesa_
   if (params->precision == NESA_MIXED) {
     try {
       build_mixed(c);
+      if (params->translate == NESA_TRANSLATE_TENSOR) tc_build(c);
     } catch (const Error &e) {
       g_last_error = e.what;
       free_ctx(c);

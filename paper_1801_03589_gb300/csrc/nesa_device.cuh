@@ -116,6 +116,8 @@ struct nesa_ctx {
   std::vector<cudaEvent_t> event_pool;
   nesa_profile prof{};
   void *solve_work = nullptr;    // GMRES workspace (nesa_solve.cu)
+  void *tc_state = nullptr;      // tensor-core translation state (nesa_tc.cu)
+  bool tc_enabled = false;
   std::vector<void *> allocs;    // every device allocation owned by the context
 };
 
@@ -127,6 +129,12 @@ void check_cuda(cudaError_t e, const char *what);
 void launch_matvec(nesa_ctx *c, const cplx *x, cplx *y, int nrhs, int parts);
 // converted copies of the operator for the mixed-precision product
 void build_mixed(nesa_ctx *c);
+// tensor-core translations of the mixed product (nesa_tc.cu)
+void tc_build(nesa_ctx *c);
+void tc_translate_level(nesa_ctx *c, int l, const cplxf *s, cplxf *o, const cplxf *op, const cplxf *Ct, int nrhs,
+                        int tr, int ntile, int threads);
+int tc_take_error(nesa_ctx *c);
+void tc_free(nesa_ctx *c);
 int ensure_workspace(nesa_ctx *c, int nrhs);
 }  // namespace nesa
 void nesa_free_solve_work(nesa_ctx *c);

@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 
 #include "nesa_device.cuh"
 
@@ -308,6 +309,13 @@ static void run_product(nesa_ctx *c, const OpView<CT> &op, const cplx *x, cplx *
       double by = B * ((double)d.noff * d.q * d.q + (down ? 8.0 * d.q * qp : 0.0) +
                        4.0 * nrhs * (2.0 * d.nbox * d.q + (down ? (double)c->lev[l - 1].nbox * qp : 0.0)));
       StageScope sc(c, 2, fl, by);
+      if constexpr (std::is_same<CT, cplxf>::value) {
+        if (c->tc_enabled) {
+          tc_translate_level(c, l, op.s[l], op.o[l], down ? op.o[l - 1] : nullptr, down ? op.Ct[l] : nullptr, nrhs,
+                             t.tr, t.ntile, t.threads);
+          continue;
+        }
+      }
       k_translate<CT><<<dim3((unsigned)d.nbox, t.ntile), t.threads, smem, st>>>(
           op.o[l], op.s[l], op.D[l], d.il_ptr, d.il_src, d.il_slot, down ? op.o[l - 1] : nullptr,
           down ? op.Ct[l] : nullptr, d.parent, d.octant, nrhs, d.q, qp, t.tr);
@@ -469,6 +477,18 @@ int nesa_matvec_parts(nesa_ctx *c, const nesa_c128 *x, nesa_c128 *y, int nrhs, i
     ensure_workspace(c, nrhs);
     launch_matvec(c, (const cplx *)x, (cplx *)y, nrhs, parts);
     check_cuda(cudaGetLastError(), "matvec launch");
+  } catch (const Error &e) {
+    set_last_error(e.what);
+    return e.status;
+  }
+  return NESA_OK;
+}
+
+int nesa_device_status(nesa_ctx *c) {
+  if (!c) return NESA_ERR_INVALID_ARG;
+  try {
+    check_cuda(cudaStreamSynchronize(c->stream), "sync");
+    if (tc_take_error(c)) return NESA_ERR_TIMEOUT;
   } catch (const Error &e) {
     set_last_error(e.what);
     return e.status;

@@ -1,0 +1,80 @@
+"""Mixed product with the translations on the tensor cores (tcgen05, BF16 hi/lo).
+
+The error of the product against the FP64 oracle is printed per workload and bounded;
+the bound (5e-5) is derived from the arithmetic: each operand is split into two BF16
+numbers (8 significant bits each), the dropped lo.lo product and the rounding of the lo
+part leave about 2^-16 relative error per product, accumulated in FP32, on the far
+part only (the near part is complex64).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle.nesa import NesaOracle  # noqa: E402
+from workloads import get_config, plane_wave_directions, random_coefficients  # noqa: E402
+
+TOL_TC = 5e-5
+_cache = {}
+
+
+def build(name):
+    import paper_1801_03589_gb300 as nesa
+    if name not in _cache:
+        c = get_config(name)
+        g = nesa.Nesa(c["vertices"], c["triangles"], c["k"], leaf_size=c["leaf_size"], n_levels=c["n_levels"],
+                      precision=nesa.MIXED, translate=nesa.TRANSLATE_TENSOR)
+        _cache[name] = (c, g)
+    return _cache[name]
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("name", ["tiny", "C1", "C1b", "C3a"])
+def test_tensor_product_vs_fp64(name):
+    import paper_1801_03589_gb300 as nesa
+    c, g = build(name)
+    x = torch.from_numpy(random_coefficients(g.n, 1, seed=51)).cuda()
+    yt = g.matvec(x, parts=nesa.PART_ALL | nesa.PART_MIXED).cpu().numpy()[0]
+    y64 = g.matvec(x).cpu().numpy()[0]
+    ytf = g.matvec(x, parts=nesa.PART_FAR | nesa.PART_MIXED).cpu().numpy()[0]
+    yf64 = g.matvec(x, parts=nesa.PART_FAR).cpu().numpy()[0]
+    assert nesa.lib().nesa_device_status(g._h) == nesa.OK
+    e, ef = rel(yt, y64), rel(ytf, yf64)
+    print("%s tensor-core mixed product: rel err vs FP64 product %.2e (far part %.2e)" % (name, e, ef))
+    assert e < TOL_TC and ef < 10 * TOL_TC
+
+
+def test_tensor_product_vs_oracle_rows():
+    import paper_1801_03589_gb300 as nesa
+    c, g = build("C1b")
+    o = NesaOracle(c["vertices"], c["triangles"], c["k"], c["leaf_size"], c["n_levels"])
+    x = random_coefficients(g.n, 1, seed=52)[0]
+    y = g.matvec(torch.from_numpy(x).cuda().view(1, -1), parts=nesa.PART_ALL | nesa.PART_MIXED).cpu().numpy()[0]
+    rows = np.unique(np.linspace(0, g.n - 1, 30).astype(np.int64))
+    e = rel(y[rows], o.matvec_rows(x, rows))
+    print("C1b tensor-core mixed product: rel err vs oracle (30 rows) %.2e" % e)
+    assert e < TOL_TC
+
+
+def test_tensor_multi_rhs_columns_independent():
+    import paper_1801_03589_gb300 as nesa
+    c, g = build("C1b")
+    X = torch.from_numpy(random_coefficients(g.n, 3, seed=53)).cuda()
+    Y = g.matvec(X, parts=nesa.PART_ALL | nesa.PART_MIXED).cpu().numpy()
+    for r in range(3):
+        y1 = g.matvec(X[r:r + 1].contiguous(), parts=nesa.PART_ALL | nesa.PART_MIXED).cpu().numpy()[0]
+        assert rel(Y[r], y1) < 1e-6
+
+
+def test_refined_solve_with_tensor_product():
+    c, g = build("C1b")
+    kh, pol = plane_wave_directions(1, seed=54)
+    B = g.rhs_planewave(kh, pol)
+    x, info = g.solve(B, tol=1e-5, mixed=True, restart=60, inner_tol=1e-3)
+    assert info["converged"] == 1 and info["rel_residual"][0] <= 1e-5
+    r = B - g.matvec(x)
+    assert float(r.abs().pow(2).sum().sqrt() / B.abs().pow(2).sum().sqrt()) <= 1e-5
