@@ -195,16 +195,25 @@ int nesa_rhs_planewave(nesa_ctx *ctx, const double *khat, const nesa_c128 *pol, 
  * NaN/Inf.  Synchronous (the host reads one status word per Arnoldi step).
  * Device workspace: (restart + 3) * N * nrhs complex values, kept by the context.
  */
+#define NESA_PRECOND_NONE 0
+#define NESA_PRECOND_BLOCK_JACOBI 1 /* inverted near-field diagonal blocks, one per home leaf */
+#define NESA_PRECOND_LEARNED 2      /* trained network correction of NESA_PRECOND_OVERLAP (see
+                                       below); NESA_PRECOND_OVERLAP until trained */
+#define NESA_PRECOND_OVERLAP 3      /* overlapping block-Jacobi (restricted additive Schwarz):
+                                       the rows of a home-leaf group of the inverse of the
+                                       near-field block over the functions whose home leaf
+                                       touches the group's leaf (complex64) */
 typedef struct {
   int32_t restart;    /* Krylov dimension m of a cycle */
   int32_t max_iters;  /* total Arnoldi steps (over all inner solves when mixed) */
+  int32_t precond;    /* NESA_PRECOND_*: right preconditioning Z M y = b, x = M y */
   int32_t mixed;      /* 1: FP64 iterative refinement - r = b - Z~ x with the FP64 product,
                          an inner GMRES on the NESA_PART_MIXED product solves for the
                          correction to inner_tol, x += d - until ||r||/||b|| <= tol
                          (context built with NESA_MIXED); Arnoldi and Givens stay FP64 */
   int32_t max_refine; /* refinement steps (default 10) */
   double inner_tol;   /* relative tolerance of each inner solve (default 1e-3) */
-  int32_t reserved[4];
+  int32_t reserved[3];
 } nesa_solve_opts;
 typedef struct {
   int32_t iterations;      /* Arnoldi steps taken */
@@ -219,6 +228,62 @@ typedef struct {
 void nesa_default_solve_opts(nesa_solve_opts *opts);
 int nesa_solve(nesa_ctx *ctx, const nesa_c128 *b_dev, nesa_c128 *x_dev, int nrhs, double tol,
                const nesa_solve_opts *opts, nesa_solve_info *info);
+
+/*
+ * Preconditioners (not in the paper; the solver of Sec. 2 is used with them).
+ *
+ * Block-Jacobi: every RWG function belongs to the leaf holding the centroid of its T+;
+ * the near-field diagonal block of each group is inverted (Gauss-Jordan, partial
+ * pivoting, FP64).
+ *
+ * Overlapping block-Jacobi S: for each group, the extended set E = functions whose home
+ * leaf touches the group's leaf; S r on the group = rows of the group of
+ * (Z^near restricted to E x E)^-1 applied to r restricted to E (LU per group at setup).
+ * Plain block-Jacobi can slow the EFIE down (its small blocks have nearly singular
+ * loop modes); the overlapping one is the fallback of the learned preconditioner.
+ *
+ * Learned: M u = a1 u + a2 (S u) + a3 (S N S u), N = near-field product, with
+ * complex coefficients a per RWG function from a network shared by all functions:
+ * 8 static local features -> tanh 32 -> tanh 32 -> 6 (Re, Im of a1..a3).  Features:
+ * k l, A+/l^2, A-/l^2, Re and Im of Z_mm/|Z_mm|, log(|Z_mm| / mean |Z_mm|), near-row
+ * length / mean, group size / mean (mean over functions).  Weights: W1[32][8], b1[32],
+ * W2[32][32], b2[32], W3[6][32], b3[6] (row-major, 1542 FP32 values, in this order);
+ * the initial weights give a = (0, 1, 0), i.e. S.  Training (GPU kernels: forward,
+ * backward, Adam) minimises L = sum_s |M(u_s) - v_s|^2 / sum_s |v_s|^2 over pairs
+ * u_s = Z~ v_s, v_s the Arnoldi vectors of S-preconditioned GMRES for the training
+ * right-hand sides.  Inference uses an FP16 copy of the weights with FP32 arithmetic.
+ */
+#define NESA_LEARN_PARAMS 1542
+typedef struct {
+  int32_t samples; /* Arnoldi vectors per training right-hand side (default 48) */
+  int32_t steps;   /* Adam steps (default 300) */
+  float lr;        /* Adam learning rate (default 3e-3) */
+  int32_t reserved[5];
+} nesa_learn_opts;
+typedef struct {
+  double loss_initial; /* L with the initial (block-Jacobi) weights */
+  double loss_final;   /* L after training */
+  int32_t samples;     /* training pairs */
+  int32_t steps;
+  double seconds;
+} nesa_learn_info;
+/* Build the block-Jacobi blocks and the features (idempotent; also done on demand). */
+int nesa_precond_setup(nesa_ctx *ctx);
+/* z = M r for kind NESA_PRECOND_BLOCK_JACOBI or NESA_PRECOND_LEARNED (dev, N x nrhs). */
+int nesa_precond_apply(nesa_ctx *ctx, int kind, const nesa_c128 *r_dev, nesa_c128 *z_dev, int nrhs);
+void nesa_default_learn_opts(nesa_learn_opts *opts);
+/* Collect training pairs from b (dev, N x nrhs training right-hand sides) and train. */
+int nesa_precond_train(nesa_ctx *ctx, const nesa_c128 *b_dev, int nrhs, const nesa_learn_opts *opts,
+                       nesa_learn_info *info);
+/* Get (set = 0) or set (set = 1) the NESA_LEARN_PARAMS weights (host FP32).  Setting
+   them marks the learned preconditioner as trained. */
+int nesa_precond_params(nesa_ctx *ctx, int set, float *host_params);
+/* Features of every function (host, N x 8 FP32). */
+int nesa_precond_features(nesa_ctx *ctx, float *host_features);
+/* L and dL/dweights (host, NESA_LEARN_PARAMS FP32; may be NULL) for given pairs u, v
+   (dev, N x nsamples each) with the current weights. */
+int nesa_precond_loss_grad(nesa_ctx *ctx, const nesa_c128 *u_dev, const nesa_c128 *v_dev, int nsamples,
+                           double *loss, float *grad_host);
 
 /*
  * Export internal arrays for tests and tools (host copies).

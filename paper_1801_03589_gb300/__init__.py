@@ -68,8 +68,23 @@ STAGES = ("radiation", "source_transfer", "translation", "near_reception")
 
 
 class SolveOpts(ctypes.Structure):
-    _fields_ = [("restart", ctypes.c_int32), ("max_iters", ctypes.c_int32), ("mixed", ctypes.c_int32),
-                ("max_refine", ctypes.c_int32), ("inner_tol", ctypes.c_double), ("reserved", ctypes.c_int32 * 4)]
+    _fields_ = [("restart", ctypes.c_int32), ("max_iters", ctypes.c_int32), ("precond", ctypes.c_int32),
+                ("mixed", ctypes.c_int32), ("max_refine", ctypes.c_int32), ("inner_tol", ctypes.c_double),
+                ("reserved", ctypes.c_int32 * 3)]
+
+
+class LearnOpts(ctypes.Structure):
+    _fields_ = [("samples", ctypes.c_int32), ("steps", ctypes.c_int32), ("lr", ctypes.c_float),
+                ("reserved", ctypes.c_int32 * 5)]
+
+
+class LearnInfo(ctypes.Structure):
+    _fields_ = [("loss_initial", ctypes.c_double), ("loss_final", ctypes.c_double), ("samples", ctypes.c_int32),
+                ("steps", ctypes.c_int32), ("seconds", ctypes.c_double)]
+
+
+PRECOND_NONE, PRECOND_BLOCK_JACOBI, PRECOND_LEARNED, PRECOND_OVERLAP = 0, 1, 2, 3
+LEARN_PARAMS = 1542
 
 
 class SolveInfo(ctypes.Structure):
@@ -106,6 +121,14 @@ def lib():
             "nesa_profile_read": (I, [P, P]),
             "nesa_default_solve_opts": (None, [P]),
             "nesa_solve": (I, [P, P, P, I, D, P, P]),
+            "nesa_device_status": (I, [P]),
+            "nesa_precond_setup": (I, [P]),
+            "nesa_precond_apply": (I, [P, I, P, P, I]),
+            "nesa_default_learn_opts": (None, [P]),
+            "nesa_precond_train": (I, [P, P, I, P, P]),
+            "nesa_precond_params": (I, [P, I, P]),
+            "nesa_precond_features": (I, [P, P]),
+            "nesa_precond_loss_grad": (I, [P, P, P, I, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -222,8 +245,47 @@ class Nesa:
         _check(lib().nesa_rhs_planewave(self._h, kh.ctypes.data, pl.ctypes.data, nrhs, po))
         return out
 
+    # ------------------------------------------------------------ preconditioners
+    def precond_apply(self, r, kind=PRECOND_BLOCK_JACOBI):
+        import torch
+        r, pr, nrhs = _dev_ptr(r, self.n, "r")
+        z = torch.empty_like(r)
+        _check(lib().nesa_precond_apply(self._h, kind, pr, z.data_ptr(), nrhs))
+        return z
+
+    def precond_train(self, b, samples=48, steps=300, lr=3e-3):
+        b, pb, nrhs = _dev_ptr(b, self.n, "b")
+        o = LearnOpts()
+        lib().nesa_default_learn_opts(ctypes.byref(o))
+        o.samples, o.steps, o.lr = int(samples), int(steps), float(lr)
+        i = LearnInfo()
+        _check(lib().nesa_precond_train(self._h, pb, nrhs, ctypes.byref(o), ctypes.byref(i)))
+        return dict(loss_initial=i.loss_initial, loss_final=i.loss_final, samples=i.samples, steps=i.steps,
+                    seconds=i.seconds)
+
+    def precond_params(self, values=None):
+        """Get the learned weights (values None) or set them (marks the network trained)."""
+        a = np.zeros(LEARN_PARAMS, np.float32) if values is None else np.ascontiguousarray(values, np.float32)
+        _check(lib().nesa_precond_params(self._h, 0 if values is None else 1, a.ctypes.data))
+        return a
+
+    def precond_features(self):
+        a = np.zeros((self.n, 8), np.float32)
+        _check(lib().nesa_precond_features(self._h, a.ctypes.data))
+        return a
+
+    def precond_loss_grad(self, u, v):
+        u, pu, ns = _dev_ptr(u, self.n, "u")
+        v, pv, ns2 = _dev_ptr(v, self.n, "v")
+        if ns != ns2:
+            raise ValueError("u and v differ in sample count")
+        loss = ctypes.c_double()
+        g = np.zeros(LEARN_PARAMS, np.float32)
+        _check(lib().nesa_precond_loss_grad(self._h, pu, pv, ns, ctypes.byref(loss), g.ctypes.data))
+        return loss.value, g
+
     def solve(self, b, tol, x=None, restart=50, max_iters=1000, check=True, mixed=False, max_refine=10,
-              inner_tol=1e-3):
+              inner_tol=1e-3, precond=PRECOND_NONE):
         """Restarted GMRES on the device for Z~ x = b (b: [nrhs, N] complex128 CUDA).
         mixed=True: FP64 iterative refinement around GMRES on the low-precision product.
         Returns (x, info dict).  With check=False a non-converged solve returns instead
@@ -237,6 +299,7 @@ class Nesa:
         lib().nesa_default_solve_opts(ctypes.byref(o))
         o.restart, o.max_iters = int(restart), int(max_iters)
         o.mixed, o.max_refine, o.inner_tol = int(bool(mixed)), int(max_refine), float(inner_tol)
+        o.precond = int(precond)
         i = SolveInfo()
         st = lib().nesa_solve(self._h, pb, px, nrhs, float(tol), ctypes.byref(o), ctypes.byref(i))
         info = dict(status=st, iterations=i.iterations, restarts=i.restarts, converged=i.converged,

@@ -690,6 +690,7 @@ static void free_ctx(nesa_ctx *c) {
   if (!c) return;
   nesa_free_solve_work(c);
   tc_free(c);
+  precond_free(c);
   for (void *p : c->allocs) cudaFree(p);
   for (auto &p : c->pending) {
     cudaEventDestroy(p.a);

@@ -117,6 +117,7 @@ struct nesa_ctx {
   nesa_profile prof{};
   void *solve_work = nullptr;    // GMRES workspace (nesa_solve.cu)
   void *tc_state = nullptr;      // tensor-core translation state (nesa_tc.cu)
+  void *precond = nullptr;       // preconditioner state (nesa_precond.cu)
   bool tc_enabled = false;
   std::vector<void *> allocs;    // every device allocation owned by the context
 };
@@ -135,6 +136,10 @@ void tc_translate_level(nesa_ctx *c, int l, const cplxf *s, cplxf *o, const cplx
                         int tr, int ntile, int threads);
 int tc_take_error(nesa_ctx *c);
 void tc_free(nesa_ctx *c);
+// preconditioners (nesa_precond.cu): z = M r
+void precond_ready(nesa_ctx *c, int kind);
+void precond_apply(nesa_ctx *c, int kind, const cplx *r, cplx *z, int nrhs);
+void precond_free(nesa_ctx *c);
 int ensure_workspace(nesa_ctx *c, int nrhs);
 }  // namespace nesa
 void nesa_free_solve_work(nesa_ctx *c);

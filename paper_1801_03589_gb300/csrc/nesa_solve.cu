@@ -42,6 +42,8 @@ struct SolveWork {
   cplx *ro = nullptr;      // [nrhs][n] FP64 residual of the refinement loop
   cplx *dx = nullptr;      // [nrhs][n] correction from the inner solve
   double *onrm = nullptr;  // [nrhs] norms of the refinement loop
+  cplx *zt = nullptr;      // [nrhs][n] preconditioned vector M v_j / V y
+  cplx *zt2 = nullptr;     // [nrhs][n] M (V y)
 };
 
 static const int kChunk = 2048;  // vector elements per partial-sum block
@@ -174,6 +176,14 @@ __global__ void k_scale(cplx *dst, const cplx *src, const double *scale, int64_t
   }
 }
 
+// x += d
+__global__ void k_add(cplx *x, const cplx *d, int64_t total) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    cplx a = x[e], b = d[e];
+    x[e] = make_double2(a.x + b.x, a.y + b.y);
+  }
+}
+
 // r = b - r   (r holds Z~ x on entry)
 __global__ void k_residual(cplx *r, const cplx *b, int64_t total) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
@@ -285,7 +295,7 @@ static SolveWork *get_work(nesa_ctx *c, int m, int nrhs) {
   SolveWork *W = (SolveWork *)c->solve_work;
   if (W->m >= m && W->nrhs >= nrhs) return W;
   void *old[] = {W->V, W->w, W->r, W->H, W->h, W->cs, W->sn, W->g, W->y, W->part, W->nrm, W->bnorm, W->steps,
-                 W->state, W->est, W->ro, W->dx, W->onrm};
+                 W->state, W->est, W->ro, W->dx, W->onrm, W->zt, W->zt2};
   for (void *p : old) dfree(c, p);
   if (W->h_state) cudaFreeHost(W->h_state);
   if (W->h_est) cudaFreeHost(W->h_est);
@@ -309,6 +319,8 @@ static SolveWork *get_work(nesa_ctx *c, int m, int nrhs) {
   W->steps = (int *)dalloc(c, sizeof(int) * nrhs);
   W->state = (int *)dalloc(c, sizeof(int) * nrhs);
   W->est = (double *)dalloc(c, sizeof(double) * nrhs);
+  W->zt = (cplx *)dalloc(c, sizeof(cplx) * (size_t)nrhs * n);
+  W->zt2 = (cplx *)dalloc(c, sizeof(cplx) * (size_t)nrhs * n);
   W->ro = (cplx *)dalloc(c, sizeof(cplx) * (size_t)nrhs * n);
   W->dx = (cplx *)dalloc(c, sizeof(cplx) * (size_t)nrhs * n);
   W->onrm = (double *)dalloc(c, sizeof(double) * nrhs);
@@ -330,8 +342,9 @@ void nesa_free_solve_work(nesa_ctx *c) {
 // failures.  Returns NESA_OK, NESA_ERR_NOT_CONVERGED or NESA_ERR_NUMERIC; adds to the
 // counters of I and fills its true residuals.
 static int gmres_run(nesa_ctx *c, const cplx *b, cplx *x, int nrhs, double tol, int m, int max_iters, int parts,
-                     nesa_solve_info &I) {
+                     int precond, nesa_solve_info &I) {
   int status = NESA_OK;
+  if (precond != NESA_PRECOND_NONE) precond_ready(c, precond);
   {
     SolveWork *W = get_work(c, m, nrhs);
     ensure_workspace(c, nrhs);
@@ -352,7 +365,6 @@ static int gmres_run(nesa_ctx *c, const cplx *b, cplx *x, int nrhs, double tol, 
       norms(W->r, W->nrm);
       k_cycle_start<<<(nrhs + 63) / 64, 64, 0, st>>>(W->g, m, W->nrm, W->bnorm, W->steps, W->state, W->est, tol,
                                                      nrhs);
-      k_scale<<<vgrid, 256, 0, st>>>(W->V, W->r, W->nrm, n, nrhs);
       check_cuda(cudaMemcpyAsync(W->h_state, W->state, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st), "state");
       check_cuda(cudaMemcpyAsync(W->h_est, W->est, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st), "est");
       check_cuda(cudaStreamSynchronize(st), "cycle start");
@@ -361,12 +373,18 @@ static int gmres_run(nesa_ctx *c, const cplx *b, cplx *x, int nrhs, double tol, 
       for (int r = 0; r < nrhs; ++r)
         if (W->h_state[r] == 3) status = NESA_ERR_NUMERIC;
       if (!running || status != NESA_OK || total >= max_iters) break;
+      k_scale<<<vgrid, 256, 0, st>>>(W->V, W->r, W->nrm, n, nrhs);
       I.restarts += total > 0;
       int j = 0;
       for (; j < m && total < max_iters; ++j) {
         cplx *Vj = W->V + (size_t)j * nrhs * n;
         cplx *Vn = W->V + (size_t)(j + 1) * nrhs * n;
-        launch_matvec(c, Vj, W->w, nrhs, parts);
+        if (precond != NESA_PRECOND_NONE) {  // right preconditioning: w = Z (M v_j)
+          precond_apply(c, precond, Vj, W->zt, nrhs);
+          launch_matvec(c, W->zt, W->w, nrhs, parts);
+        } else {
+          launch_matvec(c, Vj, W->w, nrhs, parts);
+        }
         I.matvecs += 1;
         // CGS2: two rounds of projection onto V_0..V_j
         for (int pass = 0; pass < 2; ++pass) {
@@ -390,7 +408,14 @@ static int gmres_run(nesa_ctx *c, const cplx *b, cplx *x, int nrhs, double tol, 
       }
       // x += V y for the steps each column took in this cycle
       k_backsolve<<<(nrhs + 63) / 64, 64, 0, st>>>(W->y, W->H, W->g, W->steps, m, nrhs);
-      k_update_x<<<vgrid, 256, 0, st>>>(x, W->V, W->y, m, W->steps, n, nrhs);
+      if (precond != NESA_PRECOND_NONE) {  // x += M (V y)
+        check_cuda(cudaMemsetAsync(W->zt, 0, sizeof(cplx) * (size_t)nrhs * n, st), "zt");
+        k_update_x<<<vgrid, 256, 0, st>>>(W->zt, W->V, W->y, m, W->steps, n, nrhs);
+        precond_apply(c, precond, W->zt, W->zt2, nrhs);
+        k_add<<<blocks_for((int64_t)nrhs * n, 256, 4096), 256, 0, st>>>(x, W->zt2, (int64_t)nrhs * n);
+      } else {
+        k_update_x<<<vgrid, 256, 0, st>>>(x, W->V, W->y, m, W->steps, n, nrhs);
+      }
       // true residual
       launch_matvec(c, x, W->r, nrhs, parts);
       I.matvecs += 1;
@@ -461,7 +486,7 @@ static int refine_run(nesa_ctx *c, const cplx *b, cplx *x, int nrhs, double tol,
     nesa_solve_info Ii;
     std::memset(&Ii, 0, sizeof(Ii));
     int si = gmres_run(c, W->ro, W->dx, nrhs, o.inner_tol, o.restart, o.max_iters - I.iterations,
-                       NESA_PART_ALL | NESA_PART_MIXED, Ii);
+                       NESA_PART_ALL | NESA_PART_MIXED, o.precond, Ii);
     I.iterations += Ii.iterations;
     I.matvecs += Ii.matvecs;
     I.restarts += Ii.restarts;
@@ -483,6 +508,32 @@ static int refine_run(nesa_ctx *c, const cplx *b, cplx *x, int nrhs, double tol,
   return status;
 }
 
+// Arnoldi vectors v_0..v_{ns-1} of block-Jacobi-preconditioned GMRES (one cycle of ns
+// steps from x0 = 0) for each of the nrhs right-hand sides, into V [nrhs * ns][n]
+// (right-hand side major).  Columns past a breakdown are zero.
+int nesa_collect_krylov(nesa_ctx *c, const cplx *b, int nrhs, int ns, cplx *V) {
+  SolveWork *W = get_work(c, ns, nrhs);
+  nesa_solve_info I;
+  std::memset(&I, 0, sizeof(I));
+  int st = gmres_run(c, b, W->dx, nrhs, 1e-300, ns, ns, NESA_PART_ALL, NESA_PRECOND_OVERLAP, I);
+  if (st == NESA_ERR_NUMERIC) return st;
+  std::vector<int> steps(nrhs);
+  check_cuda(cudaMemcpy(steps.data(), W->steps, sizeof(int) * nrhs, cudaMemcpyDeviceToHost), "steps");
+  const int64_t n = c->n;
+  for (int r = 0; r < nrhs; ++r)
+    for (int j = 0; j < ns; ++j) {
+      cplx *dst = V + ((size_t)r * ns + j) * n;
+      if (j <= steps[r] && j < ns)
+        check_cuda(cudaMemcpyAsync(dst, W->V + ((size_t)j * nrhs + r) * n, sizeof(cplx) * n,
+                                   cudaMemcpyDeviceToDevice, c->stream),
+                   "krylov copy");
+      else
+        check_cuda(cudaMemsetAsync(dst, 0, sizeof(cplx) * n, c->stream), "krylov zero");
+    }
+  check_cuda(cudaStreamSynchronize(c->stream), "krylov");
+  return NESA_OK;
+}
+
 extern "C" {
 
 void nesa_default_solve_opts(nesa_solve_opts *o) {
@@ -502,7 +553,8 @@ int nesa_solve(nesa_ctx *c, const nesa_c128 *b_dev, nesa_c128 *x_dev, int nrhs, 
   nesa_default_solve_opts(&o);
   if (opts) o = *opts;
   if (o.restart < 1 || o.restart > 1000 || o.max_iters < 1 || (o.mixed != 0 && o.mixed != 1) ||
-      o.max_refine < 0 || !(o.inner_tol > 0.0 && o.inner_tol < 1.0))
+      o.max_refine < 0 || !(o.inner_tol > 0.0 && o.inner_tol < 1.0) || o.precond < NESA_PRECOND_NONE ||
+      o.precond > NESA_PRECOND_OVERLAP)
     return NESA_ERR_INVALID_ARG;
   auto t0 = std::chrono::steady_clock::now();
   nesa_solve_info I;
@@ -512,7 +564,8 @@ int nesa_solve(nesa_ctx *c, const nesa_c128 *b_dev, nesa_c128 *x_dev, int nrhs, 
     if (o.mixed) {
       status = refine_run(c, (const cplx *)b_dev, (cplx *)x_dev, nrhs, tol, o, I);
     } else {
-      status = gmres_run(c, (const cplx *)b_dev, (cplx *)x_dev, nrhs, tol, o.restart, o.max_iters, NESA_PART_ALL, I);
+      status = gmres_run(c, (const cplx *)b_dev, (cplx *)x_dev, nrhs, tol, o.restart, o.max_iters, NESA_PART_ALL,
+                         o.precond, I);
       I.fp64_matvecs = I.matvecs;
     }
   } catch (const Error &e) {
