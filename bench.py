@@ -309,30 +309,103 @@ def run_ours(args, world, rank, local):
         g.matvec_host_ptr(xh.data_ptr(), yh.data_ptr(), nrhs, mixed)
     e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps)
 
-    # one solve to 1e-5: FP64 refinement around GMRES on the mixed product
+    # solves to 1e-5 (x-polarised plane wave along +z): FP64 refinement around GMRES(100)
+    # on the mixed product (inner tolerance 1e-2), without and with the overlapping
+    # block-Jacobi preconditioner; optionally the plain FP64 solve for comparison
     solve = None
     if not args.no_solve:
         b = g.rhs_planewave([[0.0, 0.0, 1.0]], [[1.0, 0.0, 0.0]])
         torch.cuda.synchronize()
         barrier()
-        xs, si = g.solve(b, tol=1e-5, mixed=True, restart=100, max_iters=4000, inner_tol=1e-2, check=False)
-        solve = {"tol": 1e-5, "seconds": max_over_ranks(si["seconds"]), "status": si["status"],
-                 "iterations": si["iterations"], "refinements": si["refinements"],
-                 "fp64_products": si["fp64_matvecs"], "true_rel_residual": si["rel_residual"][0],
-                 "method": "FP64 iterative refinement, inner GMRES(100) on the mixed product to 1e-2, "
-                           "x-polarised plane wave along +z"}
+
+        def one(**kw):
+            _, si = g.solve(b, tol=1e-5, restart=100, max_iters=4000, check=False, **kw)
+            return {"seconds": max_over_ranks(si["seconds"]), "status": si["status"],
+                    "iterations": si["iterations"], "refinements": si["refinements"],
+                    "fp64_products": si["fp64_matvecs"], "true_rel_residual": si["rel_residual"][0]}
+
+        t0 = time.perf_counter()
+        g.precond_apply(b, nesa.PRECOND_OVERLAP)
+        torch.cuda.synchronize()
+        setup_s = time.perf_counter() - t0
+        solve = {"tol": 1e-5,
+                 "mixed_none": one(mixed=True, inner_tol=1e-2),
+                 "mixed_overlap": one(mixed=True, inner_tol=1e-2, precond=nesa.PRECOND_OVERLAP),
+                 "overlap_setup_seconds": setup_s,
+                 "method": "FP64 iterative refinement, inner GMRES(100) on the mixed product to 1e-2; overlapping "
+                           "block-Jacobi = near-field restricted additive Schwarz over touching leaves"}
+        if args.fp64_solve:
+            solve["fp64_none"] = one()
+
+    # batched sweep: three meshes of uneven size with 64 right-hand sides each, one CUDA
+    # graph launch per pass over all of them (mixed product, autotuned tile widths)
+    batch = None
+    if not args.no_batch:
+        names = ("C3a", "C3b", "C3c")
+        t0 = time.perf_counter()
+        members = []
+        for nm in names:
+            cf = get_config(nm)
+            members.append(nesa.Nesa(cf["vertices"], cf["triangles"], cf["k"], leaf_size=cf["leaf_size"],
+                                     n_levels=cf["n_levels"], precision=nesa.MIXED,
+                                     translate=nesa.TRANSLATE_TENSOR))
+        bx = [torch.from_numpy(random_coefficients(m.n, 64, seed=300 + i)).cuda() for i, m in enumerate(members)]
+        by = [torch.empty_like(v) for v in bx]
+        bt = nesa.Batch(members, bx, by, parts=mixed)
+        build_s = time.perf_counter() - t0
+        for _ in range(max(3, args.warmup)):
+            bt.launch(stream)
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            bt.launch(stream)
+        e1.record(stream)
+        stream.synchronize()
+        pass_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+        batch = {"workload": "sphere r=2 (30,720 RWG), 3:1 spheroid (60,750 RWG), 4x4 plate (42,960 RWG); "
+                             "64 right-hand sides each; mixed product",
+                 "pass_ms": pass_ms, "matvec_per_s": world * 3 * 64 * 1e3 / pass_ms,
+                 "graph_kernel_nodes": bt.kernel_nodes, "launches_per_pass": 1, "build_and_capture_s": build_s,
+                 "tile_n": [{l: t["tile_n"] for l, t in m.tuning().items()} for m in members]}
+        bt.close()
 
     if rank != 0:
         if pg is not None:
             pg.destroy_process_group()
         return 0
 
-    # roofline of the dominant stage of the mixed product (largest device time)
-    dom = max(prof_mx, key=lambda k: prof_mx[k]["ms"])
-    d = prof_mx[dom]
-    achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
-    launches = sum(v["launches"] for v in prof_mx.values())
+    # roofline of the dominant kernel of the mixed product (largest device time); the
+    # tensor-core GEMM is timed alone (stage 4), the rest of the translation stage is
+    # its split and reduction kernels
     peaks = _peaks()
+    gemm = prof_mx["translation_tensor_gemm"]
+    rest = {"ms": prof_mx["translation"]["ms"] - gemm["ms"], "flops": 0.0,
+            "bytes": prof_mx["translation"]["bytes"] - gemm["bytes"]}
+    kernels = {"k_tc_translate": (gemm, "tensor"), "k_near_receive<float2>": (prof_mx["near_reception"], "hbm"),
+               "k_upward<float2>": (prof_mx["source_transfer"], "alu"),
+               "k_radiate<float2>": (prof_mx["radiation"], "hbm"),
+               "k_split_s + k_pair_reduce": (rest, "hbm")}
+    kernel = max(kernels, key=lambda k: kernels[k][0]["ms"])
+    d, bound = kernels[kernel]
+    sec = d["ms"] * 1e-3
+    if bound == "tensor":
+        roof = {"bound": "tensor", "achieved": d["flops"] / sec / 1e12, "unit": "TFLOP/s",
+                "peak": peaks.get("bf16_tflops_sustained", 1700.0),
+                "peak_note": "BF16 dense, sustained, measured (MEASURED_PEAKS.json); achieved counts 8 flops per "
+                             "complex multiply-add of the translations, the BF16 hi/lo split executes 3x that"}
+    elif bound == "hbm":
+        roof = {"bound": "hbm", "achieved": d["bytes"] / sec / 1e9, "unit": "GB/s",
+                "peak": peaks.get("hbm_gbs", 6800.0), "peak_note": "HBM copy bandwidth, measured"}
+    else:
+        roof = {"bound": "alu", "achieved": d["flops"] / sec / 1e12, "unit": "TFLOP/s", "peak": FP32_PEAK_TFLOPS,
+                "peak_note": "FP32: 152 SMs x 256 flop/clk x 2070 MHz (derived)"}
+    roof.update({"kernel": kernel, "frac": roof["achieved"] / roof["peak"], "traffic": None,
+                 "ms_per_step": d["ms"] / args.steps})
+    # kernels launched: the tensor translation is three kernels per level
+    launches = (prof_mx["radiation"]["launches"] + prof_mx["source_transfer"]["launches"] +
+                prof_mx["near_reception"]["launches"] + prof_mx["translation"]["launches"] + 2 * gemm["launches"])
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -342,8 +415,6 @@ def run_ours(args, world, rank, local):
         cpu = {"value": 1.0 / sec, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
                "seconds_per_matvec": sec, "stage_seconds": parts}
 
-    kernel = {"translation": "k_tc_translate (+k_split_s, k_pair_reduce)", "near_reception": "k_near_receive<float2>",
-              "radiation": "k_radiate<float2>", "source_transfer": "k_upward<float2>"}[dom]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms_mx, "higher_is_better": True, "scaling": "weak",
@@ -363,11 +434,7 @@ def run_ours(args, world, rank, local):
         "e2e": {"value": world * nrhs * 1e3 / e2e_ms, "unit": UNIT, "h2d_bytes_per_step": 16 * n * nrhs,
                 "d2h_bytes_per_step": 16 * n * nrhs, "ms_per_step": e2e_ms},
         "gpu_launches": launches,
-        "roofline": {"kernel": kernel, "stage": dom, "bound": "alu", "achieved": achieved,
-                     "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                     "traffic": None,
-                     "peak_note": "FP32: 152 SMs x 256 flop/clk x 2070 MHz (derived; MEASURED_PEAKS.json has "
-                                  "HBM %s GB/s and BF16 only)" % peaks.get("hbm_gbs")},
+        "roofline": roof,
         "stages": _stages(prof_mx, args.steps),
         "fp64": {"value": world * nrhs * 1e3 / ms64, "unit": UNIT, "ms_per_step": ms64, "dtype": "f64",
                  "stages": _stages(prof64, args.steps),
@@ -378,6 +445,7 @@ def run_ours(args, world, rank, local):
                               / FP64_PEAK_TFLOPS}},
         "mixed_vs_fp64": ms64 / ms_mx,
         "solve": solve,
+        "batch": batch,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line))
@@ -394,6 +462,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--fp64-solve", action="store_true", help="also time the plain FP64 solve (about 2 minutes)")
     ap.add_argument("--workload", default=CONFIG, help="workload name (smaller ones are for profiling runs)")
     args = ap.parse_args()
     world, rank, local = dist_setup()

@@ -303,10 +303,11 @@ int nesa_export(const nesa_ctx *ctx, int which, void *host_buf, size_t bytes);
  * since the last read to the totals and returns them.  Stages:
  *   0 radiation (Eq. 10)   1 source transfer (Eq. 11)
  *   2 translation + potential transfer (Eqs. 12-13)   3 near field + reception (Eqs. 9, 14)
+ *   4 the tensor-core GEMM launches alone (part of stage 2, NESA_TRANSLATE_TENSOR)
  * flops and bytes are the algorithmic FP64 flops (8 per complex multiply-add) and the
  * bytes of operator data and vectors each launch must touch at least once.
  */
-#define NESA_STAGES 4
+#define NESA_STAGES 5
 typedef struct {
   int64_t launches[NESA_STAGES];
   double ms[NESA_STAGES];
@@ -342,6 +343,34 @@ int nesa_profile_read(nesa_ctx *ctx, nesa_profile *out);
  */
 #define NESA_NOALLOC_SCRATCH_BYTES (32u << 20)
 int nesa_matvec_noalloc(nesa_ctx *ctx, const nesa_c128 *x_dev, nesa_c128 *y_dev, int nrhs);
+
+/*
+ * Batched passes over several operators (meshes of uneven size), each with its own
+ * right-hand sides: one CUDA graph holds the products of all members as independent
+ * branches, and one launch runs a pass (y_i = Z~_i x_i for every member i).
+ *   ctxs[n], x_dev[n], y_dev[n], nrhs[n]   members and their buffers (dev, N_i x nrhs_i;
+ *                                          bound into the graph: keep them alive)
+ *   parts                                  NESA_PART_* bits as in nesa_matvec_parts
+ * nesa_batch_create runs every product once eagerly (allocations, tile tuning), then
+ * captures the kernels; it is synchronous.  A member context must not be destroyed or
+ * rebuilt while the batch exists, and the batch must not run concurrently with other
+ * work on its members.  nesa_batch_launch is asynchronous on `stream`.
+ */
+typedef struct nesa_batch nesa_batch;
+int nesa_batch_create(nesa_ctx *const *ctxs, int n, const nesa_c128 *const *x_dev, nesa_c128 *const *y_dev,
+                      const int *nrhs, int parts, nesa_batch **out);
+int nesa_batch_launch(nesa_batch *batch, void *cuda_stream);
+/* number of kernel nodes in the batch's graph */
+int nesa_batch_kernels(const nesa_batch *batch, int64_t *kernel_nodes);
+void nesa_batch_destroy(nesa_batch *batch);
+
+/*
+ * Tile widths (64, 128 or 256 columns) of the tensor-core translation GEMM chosen by the
+ * autotuner for each level (0 above l0 or without NESA_TRANSLATE_TENSOR), and the times
+ * it measured (ms per launch for widths 64, 128, 256; [level][3]).  Host arrays of
+ * NESA_MAX_LEVELS and 3 * NESA_MAX_LEVELS entries.
+ */
+int nesa_get_tuning(nesa_ctx *ctx, int32_t *tile_n, float *ms);
 
 /*
  * Device-side status of the context's kernels since the last call: NESA_OK, or

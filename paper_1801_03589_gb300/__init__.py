@@ -60,11 +60,11 @@ class Info(ctypes.Structure):
 
 
 class Profile(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_int64 * 4), ("ms", ctypes.c_double * 4), ("flops", ctypes.c_double * 4),
-                ("bytes", ctypes.c_double * 4)]
+    _fields_ = [("launches", ctypes.c_int64 * 5), ("ms", ctypes.c_double * 5), ("flops", ctypes.c_double * 5),
+                ("bytes", ctypes.c_double * 5)]
 
 
-STAGES = ("radiation", "source_transfer", "translation", "near_reception")
+STAGES = ("radiation", "source_transfer", "translation", "near_reception", "translation_tensor_gemm")
 
 
 class SolveOpts(ctypes.Structure):
@@ -129,6 +129,11 @@ def lib():
             "nesa_precond_params": (I, [P, I, P]),
             "nesa_precond_features": (I, [P, P]),
             "nesa_precond_loss_grad": (I, [P, P, P, I, P, P]),
+            "nesa_batch_create": (I, [P, I, P, P, P, I, P]),
+            "nesa_batch_launch": (I, [P, P]),
+            "nesa_batch_kernels": (I, [P, P]),
+            "nesa_batch_destroy": (None, [P]),
+            "nesa_get_tuning": (I, [P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -170,6 +175,45 @@ def _dev_ptr(t, n, what):
     if t.shape[-1] != n:
         raise ValueError("%s has %d columns, expected %d" % (what, t.shape[-1], n))
     return t, t.data_ptr(), t.shape[0]
+
+
+class Batch:
+    """One CUDA graph holding the products of several operators; launch() runs a pass."""
+
+    def __init__(self, members, xs, ys, parts=PART_ALL):
+        n = len(members)
+        self._keep = (list(members), list(xs), list(ys))
+        ctxs = (ctypes.c_void_p * n)(*[m._h.value for m in members])
+        xp = (ctypes.c_void_p * n)()
+        yp = (ctypes.c_void_p * n)()
+        nr = (ctypes.c_int * n)()
+        for i, (m, x, y) in enumerate(zip(members, xs, ys)):
+            x, px, nrhs = _dev_ptr(x, m.n, "x")
+            y, py, nr2 = _dev_ptr(y, m.n, "y")
+            if nr2 != nrhs:
+                raise ValueError("x and y differ in nrhs")
+            xp[i], yp[i], nr[i] = px, py, nrhs
+        h = ctypes.c_void_p()
+        _check(lib().nesa_batch_create(ctxs, n, xp, yp, nr, parts, ctypes.byref(h)))
+        self._h = h
+        k = ctypes.c_int64()
+        _check(lib().nesa_batch_kernels(h, ctypes.byref(k)))
+        self.kernel_nodes = k.value
+
+    def launch(self, stream=None):
+        handle = getattr(stream, "cuda_stream", stream)
+        _check(lib().nesa_batch_launch(self._h, ctypes.c_void_p(handle)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().nesa_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
 
 
 class Nesa:
@@ -318,6 +362,14 @@ class Nesa:
         _check(lib().nesa_profile_read(self._h, ctypes.byref(p)))
         return {name: dict(launches=p.launches[i], ms=p.ms[i], flops=p.flops[i], bytes=p.bytes[i])
                 for i, name in enumerate(STAGES)}
+
+    def tuning(self):
+        """Tile width chosen per level by the autotuner and the measured times (ms) for
+        widths 64, 128, 256."""
+        tn = (ctypes.c_int32 * MAX_LEVELS)()
+        ms = (ctypes.c_float * (3 * MAX_LEVELS))()
+        _check(lib().nesa_get_tuning(self._h, tn, ms))
+        return {l: dict(tile_n=tn[l], ms=list(ms[3 * l:3 * l + 3])) for l in range(MAX_LEVELS) if tn[l]}
 
     def export_point_leaf(self):
         a = np.empty((self.info()["n_points"], 3), np.int32)

@@ -119,6 +119,7 @@ struct nesa_ctx {
   void *tc_state = nullptr;      // tensor-core translation state (nesa_tc.cu)
   void *precond = nullptr;       // preconditioner state (nesa_precond.cu)
   bool tc_enabled = false;
+  bool autotune = true;          // tune the GEMM tile width at the first product per chunk size
   std::vector<void *> allocs;    // every device allocation owned by the context
 };
 
@@ -130,12 +131,15 @@ void check_cuda(cudaError_t e, const char *what);
 void launch_matvec(nesa_ctx *c, const cplx *x, cplx *y, int nrhs, int parts);
 // converted copies of the operator for the mixed-precision product
 void build_mixed(nesa_ctx *c);
+// an event from the context's pool (stage timing)
+cudaEvent_t take_event(nesa_ctx *c);
 // tensor-core translations of the mixed product (nesa_tc.cu)
 void tc_build(nesa_ctx *c);
 void tc_translate_level(nesa_ctx *c, int l, const cplxf *s, cplxf *o, const cplxf *op, const cplxf *Ct, int nrhs,
                         int tr, int ntile, int threads);
 int tc_take_error(nesa_ctx *c);
 void tc_free(nesa_ctx *c);
+void tc_tuning(nesa_ctx *c, int32_t *tn, float *ms);
 // preconditioners (nesa_precond.cu): z = M r
 void precond_ready(nesa_ctx *c, int kind);
 void precond_apply(nesa_ctx *c, int kind, const cplx *r, cplx *z, int nrhs);

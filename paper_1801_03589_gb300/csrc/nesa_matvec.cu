@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(256) k_near_receive(cplx *__restrict__ y, cons
 static inline unsigned grid_for(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
 // Stage timing: an event before and after a launch when profiling is on.
-static cudaEvent_t take_event(nesa_ctx *c) {
+cudaEvent_t take_event(nesa_ctx *c) {
   if (!c->event_pool.empty()) {
     cudaEvent_t e = c->event_pool.back();
     c->event_pool.pop_back();

@@ -22,6 +22,9 @@ struct TcLevel {
   std::vector<int32_t> h_slot_npairs;
   // per-nrhs state
   int nrhs = 0;
+  int tn = 128;          // column-tile width of the GEMM (autotuned)
+  int tuned_nrhs = 0;    // number of right-hand sides the width was tuned for
+  float tune_ms[3] = {0, 0, 0};  // measured times for widths 64, 128, 256
   tc::Work *work = nullptr;
   int64_t nwork = 0;
   __nv_bfloat16 *s_hi = nullptr, *s_lo = nullptr;  // [nbox][4 nrhs][kp]
@@ -48,7 +51,7 @@ __global__ void k_prep_A(__nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo, const cplx *D
     const int64_t slot = rest / nmt;
     // inverse of tc::tile_offset
     const int b = 2 * t;
-    const int kgrp = b / tc::LBO, rem = b % tc::LBO;
+    const int kgrp = b / tc::LBO_A, rem = b % tc::LBO_A;
     const int rgrp = rem / tc::SBO, rem2 = rem % tc::SBO;
     const int m = mt * tc::TM + rgrp * 8 + rem2 / 16;
     const int k = kc * tc::TK + kgrp * 8 + (rem2 % 16) / 2;
@@ -70,13 +73,15 @@ __global__ void k_prep_A(__nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo, const cplx *D
 }
 
 // s (complex64, [box][ccol][q]) -> hi/lo planes [box][ccol][kp] of [Re; Im; 0]
-__global__ void k_split_s(__nv_bfloat16 *s_hi, __nv_bfloat16 *s_lo, const cplxf *s, int64_t ncolumns, int q,
-                          int kp) {
-  const int64_t total = ncolumns * kp;
+// (columns col0 .. col0+cchunk-1 of every box; s has ctotal columns per box)
+__global__ void k_split_s(__nv_bfloat16 *s_hi, __nv_bfloat16 *s_lo, const cplxf *s, int64_t nbox, int ctotal,
+                          int col0, int cchunk, int q, int kp) {
+  const int64_t total = nbox * cchunk * (int64_t)kp;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int k = (int)(idx % kp);
-    const int64_t col = idx / kp;
+    const int64_t oc = idx / kp;
+    const int64_t col = (oc / cchunk) * ctotal + col0 + oc % cchunk;
     float v = 0.0f;
     if (k < q)
       v = s[col * q + k].x;
@@ -88,12 +93,13 @@ __global__ void k_split_s(__nv_bfloat16 *s_hi, __nv_bfloat16 *s_lo, const cplxf 
   }
 }
 
-// o_a = C^T o_P (Eq. 13) + sum of the translated columns of a's pairs (Eq. 12)
+// o_a = C^T o_P (Eq. 13) + sum of the translated columns of a's pairs (Eq. 12), for the
+// right-hand sides r0 .. r0+rc-1 (P holds 4 rc columns per pair; o, op hold 4 nrhs)
 __global__ void __launch_bounds__(512) k_pair_reduce(cplxf *__restrict__ o, const float *__restrict__ P,
                                                      const int32_t *__restrict__ il_ptr, const cplxf *__restrict__ op,
                                                      const cplxf *__restrict__ Ct, const int32_t *__restrict__ parent,
-                                                     const int32_t *__restrict__ octant, int nrhs, int q, int qp,
-                                                     int tr) {
+                                                     const int32_t *__restrict__ octant, int nrhs, int r0, int rc,
+                                                     int q, int qp, int tr) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplxf *col = (cplxf *)smem_raw;
   const int32_t a = blockIdx.x;
@@ -101,9 +107,9 @@ __global__ void __launch_bounds__(512) k_pair_reduce(cplxf *__restrict__ o, cons
   const int ch = threadIdx.x / tr;
   const int i = tile * tr + threadIdx.x % tr;
   const bool active = ch < 4 && i < q;
-  const int ccol = 4 * nrhs;
+  const int ccol = 4 * nrhs, pcol = 4 * rc;
   const int32_t e0 = il_ptr[a], e1 = il_ptr[a + 1];
-  for (int r = 0; r < nrhs; ++r) {
+  for (int r = r0; r < r0 + rc; ++r) {
     cplxf acc = {0.0f, 0.0f};
     if (op) {
       __syncthreads();
@@ -120,7 +126,7 @@ __global__ void __launch_bounds__(512) k_pair_reduce(cplxf *__restrict__ o, cons
     }
     if (active) {
       for (int32_t e = e0; e < e1; ++e) {
-        const float *pc = P + ((int64_t)e * ccol + 4 * r + ch) * 2 * q;
+        const float *pc = P + ((int64_t)e * pcol + 4 * (r - r0) + ch) * 2 * q;
         acc.x += pc[i];
         acc.y += pc[q + i];
       }
@@ -134,6 +140,15 @@ static TcState *state(nesa_ctx *c) { return (TcState *)c->tc_state; }
 void tc_build(nesa_ctx *c) {
   TcState *S = new TcState();
   c->tc_state = S;
+  check_cuda(cudaFuncSetAttribute(tc::k_tc_translate<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  tc::smem_bytes<64>()),
+             "smem attribute");
+  check_cuda(cudaFuncSetAttribute(tc::k_tc_translate<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  tc::smem_bytes<128>()),
+             "smem attribute");
+  check_cuda(cudaFuncSetAttribute(tc::k_tc_translate<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  tc::smem_bytes<256>()),
+             "smem attribute");
   S->err = (int *)dalloc(c, sizeof(int));
   check_cuda(cudaMemset(S->err, 0, sizeof(int)), "tc flag");
   for (int l = c->l0; l <= c->L; ++l) {
@@ -167,17 +182,15 @@ void tc_build(nesa_ctx *c) {
   c->tc_enabled = true;
 }
 
-static void tc_prepare_nrhs(nesa_ctx *c, TcLevel &t, const DevLevel &d, int nrhs) {
-  if (t.nrhs == nrhs) return;
+// work list of the GEMM for a column-tile width tn
+static void tc_make_work(nesa_ctx *c, TcLevel &t, const DevLevel &d, int nrhs, int tn) {
   dfree(c, t.work);
-  dfree(c, t.s_hi);
-  dfree(c, t.s_lo);
-  dfree(c, t.P);
+  t.work = nullptr;
   const int ccol = 4 * nrhs;
   std::vector<tc::Work> w;
   for (int64_t s = 0; s < d.noff; ++s) {
     const int64_t ncols = (int64_t)t.h_slot_npairs[s] * ccol;
-    const int nnt = (int)((ncols + tc::TN - 1) / tc::TN);
+    const int nnt = (int)((ncols + tn - 1) / tn);
     for (int mt = 0; mt < t.nmt; ++mt)
       for (int nt = 0; nt < nnt; ++nt) w.push_back({(int32_t)s, mt, nt, 0});
   }
@@ -185,9 +198,74 @@ static void tc_prepare_nrhs(nesa_ctx *c, TcLevel &t, const DevLevel &d, int nrhs
   t.work = (tc::Work *)dalloc(c, sizeof(tc::Work) * std::max<size_t>(1, w.size()));
   if (!w.empty())
     check_cuda(cudaMemcpy(t.work, w.data(), sizeof(tc::Work) * w.size(), cudaMemcpyHostToDevice), "work");
+  t.tn = tn;
+}
+
+static void tc_gemm(nesa_ctx *c, TcLevel &t, const DevLevel &d, int nrhs) {
+  TcState *S = state(c);
+  const int ccol = 4 * nrhs;
+  cudaStream_t st = c->stream;
+  switch (t.tn) {
+    case 64:
+      tc::k_tc_translate<64><<<(unsigned)t.nwork, 128, tc::smem_bytes<64>(), st>>>(
+          t.work, t.A_hi, t.A_lo, t.s_hi, t.s_lo, t.slot_ptr, t.slot_pair, d.il_src, t.P, d.q, t.kp, t.nmt, ccol,
+          S->err);
+      break;
+    case 256:
+      tc::k_tc_translate<256><<<(unsigned)t.nwork, 128, tc::smem_bytes<256>(), st>>>(
+          t.work, t.A_hi, t.A_lo, t.s_hi, t.s_lo, t.slot_ptr, t.slot_pair, d.il_src, t.P, d.q, t.kp, t.nmt, ccol,
+          S->err);
+      break;
+    default:
+      tc::k_tc_translate<128><<<(unsigned)t.nwork, 128, tc::smem_bytes<128>(), st>>>(
+          t.work, t.A_hi, t.A_lo, t.s_hi, t.s_lo, t.slot_ptr, t.slot_pair, d.il_src, t.P, d.q, t.kp, t.nmt, ccol,
+          S->err);
+  }
+}
+
+// Autotuner of the column-tile width: every candidate runs three times on the level's
+// current operands (timed with CUDA events on the context's stream), the fastest is
+// kept for this level and number of right-hand sides.  Synchronous: it runs at the
+// first mixed product with a new number of right-hand sides (or from nesa_autotune).
+static void tc_autotune(nesa_ctx *c, TcLevel &t, const DevLevel &d, int nrhs) {
+  const int cand[3] = {64, 128, 256};
+  float best = 1e30f;
+  int best_tn = 128;
+  cudaEvent_t e0, e1;
+  check_cuda(cudaEventCreate(&e0), "event");
+  check_cuda(cudaEventCreate(&e1), "event");
+  for (int tn : cand) {
+    tc_make_work(c, t, d, nrhs, tn);
+    if (t.nwork == 0) continue;
+    tc_gemm(c, t, d, nrhs);  // warm-up
+    check_cuda(cudaEventRecord(e0, c->stream), "event");
+    for (int r = 0; r < 3; ++r) tc_gemm(c, t, d, nrhs);
+    check_cuda(cudaEventRecord(e1, c->stream), "event");
+    check_cuda(cudaEventSynchronize(e1), "autotune");
+    float ms = 0.0f;
+    check_cuda(cudaEventElapsedTime(&ms, e0, e1), "event");
+    t.tune_ms[tn == 64 ? 0 : (tn == 128 ? 1 : 2)] = ms / 3.0f;
+    if (ms < best) {
+      best = ms;
+      best_tn = tn;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  tc_make_work(c, t, d, nrhs, best_tn);
+  t.tuned_nrhs = nrhs;
+}
+
+static void tc_prepare_nrhs(nesa_ctx *c, TcLevel &t, const DevLevel &d, int nrhs) {
+  if (t.nrhs == nrhs) return;
+  dfree(c, t.s_hi);
+  dfree(c, t.s_lo);
+  dfree(c, t.P);
+  const int ccol = 4 * nrhs;
   t.s_hi = (__nv_bfloat16 *)dalloc(c, sizeof(__nv_bfloat16) * (size_t)d.nbox * ccol * t.kp);
   t.s_lo = (__nv_bfloat16 *)dalloc(c, sizeof(__nv_bfloat16) * (size_t)d.nbox * ccol * t.kp);
   t.P = (float *)dalloc(c, sizeof(float) * (size_t)std::max<int64_t>(1, d.nil) * ccol * 2 * d.q);
+  tc_make_work(c, t, d, nrhs, t.tn);
   t.nrhs = nrhs;
 }
 
@@ -197,28 +275,53 @@ void tc_translate_level(nesa_ctx *c, int l, const cplxf *s, cplxf *o, const cplx
   TcState *S = state(c);
   TcLevel &t = S->lev[l];
   const DevLevel &d = c->lev[l];
-  tc_prepare_nrhs(c, t, d, nrhs);
   cudaStream_t st = c->stream;
-  const int ccol = 4 * nrhs;
-  const int64_t ncolumns = d.nbox * ccol;
-  k_split_s<<<(unsigned)std::min<int64_t>((ncolumns * t.kp + 255) / 256, 1 << 20), 256, 0, st>>>(t.s_hi, t.s_lo, s,
-                                                                                                  ncolumns, d.q, t.kp);
-  if (t.nwork > 0) {
-    static bool attr_set = false;
-    if (!attr_set) {
-      check_cuda(cudaFuncSetAttribute(tc::k_tc_translate, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      tc::SMEM_BYTES),
-                 "smem attribute");
-      attr_set = true;
-    }
-    tc::k_tc_translate<<<(unsigned)t.nwork, 128, tc::SMEM_BYTES, st>>>(t.work, t.A_hi, t.A_lo, t.s_hi, t.s_lo,
-                                                                       t.slot_ptr, t.slot_pair, d.il_src, t.P, d.q,
-                                                                       t.kp, t.nmt, ccol, S->err);
-  }
+  // right-hand sides go through in equal chunks of rc, so that the per-pair output P
+  // stays within about 1 GB (rc = the largest divisor of nrhs that fits)
+  const double per_rhs = 4.0 * 2.0 * d.q * 4.0 * (double)std::max<int64_t>(1, d.nil);
+  int rc = (int)std::max(1.0, std::min((double)nrhs, 1.0e9 / per_rhs));
+  while (nrhs % rc) --rc;
+  tc_prepare_nrhs(c, t, d, rc);
+  const int pcol = 4 * rc;
   const int qp = op ? c->lev[l - 1].q : 0;
-  size_t smem = sizeof(cplxf) * 4 * (size_t)std::max(qp, 1);
-  k_pair_reduce<<<dim3((unsigned)d.nbox, ntile), threads, smem, st>>>(o, t.P, d.il_ptr, op, Ct, d.parent, d.octant,
-                                                                      nrhs, d.q, qp, tr);
+  for (int r0 = 0; r0 < nrhs; r0 += rc) {
+    k_split_s<<<(unsigned)std::min<int64_t>((d.nbox * pcol * (int64_t)t.kp + 255) / 256, 1 << 20), 256, 0, st>>>(
+        t.s_hi, t.s_lo, s, d.nbox, 4 * nrhs, 4 * r0, pcol, d.q, t.kp);
+    if (t.nwork > 0) {
+      if (t.tuned_nrhs != rc && c->autotune) tc_autotune(c, t, d, rc);
+      cudaEvent_t ev0 = nullptr;
+      if (c->profiling) {
+        ev0 = take_event(c);
+        cudaEventRecord(ev0, st);
+      }
+      tc_gemm(c, t, d, rc);
+      if (c->profiling) {  // stage 4: the GEMM launch alone; algorithmic complex flops, operand bytes
+        cudaEvent_t ev1 = take_event(c);
+        cudaEventRecord(ev1, st);
+        const double fl = 32.0 * rc * (double)d.nil * d.q * d.q;
+        const double by = 2.0 * 2.0 * (double)d.noff * t.nmt * t.kp * tc::TM +
+                          2.0 * 2.0 * (double)d.nil * pcol * t.kp + 4.0 * (double)d.nil * pcol * 2 * d.q;
+        c->pending.push_back({4, ev0, ev1, fl, by});
+      }
+    }
+    size_t smem = sizeof(cplxf) * 4 * (size_t)std::max(qp, 1);
+    k_pair_reduce<<<dim3((unsigned)d.nbox, ntile), threads, smem, st>>>(o, t.P, d.il_ptr, op, Ct, d.parent, d.octant,
+                                                                        nrhs, r0, rc, d.q, qp, tr);
+  }
+}
+
+// tile widths chosen per level (0 where the level has no tensor work), for nesa_get_tuning
+void tc_tuning(nesa_ctx *c, int32_t *tn, float *ms) {
+  TcState *S = state(c);
+  for (int l = 0; l < NESA_MAX_LEVELS; ++l) {
+    tn[l] = 0;
+    for (int k = 0; k < 3; ++k) ms[3 * l + k] = 0.0f;
+  }
+  if (!S) return;
+  for (int l = c->l0; l <= c->L; ++l) {
+    tn[l] = S->lev[l].tn;
+    for (int k = 0; k < 3; ++k) ms[3 * l + k] = S->lev[l].tune_ms[k];
+  }
 }
 
 int tc_take_error(nesa_ctx *c) {
