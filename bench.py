@@ -230,7 +230,6 @@ def _time_products(g, x, y, parts, steps, warmup, stream, barrier):
         for _ in range(max(3, warmup)):
             g.matvec(x, y, parts=parts)
     stream.synchronize()
-    g.profile_enable(True)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     torch.cuda.synchronize()
@@ -242,6 +241,12 @@ def _time_products(g, x, y, parts, steps, warmup, stream, barrier):
     stream.synchronize()
     torch.cuda.synchronize()
     barrier()
+    # stage split: a second pass of the same products with per-stage events
+    g.profile_enable(True)
+    with torch.cuda.stream(stream):
+        for _ in range(steps):
+            g.matvec(x, y, parts=parts)
+    stream.synchronize()
     prof = g.profile_read()
     g.profile_enable(False)
     return ev0.elapsed_time(ev1) / steps, prof
@@ -377,16 +382,16 @@ def run_ours(args, world, rank, local):
         return 0
 
     # roofline of the dominant kernel of the mixed product (largest device time); the
-    # tensor-core GEMM is timed alone (stage 4), the rest of the translation stage is
-    # its split and reduction kernels
+    # tensor-core GEMMs are timed alone (stage 4), the rest of the translation stage is
+    # their split and reduction kernels
     peaks = _peaks()
     gemm = prof_mx["translation_tensor_gemm"]
     rest = {"ms": prof_mx["translation"]["ms"] - gemm["ms"], "flops": 0.0,
             "bytes": prof_mx["translation"]["bytes"] - gemm["bytes"]}
-    kernels = {"k_tc_translate": (gemm, "tensor"), "k_near_receive<float2>": (prof_mx["near_reception"], "hbm"),
+    kernels = {"k_tc_gemm": (gemm, "tensor"), "k_near_receive<float2>": (prof_mx["near_reception"], "hbm"),
                "k_upward<float2>": (prof_mx["source_transfer"], "alu"),
                "k_radiate<float2>": (prof_mx["radiation"], "hbm"),
-               "k_split_s + k_pair_reduce": (rest, "hbm")}
+               "k_split + k_pair_reduce": (rest, "hbm")}
     kernel = max(kernels, key=lambda k: kernels[k][0]["ms"])
     d, bound = kernels[kernel]
     sec = d["ms"] * 1e-3
@@ -394,7 +399,8 @@ def run_ours(args, world, rank, local):
         roof = {"bound": "tensor", "achieved": d["flops"] / sec / 1e12, "unit": "TFLOP/s",
                 "peak": peaks.get("bf16_tflops_sustained", 1700.0),
                 "peak_note": "BF16 dense, sustained, measured (MEASURED_PEAKS.json); achieved counts 8 flops per "
-                             "complex multiply-add of the translations, the BF16 hi/lo split executes 3x that"}
+                             "complex multiply-add of the translations and potential transfers, the BF16 hi/lo "
+                             "split executes 3x that"}
     elif bound == "hbm":
         roof = {"bound": "hbm", "achieved": d["bytes"] / sec / 1e9, "unit": "GB/s",
                 "peak": peaks.get("hbm_gbs", 6800.0), "peak_note": "HBM copy bandwidth, measured"}
@@ -403,9 +409,10 @@ def run_ours(args, world, rank, local):
                 "peak_note": "FP32: 152 SMs x 256 flop/clk x 2070 MHz (derived)"}
     roof.update({"kernel": kernel, "frac": roof["achieved"] / roof["peak"], "traffic": None,
                  "ms_per_step": d["ms"] / args.steps})
-    # kernels launched: the tensor translation is three kernels per level
+    # kernels launched: the tensor translation is split + GEMM + reduce at the coarsest
+    # far level and two splits + two GEMMs + reduce below it
     launches = (prof_mx["radiation"]["launches"] + prof_mx["source_transfer"]["launches"] +
-                prof_mx["near_reception"]["launches"] + prof_mx["translation"]["launches"] + 2 * gemm["launches"])
+                prof_mx["near_reception"]["launches"] + 5 * prof_mx["translation"]["launches"] - 2 * args.steps)
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -436,6 +443,7 @@ def run_ours(args, world, rank, local):
         "gpu_launches": launches,
         "roofline": roof,
         "stages": _stages(prof_mx, args.steps),
+        "tensor_tiles": {str(l): t for l, t in g.tuning().items()},
         "fp64": {"value": world * nrhs * 1e3 / ms64, "unit": UNIT, "ms_per_step": ms64, "dtype": "f64",
                  "stages": _stages(prof64, args.steps),
                  "roofline": {"kernel": "k_translate<double2>", "bound": "alu",

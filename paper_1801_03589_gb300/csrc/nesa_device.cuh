@@ -135,8 +135,7 @@ void build_mixed(nesa_ctx *c);
 cudaEvent_t take_event(nesa_ctx *c);
 // tensor-core translations of the mixed product (nesa_tc.cu)
 void tc_build(nesa_ctx *c);
-void tc_translate_level(nesa_ctx *c, int l, const cplxf *s, cplxf *o, const cplxf *op, const cplxf *Ct, int nrhs,
-                        int tr, int ntile, int threads);
+void tc_translate_level(nesa_ctx *c, int l, const cplxf *s, cplxf *o, const cplxf *op, const cplxf *Ct, int nrhs);
 int tc_take_error(nesa_ctx *c);
 void tc_free(nesa_ctx *c);
 void tc_tuning(nesa_ctx *c, int32_t *tn, float *ms);

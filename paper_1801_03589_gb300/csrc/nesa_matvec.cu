@@ -190,7 +190,10 @@ __global__ void __launch_bounds__(512) k_translate(CT *__restrict__ o, const CT 
 }
 
 // ------------------------------------------------------------------ near field + reception
-template <typename CT>
+// One warp per row m.  Right-hand sides go through in blocks of RB, so each near value,
+// column index and V column is read once per block; each lane keeps two near entries in
+// flight.  The channel weight gamma (1, 1, 1, -1/k^2) is folded into the V value.
+template <typename CT, int RB>
 __global__ void __launch_bounds__(256) k_near_receive(cplx *__restrict__ y, const cplx *__restrict__ x, int64_t n,
                                                       int nrhs, const int64_t *__restrict__ nz_ptr,
                                                       const int32_t *__restrict__ nz_col,
@@ -199,37 +202,67 @@ __global__ void __launch_bounds__(256) k_near_receive(cplx *__restrict__ y, cons
                                                       const int32_t *__restrict__ vc_leaf, const CT *__restrict__ V,
                                                       const CT *__restrict__ oL, int q, double eta_k, double inv_k2,
                                                       int parts) {
+  using RT = decltype(CT{}.x);
   const int64_t m = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (m >= n) return;
-  for (int r = 0; r < nrhs; ++r) {
-    CT near = {0, 0}, far = {0, 0};
+  const int64_t z0 = nz_ptr[m], z1 = nz_ptr[m + 1];
+  const int32_t f0 = rx_ptr[m], f1 = rx_ptr[m + 1];
+  for (int r0 = 0; r0 < nrhs; r0 += RB) {
+    const int rb = min(RB, nrhs - r0);
+    CT near[RB] = {}, far[RB] = {};
     if (parts & NESA_PART_NEAR) {
-      const cplx *xr = x + (int64_t)r * n;
-      for (int64_t e = nz_ptr[m] + lane; e < nz_ptr[m + 1]; e += 32) cfma(near, nz_val[e], from64<CT>(xr[nz_col[e]]));
+      const cplx *xr = x + (int64_t)r0 * n;
+      int64_t e = z0 + lane;
+      for (; e + 32 < z1; e += 64) {
+        const CT v0 = nz_val[e], v1 = nz_val[e + 32];
+        const int32_t k0 = nz_col[e], k1 = nz_col[e + 32];
+#pragma unroll
+        for (int rr = 0; rr < RB; ++rr)
+          if (rr < rb) {
+            cfma(near[rr], v0, from64<CT>(xr[(int64_t)rr * n + k0]));
+            cfma(near[rr], v1, from64<CT>(xr[(int64_t)rr * n + k1]));
+          }
+      }
+      if (e < z1) {
+        const CT v0 = nz_val[e];
+        const int32_t k0 = nz_col[e];
+#pragma unroll
+        for (int rr = 0; rr < RB; ++rr)
+          if (rr < rb) cfma(near[rr], v0, from64<CT>(xr[(int64_t)rr * n + k0]));
+      }
     }
     if (parts & NESA_PART_FAR) {
-      for (int32_t e = rx_ptr[m]; e < rx_ptr[m + 1]; ++e) {
+      for (int32_t e = f0; e < f1; ++e) {
         const int32_t g = rx_col[e];
         const int32_t lf = vc_leaf[g];
         const CT *vg = V + (int64_t)4 * g * q;
-        const CT *ol = oL + ((int64_t)lf * 4 * nrhs + 4 * r) * q;
+        const CT *ol = oL + ((int64_t)lf * 4 * nrhs + 4 * r0) * q;
+#pragma unroll
         for (int ch = 0; ch < 4; ++ch) {
-          CT t = {0, 0};
-          for (int i = lane; i < q; i += 32) cfma(t, vg[ch * q + i], ol[ch * q + i]);
-          const double gam = ch < 3 ? 1.0 : -inv_k2;
-          far.x += (decltype(far.x))(gam * t.x);
-          far.y += (decltype(far.y))(gam * t.y);
+          const RT gam = ch < 3 ? (RT)1 : (RT)(-inv_k2);
+          for (int i = lane; i < q; i += 32) {
+            CT v = vg[ch * q + i];
+            v.x *= gam;
+            v.y *= gam;
+#pragma unroll
+            for (int rr = 0; rr < RB; ++rr)
+              if (rr < rb) cfma(far[rr], v, ol[(int64_t)(4 * rr + ch) * q + i]);
+          }
         }
       }
     }
-    // -i eta k * far, summed over the warp in FP64
-    double2 v = make_double2((double)near.x + eta_k * (double)far.y, (double)near.y - eta_k * (double)far.x);
-    for (int off = 16; off > 0; off >>= 1) {
-      v.x += __shfl_down_sync(0xffffffffu, v.x, off);
-      v.y += __shfl_down_sync(0xffffffffu, v.y, off);
+    // y = near - i eta k far, summed over the warp in FP64
+#pragma unroll
+    for (int rr = 0; rr < RB; ++rr) {
+      double2 v = make_double2((double)near[rr].x + eta_k * (double)far[rr].y,
+                               (double)near[rr].y - eta_k * (double)far[rr].x);
+      for (int off = 16; off > 0; off >>= 1) {
+        v.x += __shfl_down_sync(0xffffffffu, v.x, off);
+        v.y += __shfl_down_sync(0xffffffffu, v.y, off);
+      }
+      if (lane == 0 && rr < rb) y[(int64_t)(r0 + rr) * n + m] = v;
     }
-    if (lane == 0) y[(int64_t)r * n + m] = v;
   }
 }
 
@@ -311,8 +344,7 @@ static void run_product(nesa_ctx *c, const OpView<CT> &op, const cplx *x, cplx *
       StageScope sc(c, 2, fl, by);
       if constexpr (std::is_same<CT, cplxf>::value) {
         if (c->tc_enabled) {
-          tc_translate_level(c, l, op.s[l], op.o[l], down ? op.o[l - 1] : nullptr, down ? op.Ct[l] : nullptr, nrhs,
-                             t.tr, t.ntile, t.threads);
+          tc_translate_level(c, l, op.s[l], op.o[l], down ? op.o[l - 1] : nullptr, down ? op.Ct[l] : nullptr, nrhs);
           continue;
         }
       }
@@ -329,9 +361,10 @@ static void run_product(nesa_ctx *c, const OpView<CT> &op, const cplx *x, cplx *
               ((parts & NESA_PART_FAR) ? B * 4.0 * ncol * dL.q + B * 4.0 * nrhs * dL.nbox * dL.q : 0.0) +
               16.0 * 2.0 * nrhs * c->n;
   StageScope sc(c, 3, fl, by);
-  k_near_receive<CT><<<grid_for(c->n * 32, 256), 256, 0, st>>>(y, x, c->n, nrhs, c->d_nz_ptr, c->d_nz_col, op.nz_val,
-                                                              c->d_rx_ptr, c->d_rx_col, c->d_vc_leaf, op.V, op.o[L],
-                                                              dL.q, c->eta * c->k, 1.0 / (c->k * c->k), parts);
+  auto near = nrhs == 1 ? k_near_receive<CT, 1> : k_near_receive<CT, 4>;
+  near<<<grid_for(c->n * 32, 256), 256, 0, st>>>(y, x, c->n, nrhs, c->d_nz_ptr, c->d_nz_col, op.nz_val, c->d_rx_ptr,
+                                                c->d_rx_col, c->d_vc_leaf, op.V, op.o[L], dL.q, c->eta * c->k,
+                                                1.0 / (c->k * c->k), parts);
 }
 
 // Launch the product on the context's stream.

@@ -1,11 +1,15 @@
-// Mixed-precision translation on the tensor cores (NESA_TRANSLATE_TENSOR).
+// Mixed-precision translation and potential transfer on the tensor cores
+// (NESA_TRANSLATE_TENSOR).
 //
-// Per level l (Eq. 12 and Eq. 13):
-//   k_split_s      s_l (complex64) -> BF16 hi/lo planes [box][4r+ch][Re s; Im s; 0]
-//   k_tc_translate for every offset slot o: C = A(o) B(pairs with offset o) on tcgen05
-//                  (nesa_tc.cuh), one FP32 column of 2Q values per pair and column
-//   k_pair_reduce  o_a = C^T o_P(a) + sum over the pairs of a of their columns
-// The reduction runs over each target's own pairs in a fixed order (owner computes),
+// Per level l, for each chunk of rc right-hand sides (Eq. 12 and Eq. 13):
+//   k_split        s_l (complex64) -> BF16 hi/lo column-group blocks (nesa_tc.cuh)
+//   k_tc_gemm      translations: one GEMM per offset slot, D(o) [s_b ...]; every pair
+//                  (a, b) gets its own block of P
+//   k_split        o_{l-1} -> BF16 blocks (l > l0)
+//   k_tc_gemm      potential transfer: one GEMM per octant, C_l(octant)^T [o_P ...];
+//                  every box a gets the block nil + a of P
+//   k_pair_reduce  o_a = P[nil + a] + sum over the pairs of a of P[pair]
+// The reduction runs over each target's own blocks in a fixed order (owner computes),
 // so the product is deterministic.
 #include <algorithm>
 #include <vector>
@@ -15,298 +19,357 @@
 
 namespace nesa {
 
-struct TcLevel {
-  int kp = 0, nmt = 0;
-  __nv_bfloat16 *A_hi = nullptr, *A_lo = nullptr;  // [noff][nmt][kp/32][4096]
-  int32_t *slot_ptr = nullptr, *slot_pair = nullptr;
-  std::vector<int32_t> h_slot_npairs;
-  // per-nrhs state
-  int nrhs = 0;
-  int tn = 128;          // column-tile width of the GEMM (autotuned)
-  int tuned_nrhs = 0;    // number of right-hand sides the width was tuned for
-  float tune_ms[3] = {0, 0, 0};  // measured times for widths 64, 128, 256
-  tc::Work *work = nullptr;
+// One family of equal-shaped GEMMs (all offsets of a level, or its eight octants).
+struct TcGemm {
+  int q = 0, kdim = 0;  // complex rows and columns of each matrix
+  int nk16 = 0, nkc = 0, nmt = 0;
+  int64_t nslot = 0, nent = 0;
+  __nv_bfloat16 *A_hi = nullptr, *A_lo = nullptr;  // [slot][nmt][nkc][4096]
+  std::vector<int32_t> h_ptr, h_dst, h_src;         // entries (output block, source box) by slot
+  int tn = 128;                   // column-tile width (autotuned)
+  int tuned_rc = 0;               // chunk size the width was tuned for
+  float tune_ms[3] = {0, 0, 0};   // measured times for widths 64, 128, 256
+  tc::Work *work = nullptr;       // work list for (work_tn, work_rc)
+  int32_t *wsrc = nullptr, *wdst = nullptr;
   int64_t nwork = 0;
-  __nv_bfloat16 *s_hi = nullptr, *s_lo = nullptr;  // [nbox][4 nrhs][kp]
-  float *P = nullptr;                              // [nil][4 nrhs][2q]
+  int work_tn = 0, work_rc = 0;
+};
+
+struct TcLevel {
+  TcGemm tr, dn;  // translations (Eq. 12); potential transfer (Eq. 13, l > l0)
+  int rc = 0;     // right-hand sides per chunk the buffers below are sized for
+  __nv_bfloat16 *s_hi = nullptr, *s_lo = nullptr;  // [nbox][rc][tr.nkc][256]
+  __nv_bfloat16 *o_hi = nullptr, *o_lo = nullptr;  // [parent boxes][rc][dn.nkc][256]
+  cplxf *P = nullptr;                              // [nil + nbox][4 rc][q]
 };
 
 struct TcState {
   TcLevel lev[NESA_MAX_LEVELS];
   int *err = nullptr;
+  int nsm = 0;
 };
 
-// A(o) for every offset slot, split and tiled in the shared-memory layout
-__global__ void k_prep_A(__nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo, const cplx *D, int64_t noff, int q, int kp,
-                         int nmt) {
-  const int nkc = kp / tc::TK;
-  const int64_t total = noff * nmt * nkc * (int64_t)tc::TILE_ELEMS;
+static TcState *state(nesa_ctx *c) { return (TcState *)c->tc_state; }
+
+// Real A tiles of nslot complex matrices M (q x kdim, column-major, complex128): row 2i
+// of A is Re M(i,:), row 2i+1 is Im M(i,:); rows >= 2q and columns >= kdim are zero.
+// Each value v is split as hi = bf16(v), lo = bf16(v - hi).
+__global__ void k_prep_A(__nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo, const cplx *M, int64_t nslot, int q, int kdim,
+                         int nmt, int nkc) {
+  const int64_t total = nslot * nmt * nkc * (int64_t)tc::TILE_ELEMS;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    const int t = (int)(idx % tc::TILE_ELEMS);
+    const int e = (int)(idx % tc::TILE_ELEMS);  // (row, k) with k fastest
     int64_t rest = idx / tc::TILE_ELEMS;
     const int kc = (int)(rest % nkc);
     rest /= nkc;
     const int mt = (int)(rest % nmt);
     const int64_t slot = rest / nmt;
-    // inverse of tc::tile_offset
-    const int b = 2 * t;
-    const int kgrp = b / tc::LBO_A, rem = b % tc::LBO_A;
-    const int rgrp = rem / tc::SBO, rem2 = rem % tc::SBO;
-    const int m = mt * tc::TM + rgrp * 8 + rem2 / 16;
-    const int k = kc * tc::TK + kgrp * 8 + (rem2 % 16) / 2;
+    const int rloc = e / tc::TK, kloc = e % tc::TK;
+    const int row = mt * tc::TM + rloc, k = kc * tc::TK + kloc;
+    const int i = row >> 1;
     double v = 0.0;
-    if (m < 2 * q && k < 2 * q) {
-      const cplx *Dm = D + slot * (int64_t)q * q;
-      const int i = m < q ? m : m - q, j = k < q ? k : k - q;
-      const cplx d = Dm[i + (int64_t)j * q];
-      if (m < q)
-        v = k < q ? d.x : -d.y;
-      else
-        v = k < q ? d.y : d.x;
+    if (i < q && k < kdim) {
+      const cplx m = M[slot * (int64_t)q * kdim + i + (int64_t)k * q];
+      v = (row & 1) ? m.y : m.x;
     }
     const __nv_bfloat16 hi = __float2bfloat16_rn((float)v);
     const __nv_bfloat16 lo = __float2bfloat16_rn((float)(v - (double)__bfloat162float(hi)));
-    A_hi[idx] = hi;
-    A_lo[idx] = lo;
+    const int64_t out = ((slot * nmt + mt) * nkc + kc) * tc::TILE_ELEMS + tc::a_tile_elem(rloc, kloc);
+    A_hi[out] = hi;
+    A_lo[out] = lo;
   }
 }
 
-// s (complex64, [box][ccol][q]) -> hi/lo planes [box][ccol][kp] of [Re; Im; 0]
-// (columns col0 .. col0+cchunk-1 of every box; s has ctotal columns per box)
-__global__ void k_split_s(__nv_bfloat16 *s_hi, __nv_bfloat16 *s_lo, const cplxf *s, int64_t nbox, int ctotal,
-                          int col0, int cchunk, int q, int kp) {
-  const int64_t total = nbox * cchunk * (int64_t)kp;
+// x (complex64, [box][4 nrhs][q], column 4r + ch) -> hi/lo blocks [box][rc][nkc][256]
+// for the right-hand sides r0 .. r0+rc-1: block (box, r, kc) holds the 8 columns
+// 2ch + part (part 0: Re x_ch, 1: Im x_ch) at K = 32 kc .. 32 kc + 31 (zero past q)
+__global__ void k_split(__nv_bfloat16 *x_hi, __nv_bfloat16 *x_lo, const cplxf *x, int64_t nbox, int nrhs, int r0,
+                        int rc, int q, int nkc) {
+  const int64_t total = nbox * rc * nkc * (int64_t)tc::GROUP_ELEMS;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    const int k = (int)(idx % kp);
-    const int64_t oc = idx / kp;
-    const int64_t col = (oc / cchunk) * ctotal + col0 + oc % cchunk;
+    const int e = (int)(idx % tc::GROUP_ELEMS);  // (column, k) with k fastest
+    int64_t rest = idx / tc::GROUP_ELEMS;
+    const int kc = (int)(rest % nkc);
+    rest /= nkc;
+    const int r = (int)(rest % rc);
+    const int64_t box = rest / rc;
+    const int col = e / tc::TK, kloc = e % tc::TK, k = kc * tc::TK + kloc;
     float v = 0.0f;
-    if (k < q)
-      v = s[col * q + k].x;
-    else if (k < 2 * q)
-      v = s[col * q + (k - q)].y;
+    if (k < q) {
+      const cplxf z = x[(box * 4 * nrhs + 4 * (r0 + r) + (col >> 1)) * q + k];
+      v = (col & 1) ? z.y : z.x;
+    }
     const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-    s_hi[idx] = hi;
-    s_lo[idx] = __float2bfloat16_rn(v - __bfloat162float(hi));
+    const int64_t out = ((box * rc + r) * nkc + kc) * tc::GROUP_ELEMS + tc::b_group_elem(col, kloc);
+    x_hi[out] = hi;
+    x_lo[out] = __float2bfloat16_rn(v - __bfloat162float(hi));
   }
 }
 
-// o_a = C^T o_P (Eq. 13) + sum of the translated columns of a's pairs (Eq. 12), for the
-// right-hand sides r0 .. r0+rc-1 (P holds 4 rc columns per pair; o, op hold 4 nrhs)
-__global__ void __launch_bounds__(512) k_pair_reduce(cplxf *__restrict__ o, const float *__restrict__ P,
-                                                     const int32_t *__restrict__ il_ptr, const cplxf *__restrict__ op,
-                                                     const cplxf *__restrict__ Ct, const int32_t *__restrict__ parent,
-                                                     const int32_t *__restrict__ octant, int nrhs, int r0, int rc,
-                                                     int q, int qp, int tr) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cplxf *col = (cplxf *)smem_raw;
+// o_a (right-hand sides r0 .. r0+rc-1) = P[down + a] (when down >= 0) + sum of the
+// pair blocks of a in list order; P blocks are [4 rc][q] complex64
+__global__ void __launch_bounds__(256) k_pair_reduce(cplxf *__restrict__ o, const cplxf *__restrict__ P,
+                                                     const int32_t *__restrict__ il_ptr, int64_t down, int nrhs,
+                                                     int r0, int rc, int q) {
   const int32_t a = blockIdx.x;
-  const int tile = blockIdx.y;
-  const int ch = threadIdx.x / tr;
-  const int i = tile * tr + threadIdx.x % tr;
-  const bool active = ch < 4 && i < q;
-  const int ccol = 4 * nrhs, pcol = 4 * rc;
+  const int64_t blk = 4 * (int64_t)rc * q;
+  const int64_t j = blockIdx.y * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= blk) return;
+  cplxf acc = down >= 0 ? P[(down + a) * blk + j] : make_float2(0.0f, 0.0f);
   const int32_t e0 = il_ptr[a], e1 = il_ptr[a + 1];
-  for (int r = r0; r < r0 + rc; ++r) {
-    cplxf acc = {0.0f, 0.0f};
-    if (op) {
-      __syncthreads();
-      const int32_t Pp = parent[a];
-      const cplxf *src = op + ((int64_t)Pp * ccol + 4 * r) * qp;
-      for (int j = threadIdx.x; j < 4 * qp; j += blockDim.x) col[j] = src[j];
-      __syncthreads();
-      if (active) {
-        const cplxf *Bm = Ct + (int64_t)octant[a] * q * qp + i;
-        const cplxf *cs = col + ch * qp;
-#pragma unroll 4
-        for (int j = 0; j < qp; ++j) cfma(acc, Bm[(int64_t)j * q], cs[j]);
-      }
-    }
-    if (active) {
-      for (int32_t e = e0; e < e1; ++e) {
-        const float *pc = P + ((int64_t)e * pcol + 4 * (r - r0) + ch) * 2 * q;
-        acc.x += pc[i];
-        acc.y += pc[q + i];
-      }
-      o[((int64_t)a * ccol + 4 * r + ch) * q + i] = acc;
-    }
+  for (int32_t e = e0; e < e1; ++e) {
+    const cplxf v = P[(int64_t)e * blk + j];
+    acc.x += v.x;
+    acc.y += v.y;
+  }
+  o[((int64_t)a * 4 * nrhs + 4 * r0) * q + j] = acc;
+}
+
+// A tiles and entry lists of one GEMM family; M = nslot matrices q x kdim (complex128)
+static void gemm_setup(nesa_ctx *c, TcGemm &g, const cplx *M, int64_t nslot, int q, int kdim,
+                       const std::vector<int32_t> &ent_slot, const std::vector<int32_t> &dst,
+                       const std::vector<int32_t> &src) {
+  g.q = q;
+  g.kdim = kdim;
+  g.nk16 = (kdim + 15) / 16;
+  g.nkc = (g.nk16 + 1) / 2;
+  g.nmt = (2 * q + tc::TM - 1) / tc::TM;
+  g.nslot = nslot;
+  g.nent = (int64_t)ent_slot.size();
+  const int64_t nel = nslot * g.nmt * (int64_t)g.nkc * tc::TILE_ELEMS;
+  g.A_hi = (__nv_bfloat16 *)dalloc(c, sizeof(__nv_bfloat16) * nel);
+  g.A_lo = (__nv_bfloat16 *)dalloc(c, sizeof(__nv_bfloat16) * nel);
+  k_prep_A<<<(unsigned)std::min<int64_t>((nel + 255) / 256, 1 << 20), 256, 0, c->stream>>>(g.A_hi, g.A_lo, M, nslot,
+                                                                                         q, kdim, g.nmt, g.nkc);
+  check_cuda(cudaGetLastError(), "prep A");
+  // entries grouped by slot (stable: ascending entry order within a slot)
+  g.h_ptr.assign(nslot + 1, 0);
+  g.h_dst.resize(g.nent);
+  g.h_src.resize(g.nent);
+  for (int32_t sl : ent_slot) g.h_ptr[sl + 1]++;
+  for (int64_t s = 0; s < nslot; ++s) g.h_ptr[s + 1] += g.h_ptr[s];
+  std::vector<int32_t> fill(g.h_ptr.begin(), g.h_ptr.end() - 1);
+  for (int64_t e = 0; e < g.nent; ++e) {
+    const int32_t at = fill[ent_slot[e]]++;
+    g.h_dst[at] = dst[e];
+    g.h_src[at] = src[e];
   }
 }
 
-static TcState *state(nesa_ctx *c) { return (TcState *)c->tc_state; }
+template <int TN>
+static void set_smem() {
+  check_cuda(cudaFuncSetAttribute(tc::k_tc_gemm<TN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  tc::smem_bytes<TN>()),
+             "smem attribute");
+}
 
 void tc_build(nesa_ctx *c) {
   TcState *S = new TcState();
   c->tc_state = S;
-  check_cuda(cudaFuncSetAttribute(tc::k_tc_translate<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  tc::smem_bytes<64>()),
-             "smem attribute");
-  check_cuda(cudaFuncSetAttribute(tc::k_tc_translate<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  tc::smem_bytes<128>()),
-             "smem attribute");
-  check_cuda(cudaFuncSetAttribute(tc::k_tc_translate<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  tc::smem_bytes<256>()),
-             "smem attribute");
+  set_smem<64>();
+  set_smem<128>();
+  set_smem<256>();
+  int dev = 0;
+  check_cuda(cudaGetDevice(&dev), "device");
+  check_cuda(cudaDeviceGetAttribute(&S->nsm, cudaDevAttrMultiProcessorCount, dev), "SM count");
   S->err = (int *)dalloc(c, sizeof(int));
   check_cuda(cudaMemset(S->err, 0, sizeof(int)), "tc flag");
   for (int l = c->l0; l <= c->L; ++l) {
     DevLevel &d = c->lev[l];
     TcLevel &t = S->lev[l];
     const HostLevel &hl = c->h.lev[l];
-    t.kp = ((2 * d.q + tc::TK - 1) / tc::TK) * tc::TK;
-    t.nmt = (2 * d.q + tc::TM - 1) / tc::TM;
-    const int64_t nel = d.noff * t.nmt * (int64_t)(t.kp / tc::TK) * tc::TILE_ELEMS;
-    t.A_hi = (__nv_bfloat16 *)dalloc(c, sizeof(__nv_bfloat16) * nel);
-    t.A_lo = (__nv_bfloat16 *)dalloc(c, sizeof(__nv_bfloat16) * nel);
-    k_prep_A<<<(unsigned)std::min<int64_t>((nel + 255) / 256, 1 << 20), 256, 0, c->stream>>>(t.A_hi, t.A_lo, d.D,
-                                                                                           d.noff, d.q, t.kp, t.nmt);
-    check_cuda(cudaGetLastError(), "prep A");
-    // pairs grouped by offset slot (stable: ascending target within a slot)
-    std::vector<int32_t> ptr(d.noff + 1, 0), pairs(hl.il_slot.size());
-    for (int32_t sl : hl.il_slot) ptr[sl + 1]++;
-    for (int64_t s = 0; s < d.noff; ++s) ptr[s + 1] += ptr[s];
-    std::vector<int32_t> fill(ptr.begin(), ptr.end() - 1);
-    for (size_t e = 0; e < hl.il_slot.size(); ++e) pairs[fill[hl.il_slot[e]]++] = (int32_t)e;
-    t.h_slot_npairs.resize(d.noff);
-    for (int64_t s = 0; s < d.noff; ++s) t.h_slot_npairs[s] = ptr[s + 1] - ptr[s];
-    t.slot_ptr = (int32_t *)dalloc(c, sizeof(int32_t) * ptr.size());
-    t.slot_pair = (int32_t *)dalloc(c, sizeof(int32_t) * std::max<size_t>(1, pairs.size()));
-    check_cuda(cudaMemcpy(t.slot_ptr, ptr.data(), sizeof(int32_t) * ptr.size(), cudaMemcpyHostToDevice), "slots");
-    if (!pairs.empty())
-      check_cuda(cudaMemcpy(t.slot_pair, pairs.data(), sizeof(int32_t) * pairs.size(), cudaMemcpyHostToDevice),
-                 "pairs");
+    // translations: entry = pair e, slot = its offset, source = il_src[e]
+    std::vector<int32_t> dst(hl.il_slot.size());
+    for (size_t e = 0; e < dst.size(); ++e) dst[e] = (int32_t)e;
+    gemm_setup(c, t.tr, d.D, d.noff, d.q, d.q, hl.il_slot, dst, hl.il_src);
+    if (l > c->l0) {  // potential transfer: entry = box a, slot = octant, source = parent
+      std::vector<int32_t> bd(d.nbox);
+      for (int64_t a = 0; a < d.nbox; ++a) bd[a] = (int32_t)(d.nil + a);
+      gemm_setup(c, t.dn, d.Ct, 8, d.q, c->lev[l - 1].q, hl.octant, bd, hl.parent);
+    }
   }
   check_cuda(cudaStreamSynchronize(c->stream), "tc build");
   c->tc_enabled = true;
 }
 
-// work list of the GEMM for a column-tile width tn
-static void tc_make_work(nesa_ctx *c, TcLevel &t, const DevLevel &d, int nrhs, int tn) {
-  dfree(c, t.work);
-  t.work = nullptr;
-  const int ccol = 4 * nrhs;
+// Work list (slot-major, so that CTAs running together share the slot's A tiles) and,
+// per work item, the source block (box * rc + r) and output column (block * 4 rc + 4 r)
+// of each of its tn/8 column groups (-1 past the slot's last group).
+static void make_work(nesa_ctx *c, TcGemm &g, int rc, int tn) {
+  if (g.work && g.work_tn == tn && g.work_rc == rc) return;
+  dfree(c, g.work);
+  dfree(c, g.wsrc);
+  dfree(c, g.wdst);
+  g.work = nullptr;
+  g.wsrc = g.wdst = nullptr;
   std::vector<tc::Work> w;
-  for (int64_t s = 0; s < d.noff; ++s) {
-    const int64_t ncols = (int64_t)t.h_slot_npairs[s] * ccol;
-    const int nnt = (int)((ncols + tn - 1) / tn);
-    for (int mt = 0; mt < t.nmt; ++mt)
-      for (int nt = 0; nt < nnt; ++nt) w.push_back({(int32_t)s, mt, nt, 0});
+  std::vector<int32_t> ws, wd;
+  const int gt = tn / 8;
+  for (int64_t s = 0; s < g.nslot; ++s) {
+    const int32_t e0 = g.h_ptr[s];
+    const int64_t ngroups = (int64_t)(g.h_ptr[s + 1] - e0) * rc;
+    const int nnt = (int)((ngroups + gt - 1) / gt);
+    for (int mt = 0; mt < g.nmt; ++mt)
+      for (int nt = 0; nt < nnt; ++nt) {
+        const int nvalid = (int)std::min<int64_t>(gt, ngroups - (int64_t)nt * gt);
+        w.push_back({(int32_t)s, mt, nvalid, 0});
+        for (int j = 0; j < gt; ++j) {
+          const int64_t G = (int64_t)nt * gt + j;
+          if (j < nvalid) {
+            const int32_t e = e0 + (int32_t)(G / rc), r = (int32_t)(G % rc);
+            ws.push_back(g.h_src[e] * rc + r);
+            wd.push_back(g.h_dst[e] * 4 * rc + 4 * r);
+          } else {
+            ws.push_back(-1);
+            wd.push_back(-1);
+          }
+        }
+      }
   }
-  t.nwork = (int64_t)w.size();
-  t.work = (tc::Work *)dalloc(c, sizeof(tc::Work) * std::max<size_t>(1, w.size()));
-  if (!w.empty())
-    check_cuda(cudaMemcpy(t.work, w.data(), sizeof(tc::Work) * w.size(), cudaMemcpyHostToDevice), "work");
-  t.tn = tn;
+  g.nwork = (int64_t)w.size();
+  g.work = (tc::Work *)dalloc(c, sizeof(tc::Work) * std::max<size_t>(1, w.size()));
+  g.wsrc = (int32_t *)dalloc(c, sizeof(int32_t) * std::max<size_t>(1, ws.size()));
+  g.wdst = (int32_t *)dalloc(c, sizeof(int32_t) * std::max<size_t>(1, wd.size()));
+  if (!w.empty()) {
+    check_cuda(cudaMemcpy(g.work, w.data(), sizeof(tc::Work) * w.size(), cudaMemcpyHostToDevice), "work");
+    check_cuda(cudaMemcpy(g.wsrc, ws.data(), sizeof(int32_t) * ws.size(), cudaMemcpyHostToDevice), "work");
+    check_cuda(cudaMemcpy(g.wdst, wd.data(), sizeof(int32_t) * wd.size(), cudaMemcpyHostToDevice), "work");
+  }
+  g.work_tn = tn;
+  g.work_rc = rc;
 }
 
-static void tc_gemm(nesa_ctx *c, TcLevel &t, const DevLevel &d, int nrhs) {
+static void launch_gemm(nesa_ctx *c, const TcGemm &g, const __nv_bfloat16 *B_hi, const __nv_bfloat16 *B_lo,
+                        cplxf *P, int rc) {
   TcState *S = state(c);
-  const int ccol = 4 * nrhs;
+  if (g.nwork == 0) return;
+  (void)rc;
+  tc::GemmArgs a{g.work, g.wsrc, g.wdst, g.nwork, g.A_hi, g.A_lo, B_hi, B_lo, P, g.q, g.nk16, g.nmt, S->err};
+  const unsigned grid = (unsigned)std::min<int64_t>(g.nwork, S->nsm);
   cudaStream_t st = c->stream;
-  switch (t.tn) {
+  switch (g.work_tn) {
     case 64:
-      tc::k_tc_translate<64><<<(unsigned)t.nwork, 128, tc::smem_bytes<64>(), st>>>(
-          t.work, t.A_hi, t.A_lo, t.s_hi, t.s_lo, t.slot_ptr, t.slot_pair, d.il_src, t.P, d.q, t.kp, t.nmt, ccol,
-          S->err);
+      tc::k_tc_gemm<64><<<grid, tc::THREADS, tc::smem_bytes<64>(), st>>>(a);
       break;
     case 256:
-      tc::k_tc_translate<256><<<(unsigned)t.nwork, 128, tc::smem_bytes<256>(), st>>>(
-          t.work, t.A_hi, t.A_lo, t.s_hi, t.s_lo, t.slot_ptr, t.slot_pair, d.il_src, t.P, d.q, t.kp, t.nmt, ccol,
-          S->err);
+      tc::k_tc_gemm<256><<<grid, tc::THREADS, tc::smem_bytes<256>(), st>>>(a);
       break;
     default:
-      tc::k_tc_translate<128><<<(unsigned)t.nwork, 128, tc::smem_bytes<128>(), st>>>(
-          t.work, t.A_hi, t.A_lo, t.s_hi, t.s_lo, t.slot_ptr, t.slot_pair, d.il_src, t.P, d.q, t.kp, t.nmt, ccol,
-          S->err);
+      tc::k_tc_gemm<128><<<grid, tc::THREADS, tc::smem_bytes<128>(), st>>>(a);
   }
 }
 
-// Autotuner of the column-tile width: every candidate runs three times on the level's
-// current operands (timed with CUDA events on the context's stream), the fastest is
-// kept for this level and number of right-hand sides.  Synchronous: it runs at the
-// first mixed product with a new number of right-hand sides (or from nesa_autotune).
-static void tc_autotune(nesa_ctx *c, TcLevel &t, const DevLevel &d, int nrhs) {
+// Autotuner of the column-tile width: every candidate runs three times on the current
+// operands (timed with CUDA events on the context's stream), the fastest is kept for
+// this GEMM family and chunk size.  Synchronous: it runs at the first mixed product
+// with a new chunk size (never inside a graph capture: the eager product comes first).
+static void autotune(nesa_ctx *c, TcGemm &g, const __nv_bfloat16 *B_hi, const __nv_bfloat16 *B_lo, cplxf *P,
+                     int rc) {
   const int cand[3] = {64, 128, 256};
   float best = 1e30f;
   int best_tn = 128;
   cudaEvent_t e0, e1;
   check_cuda(cudaEventCreate(&e0), "event");
   check_cuda(cudaEventCreate(&e1), "event");
-  for (int tn : cand) {
-    tc_make_work(c, t, d, nrhs, tn);
-    if (t.nwork == 0) continue;
-    tc_gemm(c, t, d, nrhs);  // warm-up
+  for (int k = 0; k < 3; ++k) {
+    make_work(c, g, rc, cand[k]);
+    launch_gemm(c, g, B_hi, B_lo, P, rc);  // warm-up
     check_cuda(cudaEventRecord(e0, c->stream), "event");
-    for (int r = 0; r < 3; ++r) tc_gemm(c, t, d, nrhs);
+    for (int r = 0; r < 3; ++r) launch_gemm(c, g, B_hi, B_lo, P, rc);
     check_cuda(cudaEventRecord(e1, c->stream), "event");
     check_cuda(cudaEventSynchronize(e1), "autotune");
     float ms = 0.0f;
     check_cuda(cudaEventElapsedTime(&ms, e0, e1), "event");
-    t.tune_ms[tn == 64 ? 0 : (tn == 128 ? 1 : 2)] = ms / 3.0f;
+    g.tune_ms[k] = ms / 3.0f;
     if (ms < best) {
       best = ms;
-      best_tn = tn;
+      best_tn = cand[k];
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  tc_make_work(c, t, d, nrhs, best_tn);
-  t.tuned_nrhs = nrhs;
+  make_work(c, g, rc, best_tn);
+  g.tn = best_tn;
+  g.tuned_rc = rc;
 }
 
-static void tc_prepare_nrhs(nesa_ctx *c, TcLevel &t, const DevLevel &d, int nrhs) {
-  if (t.nrhs == nrhs) return;
+static void prepare_rc(nesa_ctx *c, TcLevel &t, int l, int rc) {
+  if (t.rc == rc) return;
+  const DevLevel &d = c->lev[l];
   dfree(c, t.s_hi);
   dfree(c, t.s_lo);
+  dfree(c, t.o_hi);
+  dfree(c, t.o_lo);
   dfree(c, t.P);
-  const int ccol = 4 * nrhs;
-  t.s_hi = (__nv_bfloat16 *)dalloc(c, sizeof(__nv_bfloat16) * (size_t)d.nbox * ccol * t.kp);
-  t.s_lo = (__nv_bfloat16 *)dalloc(c, sizeof(__nv_bfloat16) * (size_t)d.nbox * ccol * t.kp);
-  t.P = (float *)dalloc(c, sizeof(float) * (size_t)std::max<int64_t>(1, d.nil) * ccol * 2 * d.q);
-  tc_make_work(c, t, d, nrhs, t.tn);
-  t.nrhs = nrhs;
+  t.o_hi = t.o_lo = nullptr;
+  t.s_hi = (__nv_bfloat16 *)dalloc(c, sizeof(__nv_bfloat16) * (size_t)d.nbox * rc * t.tr.nkc * tc::GROUP_ELEMS);
+  t.s_lo = (__nv_bfloat16 *)dalloc(c, sizeof(__nv_bfloat16) * (size_t)d.nbox * rc * t.tr.nkc * tc::GROUP_ELEMS);
+  int64_t nblk = d.nil;
+  if (l > c->l0) {
+    const int64_t np = c->lev[l - 1].nbox;
+    t.o_hi = (__nv_bfloat16 *)dalloc(c, sizeof(__nv_bfloat16) * (size_t)np * rc * t.dn.nkc * tc::GROUP_ELEMS);
+    t.o_lo = (__nv_bfloat16 *)dalloc(c, sizeof(__nv_bfloat16) * (size_t)np * rc * t.dn.nkc * tc::GROUP_ELEMS);
+    nblk += d.nbox;
+  }
+  t.P = (cplxf *)dalloc(c, sizeof(cplxf) * (size_t)std::max<int64_t>(1, nblk) * 4 * rc * d.q);
+  t.rc = rc;
 }
 
+static inline unsigned grid_of(int64_t n) { return (unsigned)std::min<int64_t>((n + 255) / 256, 1 << 20); }
+
 // Translation + potential transfer of level l on the tensor cores (mixed product).
-void tc_translate_level(nesa_ctx *c, int l, const cplxf *s, cplxf *o, const cplxf *op, const cplxf *Ct, int nrhs,
-                        int tr, int ntile, int threads) {
+void tc_translate_level(nesa_ctx *c, int l, const cplxf *s, cplxf *o, const cplxf *op, const cplxf *Ct, int nrhs) {
+  (void)Ct;
   TcState *S = state(c);
   TcLevel &t = S->lev[l];
   const DevLevel &d = c->lev[l];
   cudaStream_t st = c->stream;
-  // right-hand sides go through in equal chunks of rc, so that the per-pair output P
-  // stays within about 1 GB (rc = the largest divisor of nrhs that fits)
-  const double per_rhs = 4.0 * 2.0 * d.q * 4.0 * (double)std::max<int64_t>(1, d.nil);
+  const bool down = op != nullptr && l > c->l0;
+  // right-hand sides go through in equal chunks of rc, so that P stays within about
+  // 1 GB (rc = the largest divisor of nrhs that fits)
+  const double per_rhs = 4.0 * 8.0 * d.q * (double)std::max<int64_t>(1, d.nil + (down ? d.nbox : 0));
   int rc = (int)std::max(1.0, std::min((double)nrhs, 1.0e9 / per_rhs));
   while (nrhs % rc) --rc;
-  tc_prepare_nrhs(c, t, d, rc);
-  const int pcol = 4 * rc;
-  const int qp = op ? c->lev[l - 1].q : 0;
+  prepare_rc(c, t, l, rc);
   for (int r0 = 0; r0 < nrhs; r0 += rc) {
-    k_split_s<<<(unsigned)std::min<int64_t>((d.nbox * pcol * (int64_t)t.kp + 255) / 256, 1 << 20), 256, 0, st>>>(
-        t.s_hi, t.s_lo, s, d.nbox, 4 * nrhs, 4 * r0, pcol, d.q, t.kp);
-    if (t.nwork > 0) {
-      if (t.tuned_nrhs != rc && c->autotune) tc_autotune(c, t, d, rc);
-      cudaEvent_t ev0 = nullptr;
-      if (c->profiling) {
-        ev0 = take_event(c);
-        cudaEventRecord(ev0, st);
-      }
-      tc_gemm(c, t, d, rc);
-      if (c->profiling) {  // stage 4: the GEMM launch alone; algorithmic complex flops, operand bytes
-        cudaEvent_t ev1 = take_event(c);
-        cudaEventRecord(ev1, st);
-        const double fl = 32.0 * rc * (double)d.nil * d.q * d.q;
-        const double by = 2.0 * 2.0 * (double)d.noff * t.nmt * t.kp * tc::TM +
-                          2.0 * 2.0 * (double)d.nil * pcol * t.kp + 4.0 * (double)d.nil * pcol * 2 * d.q;
-        c->pending.push_back({4, ev0, ev1, fl, by});
-      }
+    k_split<<<grid_of(d.nbox * rc * t.tr.nkc * (int64_t)tc::GROUP_ELEMS), 256, 0, st>>>(t.s_hi, t.s_lo, s, d.nbox,
+                                                                                       nrhs, r0, rc, d.q, t.tr.nkc);
+    if (down) {
+      const DevLevel &p = c->lev[l - 1];
+      k_split<<<grid_of(p.nbox * rc * t.dn.nkc * (int64_t)tc::GROUP_ELEMS), 256, 0, st>>>(
+          t.o_hi, t.o_lo, op, p.nbox, nrhs, r0, rc, p.q, t.dn.nkc);
     }
-    size_t smem = sizeof(cplxf) * 4 * (size_t)std::max(qp, 1);
-    k_pair_reduce<<<dim3((unsigned)d.nbox, ntile), threads, smem, st>>>(o, t.P, d.il_ptr, op, Ct, d.parent, d.octant,
-                                                                        nrhs, r0, rc, d.q, qp, tr);
+    if (c->autotune) {
+      if (t.tr.tuned_rc != rc) autotune(c, t.tr, t.s_hi, t.s_lo, t.P, rc);
+      if (down && t.dn.tuned_rc != rc) autotune(c, t.dn, t.o_hi, t.o_lo, t.P, rc);
+    }
+    make_work(c, t.tr, rc, t.tr.tn);
+    if (down) make_work(c, t.dn, rc, t.dn.tn);
+    cudaEvent_t ev0 = nullptr;
+    if (c->profiling) {
+      ev0 = take_event(c);
+      cudaEventRecord(ev0, st);
+    }
+    launch_gemm(c, t.tr, t.s_hi, t.s_lo, t.P, rc);
+    if (down) launch_gemm(c, t.dn, t.o_hi, t.o_lo, t.P, rc);
+    if (c->profiling) {  // stage 4: the GEMM launches alone; algorithmic complex flops, operand bytes
+      cudaEvent_t ev1 = take_event(c);
+      cudaEventRecord(ev1, st);
+      double fl = 32.0 * rc * (double)d.nil * d.q * d.q;
+      double by = 4.0 * (double)d.noff * t.tr.nmt * t.tr.nkc * tc::TILE_ELEMS +
+                  4.0 * (double)d.nil * rc * t.tr.nkc * tc::GROUP_ELEMS + 32.0 * (double)d.nil * rc * d.q;
+      if (down) {
+        const int qp = c->lev[l - 1].q;
+        fl += 32.0 * rc * (double)d.nbox * d.q * qp;
+        by += 4.0 * 8 * t.dn.nmt * t.dn.nkc * tc::TILE_ELEMS + 4.0 * (double)d.nbox * rc * t.dn.nkc * tc::GROUP_ELEMS +
+              32.0 * (double)d.nbox * rc * d.q;
+      }
+      c->pending.push_back({4, ev0, ev1, fl, by});
+    }
+    k_pair_reduce<<<dim3((unsigned)d.nbox, (unsigned)((4 * rc * d.q + 255) / 256)), 256, 0, st>>>(
+        o, t.P, d.il_ptr, down ? d.nil : -1, nrhs, r0, rc, d.q);
   }
 }
 
@@ -319,8 +382,8 @@ void tc_tuning(nesa_ctx *c, int32_t *tn, float *ms) {
   }
   if (!S) return;
   for (int l = c->l0; l <= c->L; ++l) {
-    tn[l] = S->lev[l].tn;
-    for (int k = 0; k < 3; ++k) ms[3 * l + k] = S->lev[l].tune_ms[k];
+    tn[l] = S->lev[l].tr.tn;
+    for (int k = 0; k < 3; ++k) ms[3 * l + k] = S->lev[l].tr.tune_ms[k];
   }
 }
 
