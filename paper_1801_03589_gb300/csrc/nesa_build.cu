@@ -762,6 +762,10 @@ int nesa_build(const nesa_mesh *mesh, double k, const nesa_params *params, nesa_
       g_last_error = e.what;
       free_ctx(c);
       return e.status;
+    } catch (const std::bad_alloc &) {
+      g_last_error = "host allocation failed";
+      free_ctx(c);
+      return NESA_ERR_OOM;
     }
   }
   I.device_bytes = (int64_t)c->device_bytes;

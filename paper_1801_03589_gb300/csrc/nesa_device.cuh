@@ -94,7 +94,14 @@ struct nesa_ctx {
   nesa::cplx *d_nz_val = nullptr;
   // complex64 copies (NESA_MIXED)
   bool mixed = false;
+  // near field of the mixed product in the internal order (RWG functions sorted by the
+  // leaf of their first quadrature point): padded CSR, rows start at multiples of 4,
+  // columns ascending in the internal order, padding repeats the last column with value 0
   nesa::cplxf *d_nz_val32 = nullptr;
+  int64_t *d_nz_ptr4 = nullptr;
+  int32_t *d_nz_col4 = nullptr;
+  int32_t *d_perm = nullptr;           // internal index -> ABI index
+  nesa::cplxf *d_xp = nullptr;         // x in the internal order, complex64 [nrhs][n]
   nesa::cplxf *d_V32 = nullptr;
   int nrhs_cap32 = 0;
   // levels
@@ -136,6 +143,7 @@ cudaEvent_t take_event(nesa_ctx *c);
 // tensor-core translations of the mixed product (nesa_tc.cu)
 void tc_build(nesa_ctx *c);
 void tc_translate_level(nesa_ctx *c, int l, const cplxf *s, cplxf *o, const cplxf *op, const cplxf *Ct, int nrhs);
+void tc_upward_level(nesa_ctx *c, int l, const cplxf *s, cplxf *sp, int nrhs);
 int tc_take_error(nesa_ctx *c);
 void tc_free(nesa_ctx *c);
 void tc_tuning(nesa_ctx *c, int32_t *tn, float *ms);

@@ -18,7 +18,10 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <thread>
 #include <type_traits>
+#include <utility>
+#include <vector>
 
 #include "nesa_device.cuh"
 
@@ -49,6 +52,8 @@ int ensure_workspace(nesa_ctx *c, int nrhs) {
 
 static void ensure_workspace32(nesa_ctx *c, int nrhs) {
   if (nrhs <= c->nrhs_cap32) return;
+  dfree(c, c->d_xp);
+  c->d_xp = (cplxf *)dalloc(c, sizeof(cplxf) * (size_t)std::max<int64_t>(1, c->n * nrhs));
   for (int l = c->l0; l <= c->L; ++l) {
     DevLevel &d = c->lev[l];
     dfree(c, d.s32);
@@ -266,6 +271,102 @@ __global__ void __launch_bounds__(256) k_near_receive(cplx *__restrict__ y, cons
   }
 }
 
+// Near field + reception of the mixed product.  Warp r handles the internal row r
+// (ABI row m = perm[r]): the near part runs over the padded complex64 CSR with four
+// entries per lane and step (16- and 32-byte streaming loads) and gathers x from its
+// internal-order complex64 copy xp; reception reads each V column and the leaf's
+// outgoing field as contiguous 4Q-value blocks, two values per lane and load.
+template <int RB>
+__global__ void __launch_bounds__(256) k_near_receive_v(cplx *__restrict__ y, const cplxf *__restrict__ xp, int64_t n,
+                                                        int nrhs, const int32_t *__restrict__ perm,
+                                                        const int64_t *__restrict__ nz_ptr,
+                                                        const int32_t *__restrict__ nz_col,
+                                                        const cplxf *__restrict__ nz_val,
+                                                        const int32_t *__restrict__ rx_ptr,
+                                                        const int32_t *__restrict__ rx_col,
+                                                        const int32_t *__restrict__ vc_leaf,
+                                                        const cplxf *__restrict__ V, const cplxf *__restrict__ oL,
+                                                        int q, double eta_k, double inv_k2, int parts) {
+  const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (r >= n) return;
+  const int32_t m = perm[r];
+  const int64_t z0 = nz_ptr[r], z1 = nz_ptr[r + 1];
+  const int32_t f0 = rx_ptr[m], f1 = rx_ptr[m + 1];
+  const int q4 = 4 * q;
+  const float mk2 = (float)(-inv_k2);
+  for (int r0 = 0; r0 < nrhs; r0 += RB) {
+    const int rb = min(RB, nrhs - r0);
+    cplxf near[RB] = {}, far[RB] = {};
+    if (parts & NESA_PART_NEAR) {
+      const cplxf *xr = xp + (int64_t)r0 * n;
+      for (int64_t e = z0 + 4 * lane; e < z1; e += 128) {
+        const int4 k = __ldcs((const int4 *)(nz_col + e));
+        const float4 va = __ldcs((const float4 *)(nz_val + e));
+        const float4 vb = __ldcs((const float4 *)(nz_val + e + 2));
+#pragma unroll
+        for (int rr = 0; rr < RB; ++rr)
+          if (rr < rb) {
+            const cplxf *xq = xr + (int64_t)rr * n;
+            cfma(near[rr], make_float2(va.x, va.y), xq[k.x]);
+            cfma(near[rr], make_float2(va.z, va.w), xq[k.y]);
+            cfma(near[rr], make_float2(vb.x, vb.y), xq[k.z]);
+            cfma(near[rr], make_float2(vb.z, vb.w), xq[k.w]);
+          }
+      }
+    }
+    if (parts & NESA_PART_FAR) {
+      for (int32_t e = f0; e < f1; ++e) {
+        const int32_t g = rx_col[e];
+        const cplxf *vg = V + (int64_t)g * q4;  // [ch][i]
+        const cplxf *ol = oL + ((int64_t)vc_leaf[g] * 4 * nrhs + 4 * r0) * q;
+        for (int j = 2 * lane; j < q4; j += 64) {  // values j, j+1 (q4 is even)
+          const float4 v2 = __ldcs((const float4 *)(vg + j));
+          const float g0 = j < 3 * q ? 1.0f : mk2, g1 = j + 1 < 3 * q ? 1.0f : mk2;
+          const cplxf v0 = make_float2(g0 * v2.x, g0 * v2.y), v1 = make_float2(g1 * v2.z, g1 * v2.w);
+#pragma unroll
+          for (int rr = 0; rr < RB; ++rr)
+            if (rr < rb) {
+              const float4 o2 = *(const float4 *)(ol + (int64_t)rr * q4 + j);
+              cfma(far[rr], v0, make_float2(o2.x, o2.y));
+              cfma(far[rr], v1, make_float2(o2.z, o2.w));
+            }
+        }
+      }
+    }
+#pragma unroll
+    for (int rr = 0; rr < RB; ++rr) {
+      double2 v = make_double2((double)near[rr].x + eta_k * (double)far[rr].y,
+                               (double)near[rr].y - eta_k * (double)far[rr].x);
+      for (int off = 16; off > 0; off >>= 1) {
+        v.x += __shfl_down_sync(0xffffffffu, v.x, off);
+        v.y += __shfl_down_sync(0xffffffffu, v.y, off);
+      }
+      if (lane == 0 && rr < rb) y[(int64_t)(r0 + rr) * n + m] = v;
+    }
+  }
+}
+
+// xp[r][i] = complex64(x[r][perm[i]])
+__global__ void k_perm_x(cplxf *__restrict__ xp, const cplx *__restrict__ x, const int32_t *__restrict__ perm,
+                         int64_t n, int nrhs) {
+  const int64_t total = n * nrhs;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t / n, i = t % n;
+    const cplx v = x[r * n + perm[i]];
+    xp[t] = make_float2((float)v.x, (float)v.y);
+  }
+}
+
+// val4[e] = complex64(val[src[e]]), 0 where src[e] < 0
+__global__ void k_gather_near(cplxf *__restrict__ val4, const int64_t *__restrict__ src, const cplx *__restrict__ val,
+                              int64_t nnz4) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz4; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = src[e];
+    val4[e] = s >= 0 ? make_float2((float)val[s].x, (float)val[s].y) : make_float2(0.0f, 0.0f);
+  }
+}
+
 static inline unsigned grid_for(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
 // Stage timing: an event before and after a launch when profiling is on.
@@ -328,6 +429,12 @@ static void run_product(nesa_ctx *c, const OpView<CT> &op, const cplx *x, cplx *
       size_t smem = sizeof(CT) * 4 * (size_t)d.q;
       StageScope sc(c, 1, 32.0 * nrhs * d.nbox * (double)p.q * d.q,
                     B * (8.0 * p.q * d.q + 4.0 * nrhs * ((double)d.nbox * d.q + (double)p.nbox * p.q)));
+      if constexpr (std::is_same<CT, cplxf>::value) {
+        if (c->tc_enabled) {
+          tc_upward_level(c, l, op.s[l], op.s[l - 1], nrhs);
+          continue;
+        }
+      }
       k_upward<CT><<<dim3((unsigned)p.nbox, t.ntile), t.threads, smem, st>>>(op.s[l - 1], op.s[l], op.C[l],
                                                                              p.child_ptr, d.octant, nrhs, p.q, d.q,
                                                                              t.tr);
@@ -361,10 +468,20 @@ static void run_product(nesa_ctx *c, const OpView<CT> &op, const cplx *x, cplx *
               ((parts & NESA_PART_FAR) ? B * 4.0 * ncol * dL.q + B * 4.0 * nrhs * dL.nbox * dL.q : 0.0) +
               16.0 * 2.0 * nrhs * c->n;
   StageScope sc(c, 3, fl, by);
-  auto near = nrhs == 1 ? k_near_receive<CT, 1> : k_near_receive<CT, 4>;
-  near<<<grid_for(c->n * 32, 256), 256, 0, st>>>(y, x, c->n, nrhs, c->d_nz_ptr, c->d_nz_col, op.nz_val, c->d_rx_ptr,
-                                                c->d_rx_col, c->d_vc_leaf, op.V, op.o[L], dL.q, c->eta * c->k,
-                                                1.0 / (c->k * c->k), parts);
+  if constexpr (std::is_same<CT, cplxf>::value) {
+    if (parts & NESA_PART_NEAR)
+      k_perm_x<<<(unsigned)std::min<int64_t>((c->n * nrhs + 255) / 256, 1 << 16), 256, 0, st>>>(c->d_xp, x, c->d_perm,
+                                                                                            c->n, nrhs);
+    auto near = nrhs == 1 ? k_near_receive_v<1> : k_near_receive_v<4>;
+    near<<<grid_for(c->n * 32, 256), 256, 0, st>>>(y, c->d_xp, c->n, nrhs, c->d_perm, c->d_nz_ptr4, c->d_nz_col4,
+                                                  op.nz_val, c->d_rx_ptr, c->d_rx_col, c->d_vc_leaf, op.V, op.o[L],
+                                                  dL.q, c->eta * c->k, 1.0 / (c->k * c->k), parts);
+  } else {
+    auto near = nrhs == 1 ? k_near_receive<CT, 1> : k_near_receive<CT, 4>;
+    near<<<grid_for(c->n * 32, 256), 256, 0, st>>>(y, x, c->n, nrhs, c->d_nz_ptr, c->d_nz_col, op.nz_val,
+                                                  c->d_rx_ptr, c->d_rx_col, c->d_vc_leaf, op.V, op.o[L], dL.q,
+                                                  c->eta * c->k, 1.0 / (c->k * c->k), parts);
+  }
 }
 
 // Launch the product on the context's stream.
@@ -412,8 +529,69 @@ static cplxf *copy_c64(nesa_ctx *c, const cplx *src, int64_t n) {
   return d;
 }
 
+// Near field of the mixed product in the internal order: RWG functions sorted (stably)
+// by the leaf of their first quadrature point, leaves in Morton order, so that the
+// near columns of a row form a few contiguous runs and neighbouring rows share them.
+// Rows are padded to multiples of 4 entries; columns are renumbered and sorted.
+static void build_near_internal(nesa_ctx *c) {
+  const HostModel &h = c->h;
+  const int64_t n = c->n;
+  // the near pattern lives on the device only (the host copy is released after upload)
+  std::vector<int64_t> nz_ptr(n + 1);
+  check_cuda(cudaMemcpy(nz_ptr.data(), c->d_nz_ptr, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost), "near ptr");
+  std::vector<int32_t> nz_col(std::max<int64_t>(nz_ptr[n], 1));
+  check_cuda(cudaMemcpy(nz_col.data(), c->d_nz_col, sizeof(int32_t) * nz_ptr[n], cudaMemcpyDeviceToHost), "near col");
+  std::vector<int32_t> perm(n), inv(n);
+  for (int64_t m = 0; m < n; ++m) perm[m] = (int32_t)m;
+  auto leaf_of = [&](int32_t m) { return h.pt_leaf[7 * (int64_t)h.rwg_tri[2 * (int64_t)m]]; };
+  std::stable_sort(perm.begin(), perm.end(), [&](int32_t a, int32_t b) { return leaf_of(a) < leaf_of(b); });
+  for (int64_t r = 0; r < n; ++r) inv[perm[r]] = (int32_t)r;
+  std::vector<int64_t> ptr4(n + 1, 0);
+  for (int64_t r = 0; r < n; ++r) {
+    const int32_t m = perm[r];
+    ptr4[r + 1] = ptr4[r] + ((nz_ptr[m + 1] - nz_ptr[m] + 3) / 4) * 4;
+  }
+  const int64_t nnz4 = std::max<int64_t>(ptr4[n], 4);
+  std::vector<int32_t> col4(nnz4, 0);
+  std::vector<int64_t> src(nnz4, -1);
+  auto fill_rows = [&](int64_t r_begin, int64_t r_end) {
+    std::vector<std::pair<int32_t, int64_t>> row;
+    for (int64_t r = r_begin; r < r_end; ++r) {
+      const int32_t m = perm[r];
+      const int64_t s0 = nz_ptr[m], len = nz_ptr[m + 1] - s0;
+      row.resize(len);
+      for (int64_t j = 0; j < len; ++j) row[j] = {inv[nz_col[s0 + j]], s0 + j};
+      std::sort(row.begin(), row.end());
+      const int64_t p = ptr4[r];
+      for (int64_t j = 0; j < len; ++j) {
+        col4[p + j] = row[j].first;
+        src[p + j] = row[j].second;
+      }
+      const int32_t last = len > 0 ? row[len - 1].first : (int32_t)r;
+      for (int64_t j = len; j < ptr4[r + 1] - p; ++j) col4[p + j] = last;
+    }
+  };
+  const int nth = (int)std::max<unsigned>(1, std::min<unsigned>(16, std::thread::hardware_concurrency()));
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nth; ++t) pool.emplace_back(fill_rows, n * t / nth, n * (t + 1) / nth);
+  for (auto &th : pool) th.join();
+  c->d_perm = (int32_t *)dalloc(c, sizeof(int32_t) * std::max<int64_t>(n, 1));
+  c->d_nz_ptr4 = (int64_t *)dalloc(c, sizeof(int64_t) * (n + 1));
+  c->d_nz_col4 = (int32_t *)dalloc(c, sizeof(int32_t) * nnz4);
+  c->d_nz_val32 = (cplxf *)dalloc(c, sizeof(cplxf) * nnz4);
+  int64_t *d_src = (int64_t *)dalloc(c, sizeof(int64_t) * nnz4);
+  check_cuda(cudaMemcpy(c->d_perm, perm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice), "near order");
+  check_cuda(cudaMemcpy(c->d_nz_ptr4, ptr4.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice), "near order");
+  check_cuda(cudaMemcpy(c->d_nz_col4, col4.data(), sizeof(int32_t) * nnz4, cudaMemcpyHostToDevice), "near order");
+  check_cuda(cudaMemcpy(d_src, src.data(), sizeof(int64_t) * nnz4, cudaMemcpyHostToDevice), "near order");
+  k_gather_near<<<(unsigned)std::min<int64_t>((nnz4 + 255) / 256, 1 << 16), 256, 0, c->stream>>>(
+      c->d_nz_val32, d_src, c->d_nz_val, nnz4);
+  check_cuda(cudaStreamSynchronize(c->stream), "near order");
+  dfree(c, d_src);
+}
+
 void build_mixed(nesa_ctx *c) {
-  c->d_nz_val32 = copy_c64(c, c->d_nz_val, c->info.near_nnz);
+  build_near_internal(c);
   c->d_V32 = copy_c64(c, c->d_V, 4 * c->info.v_columns * (int64_t)c->lev[c->L].q);
   for (int l = c->l0; l <= c->L; ++l) {
     DevLevel &d = c->lev[l];

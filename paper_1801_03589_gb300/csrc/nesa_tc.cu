@@ -36,11 +36,13 @@ struct TcGemm {
 };
 
 struct TcLevel {
-  TcGemm tr, dn;  // translations (Eq. 12); potential transfer (Eq. 13, l > l0)
-  int rc = 0;     // right-hand sides per chunk the buffers below are sized for
+  TcGemm tr, dn, up;  // translations (Eq. 12); potential transfer (Eq. 13) and source
+                      // transfer to the parent level (Eq. 11), both for l > l0
+  int rc = 0;         // right-hand sides per chunk the buffers below are sized for
   __nv_bfloat16 *s_hi = nullptr, *s_lo = nullptr;  // [nbox][rc][tr.nkc][256]
   __nv_bfloat16 *o_hi = nullptr, *o_lo = nullptr;  // [parent boxes][rc][dn.nkc][256]
   cplxf *P = nullptr;                              // [nil + nbox][4 rc][q]
+  cplxf *P_up = nullptr;                           // [nbox][4 rc][q of the parent level]
 };
 
 struct TcState {
@@ -185,9 +187,14 @@ void tc_build(nesa_ctx *c) {
     for (size_t e = 0; e < dst.size(); ++e) dst[e] = (int32_t)e;
     gemm_setup(c, t.tr, d.D, d.noff, d.q, d.q, hl.il_slot, dst, hl.il_src);
     if (l > c->l0) {  // potential transfer: entry = box a, slot = octant, source = parent
-      std::vector<int32_t> bd(d.nbox);
-      for (int64_t a = 0; a < d.nbox; ++a) bd[a] = (int32_t)(d.nil + a);
+      std::vector<int32_t> bd(d.nbox), id(d.nbox);
+      for (int64_t a = 0; a < d.nbox; ++a) {
+        bd[a] = (int32_t)(d.nil + a);
+        id[a] = (int32_t)a;
+      }
       gemm_setup(c, t.dn, d.Ct, 8, d.q, c->lev[l - 1].q, hl.octant, bd, hl.parent);
+      // source transfer: entry = child box a, slot = octant, source = a, block a of P_up
+      gemm_setup(c, t.up, d.C, 8, c->lev[l - 1].q, d.q, hl.octant, id, id);
     }
   }
   check_cuda(cudaStreamSynchronize(c->stream), "tc build");
@@ -303,7 +310,9 @@ static void prepare_rc(nesa_ctx *c, TcLevel &t, int l, int rc) {
   dfree(c, t.o_hi);
   dfree(c, t.o_lo);
   dfree(c, t.P);
+  dfree(c, t.P_up);
   t.o_hi = t.o_lo = nullptr;
+  t.P_up = nullptr;
   t.s_hi = (__nv_bfloat16 *)dalloc(c, sizeof(__nv_bfloat16) * (size_t)d.nbox * rc * t.tr.nkc * tc::GROUP_ELEMS);
   t.s_lo = (__nv_bfloat16 *)dalloc(c, sizeof(__nv_bfloat16) * (size_t)d.nbox * rc * t.tr.nkc * tc::GROUP_ELEMS);
   int64_t nblk = d.nil;
@@ -312,9 +321,21 @@ static void prepare_rc(nesa_ctx *c, TcLevel &t, int l, int rc) {
     t.o_hi = (__nv_bfloat16 *)dalloc(c, sizeof(__nv_bfloat16) * (size_t)np * rc * t.dn.nkc * tc::GROUP_ELEMS);
     t.o_lo = (__nv_bfloat16 *)dalloc(c, sizeof(__nv_bfloat16) * (size_t)np * rc * t.dn.nkc * tc::GROUP_ELEMS);
     nblk += d.nbox;
+    t.P_up = (cplxf *)dalloc(c, sizeof(cplxf) * (size_t)d.nbox * 4 * rc * c->lev[l - 1].q);
   }
   t.P = (cplxf *)dalloc(c, sizeof(cplxf) * (size_t)std::max<int64_t>(1, nblk) * 4 * rc * d.q);
   t.rc = rc;
+}
+
+// Right-hand sides per chunk at level l: the largest divisor of nrhs for which the
+// per-pair output P stays within about 1 GB.
+static int level_rc(nesa_ctx *c, int l, int nrhs) {
+  const DevLevel &d = c->lev[l];
+  const bool down = l > c->l0;
+  const double per_rhs = 4.0 * 8.0 * d.q * (double)std::max<int64_t>(1, d.nil + (down ? d.nbox : 0));
+  int rc = (int)std::max(1.0, std::min((double)nrhs, 1.0e9 / per_rhs));
+  while (nrhs % rc) --rc;
+  return rc;
 }
 
 static inline unsigned grid_of(int64_t n) { return (unsigned)std::min<int64_t>((n + 255) / 256, 1 << 20); }
@@ -327,11 +348,7 @@ void tc_translate_level(nesa_ctx *c, int l, const cplxf *s, cplxf *o, const cplx
   const DevLevel &d = c->lev[l];
   cudaStream_t st = c->stream;
   const bool down = op != nullptr && l > c->l0;
-  // right-hand sides go through in equal chunks of rc, so that P stays within about
-  // 1 GB (rc = the largest divisor of nrhs that fits)
-  const double per_rhs = 4.0 * 8.0 * d.q * (double)std::max<int64_t>(1, d.nil + (down ? d.nbox : 0));
-  int rc = (int)std::max(1.0, std::min((double)nrhs, 1.0e9 / per_rhs));
-  while (nrhs % rc) --rc;
+  const int rc = level_rc(c, l, nrhs);  // right-hand sides go through in equal chunks
   prepare_rc(c, t, l, rc);
   for (int r0 = 0; r0 < nrhs; r0 += rc) {
     k_split<<<grid_of(d.nbox * rc * t.tr.nkc * (int64_t)tc::GROUP_ELEMS), 256, 0, st>>>(t.s_hi, t.s_lo, s, d.nbox,
@@ -370,6 +387,26 @@ void tc_translate_level(nesa_ctx *c, int l, const cplxf *s, cplxf *o, const cplx
     }
     k_pair_reduce<<<dim3((unsigned)d.nbox, (unsigned)((4 * rc * d.q + 255) / 256)), 256, 0, st>>>(
         o, t.P, d.il_ptr, down ? d.nil : -1, nrhs, r0, rc, d.q);
+  }
+}
+
+// Source transfer from level l to its parent level on the tensor cores (Eq. 11):
+// s_P = sum over the children a of P of C_l(octant of a) s_a.
+void tc_upward_level(nesa_ctx *c, int l, const cplxf *s, cplxf *sp, int nrhs) {
+  TcState *S = state(c);
+  TcLevel &t = S->lev[l];
+  const DevLevel &d = c->lev[l], &p = c->lev[l - 1];
+  cudaStream_t st = c->stream;
+  const int rc = level_rc(c, l, nrhs);
+  prepare_rc(c, t, l, rc);
+  for (int r0 = 0; r0 < nrhs; r0 += rc) {
+    k_split<<<grid_of(d.nbox * rc * t.tr.nkc * (int64_t)tc::GROUP_ELEMS), 256, 0, st>>>(t.s_hi, t.s_lo, s, d.nbox,
+                                                                                       nrhs, r0, rc, d.q, t.tr.nkc);
+    if (c->autotune && t.up.tuned_rc != rc) autotune(c, t.up, t.s_hi, t.s_lo, t.P_up, rc);
+    make_work(c, t.up, rc, t.up.tn);
+    launch_gemm(c, t.up, t.s_hi, t.s_lo, t.P_up, rc);
+    k_pair_reduce<<<dim3((unsigned)p.nbox, (unsigned)((4 * rc * p.q + 255) / 256)), 256, 0, st>>>(
+        sp, t.P_up, p.child_ptr, -1, nrhs, r0, rc, p.q);
   }
 }
 
