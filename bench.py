@@ -272,7 +272,7 @@ def run_ours(args, world, rank, local):
         pg = dist
     cfg = get_config(args.workload)
     g = nesa.Nesa(cfg["vertices"], cfg["triangles"], cfg["k"], leaf_size=cfg["leaf_size"], n_levels=cfg["n_levels"],
-                  precision=nesa.MIXED, translate=nesa.TRANSLATE_TENSOR)
+                  precision=nesa.MIXED, translate=nesa.TRANSLATE_TENSOR, tile_n=args.tile_n)
     info = g.info()
     stream = torch.cuda.Stream()
     g.set_stream(stream)
@@ -386,8 +386,8 @@ def run_ours(args, world, rank, local):
     # their split and reduction kernels
     peaks = _peaks()
     gemm = prof_mx["translation_tensor_gemm"]
-    rest = {"ms": prof_mx["translation"]["ms"] - gemm["ms"], "flops": 0.0,
-            "bytes": prof_mx["translation"]["bytes"] - gemm["bytes"]}
+    rest = {"ms": max(0.0, prof_mx["translation"]["ms"] - gemm["ms"]), "flops": 0.0,
+            "bytes": max(0.0, prof_mx["translation"]["bytes"] - gemm["bytes"])}
     kernels = {"k_tc_gemm": (gemm, "tensor"), "k_near_receive<float2>": (prof_mx["near_reception"], "hbm"),
                "k_upward<float2>": (prof_mx["source_transfer"], "alu"),
                "k_radiate<float2>": (prof_mx["radiation"], "hbm"),
@@ -473,6 +473,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--fp64-solve", action="store_true", help="also time the plain FP64 solve (about 2 minutes)")
     ap.add_argument("--workload", default=CONFIG, help="workload name (smaller ones are for profiling runs)")
+    ap.add_argument("--tile-n", type=int, default=0, choices=[0, 64, 128, 256],
+                    help="fixed column-tile width of the tensor GEMMs (0: autotune); for runs under a profiler")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":

@@ -100,6 +100,10 @@ typedef struct {
  *               Frobenius norm of the fitted matrix
  *   precision   NESA_FP64 or NESA_MIXED
  *   translate   NESA_TRANSLATE_* engine of the mixed product's translations
+ *   tile_n      column-tile width of the tensor-core GEMMs (64, 128 or 256); 0 lets
+ *               the autotuner time the three widths at the first mixed product and
+ *               keep the fastest per GEMM family (a fixed width makes runs under a
+ *               profiler, which distorts the tuner's timings, use the tuned layout)
  */
 typedef struct {
   double leaf_size;
@@ -112,7 +116,8 @@ typedef struct {
   double rho_test;
   double pinv_eps;
   int32_t translate;
-  int32_t reserved[3];
+  int32_t tile_n;
+  int32_t reserved[2];
 } nesa_params;
 
 /* Sizes of a built operator (host struct filled by nesa_get_info). */

@@ -39,7 +39,7 @@ class Params(ctypes.Structure):
     _fields_ = [("leaf_size", ctypes.c_double), ("n_levels", ctypes.c_int32), ("q_mode", ctypes.c_int32),
                 ("q_fixed", ctypes.c_int32), ("precision", ctypes.c_int32), ("q_digits", ctypes.c_double),
                 ("rho_eq", ctypes.c_double), ("rho_test", ctypes.c_double), ("pinv_eps", ctypes.c_double),
-                ("translate", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("translate", ctypes.c_int32), ("tile_n", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class Info(ctypes.Structure):

@@ -708,7 +708,9 @@ int nesa_build(const nesa_mesh *mesh, double k, const nesa_params *params, nesa_
   if (!(k > 0.0) || !(params->leaf_size > 0.0) || params->n_levels < 1 || params->n_levels > NESA_MAX_LEVELS ||
       (params->q_mode != NESA_Q_FIXED && params->q_mode != NESA_Q_AUTO) || params->q_fixed < 1 ||
       (params->precision != NESA_FP64 && params->precision != NESA_MIXED) || params->translate < 0 ||
-      params->translate > 1 || !(params->rho_eq > 0.0) || !(params->rho_test > params->rho_eq) ||
+      params->translate > 1 ||
+      (params->tile_n != 0 && params->tile_n != 64 && params->tile_n != 128 && params->tile_n != 256) ||
+      !(params->rho_eq > 0.0) || !(params->rho_test > params->rho_eq) ||
       !(params->pinv_eps >= 0.0) || mesh->n_triangles > (1LL << 28))
     return NESA_ERR_INVALID_ARG;
   auto t0 = std::chrono::steady_clock::now();
@@ -757,7 +759,11 @@ int nesa_build(const nesa_mesh *mesh, double k, const nesa_params *params, nesa_
   if (params->precision == NESA_MIXED) {
     try {
       build_mixed(c);
-      if (params->translate == NESA_TRANSLATE_TENSOR) tc_build(c);
+      if (params->translate == NESA_TRANSLATE_TENSOR) {
+        c->autotune = params->tile_n == 0;
+        c->fixed_tn = params->tile_n;
+        tc_build(c);
+      }
     } catch (const Error &e) {
       g_last_error = e.what;
       free_ctx(c);

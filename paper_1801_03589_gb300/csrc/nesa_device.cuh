@@ -127,6 +127,7 @@ struct nesa_ctx {
   void *precond = nullptr;       // preconditioner state (nesa_precond.cu)
   bool tc_enabled = false;
   bool autotune = true;          // tune the GEMM tile width at the first product per chunk size
+  int fixed_tn = 0;              // tile width used when the autotuner is off
   std::vector<void *> allocs;    // every device allocation owned by the context
 };
 

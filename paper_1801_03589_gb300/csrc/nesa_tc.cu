@@ -197,6 +197,8 @@ void tc_build(nesa_ctx *c) {
       gemm_setup(c, t.up, d.C, 8, c->lev[l - 1].q, d.q, hl.octant, id, id);
     }
   }
+  if (c->fixed_tn)
+    for (int l = c->l0; l <= c->L; ++l) S->lev[l].tr.tn = S->lev[l].dn.tn = S->lev[l].up.tn = c->fixed_tn;
   check_cuda(cudaStreamSynchronize(c->stream), "tc build");
   c->tc_enabled = true;
 }
