@@ -48,46 +48,59 @@ struct SolveWork {
 
 static const int kChunk = 2048;  // vector elements per partial-sum block
 
-// part[(r*(jmax) + i)*nchunk + c] = sum over chunk c of conj(V_i[r]) w[r]   (i < ni)
-__global__ void k_dots(double2 *part, const cplx *V, const cplx *w, int ni, int64_t n, int nrhs, int nchunk) {
-  const int c = blockIdx.x, r = blockIdx.y;
+// part[(r*ni + i)*nchunk + c] = sum over chunk c of conj(V_i[r]) w[r]   (i < ni).
+// Grid (chunk, tile of kDotTile vectors, column r): every thread reads w once per
+// element and keeps kDotTile complex sums in registers.  Per vector the order of the
+// additions is the same as one dot at a time (thread strides, warp tree, warps in order).
+static const int kDotTile = 8;
+__global__ void __launch_bounds__(256) k_dots(double2 *part, const cplx *V, const cplx *w, int ni, int64_t n,
+                                              int nrhs, int nchunk) {
+  const int c = blockIdx.x, i0 = blockIdx.y * kDotTile, r = blockIdx.z;
+  const int nt = min(kDotTile, ni - i0);
   const int64_t lo = (int64_t)c * kChunk, hi = min(n, lo + kChunk);
-  __shared__ double sre[32], sim[32];
+  __shared__ double sre[8][kDotTile], sim[8][kDotTile];
   const cplx *wr = w + (int64_t)r * n;
-  for (int i = 0; i < ni; ++i) {
-    const cplx *vi = V + ((int64_t)i * nrhs + r) * n;
-    double re = 0.0, im = 0.0;
-    for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
-      cplx a = vi[e], b = wr[e];
-      re = fma(a.x, b.x, re);
-      re = fma(a.y, b.y, re);
-      im = fma(a.x, b.y, im);
-      im = fma(-a.y, b.x, im);
-    }
-    for (int off = 16; off > 0; off >>= 1) {
-      re += __shfl_down_sync(0xffffffffu, re, off);
-      im += __shfl_down_sync(0xffffffffu, im, off);
-    }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) {
-      sre[wid] = re;
-      sim[wid] = im;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double a = 0.0, b = 0.0;
-      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
-        a += sre[k];
-        b += sim[k];
+  double re[kDotTile], im[kDotTile];
+#pragma unroll
+  for (int t = 0; t < kDotTile; ++t) re[t] = im[t] = 0.0;
+  for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+    const cplx b = wr[e];
+#pragma unroll
+    for (int t = 0; t < kDotTile; ++t)
+      if (t < nt) {
+        const cplx a = V[((int64_t)(i0 + t) * nrhs + r) * n + e];
+        re[t] = fma(a.x, b.x, re[t]);
+        re[t] = fma(a.y, b.y, re[t]);
+        im[t] = fma(a.x, b.y, im[t]);
+        im[t] = fma(-a.y, b.x, im[t]);
       }
-      part[((int64_t)r * ni + i) * nchunk + c] = make_double2(a, b);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int t = 0; t < kDotTile; ++t) {
+    for (int off = 16; off > 0; off >>= 1) {
+      re[t] += __shfl_down_sync(0xffffffffu, re[t], off);
+      im[t] += __shfl_down_sync(0xffffffffu, im[t], off);
     }
-    __syncthreads();
+    if (lane == 0) {
+      sre[wid][t] = re[t];
+      sim[wid][t] = im[t];
+    }
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < nt) {
+    const int t = threadIdx.x;
+    double a = 0.0, bb = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      a += sre[k][t];
+      bb += sim[k][t];
+    }
+    part[((int64_t)r * ni + i0 + t) * nchunk + c] = make_double2(a, bb);
   }
 }
 
-// h[r][i] (+)= sum_c part  (accumulate when add != 0)
-__global__ void k_dots_reduce(cplx *h, int ldh, const double2 *part, int ni, int nchunk, int add) {
+// h[r][i] (+)= sum_c part (accumulate when add != 0); y[r][i] = the same sum
+__global__ void k_dots_reduce(cplx *h, int ldh, cplx *y, int ldy, const double2 *part, int ni, int nchunk, int add) {
   const int i = blockIdx.x, r = blockIdx.y;
   double re = 0.0, im = 0.0;
   for (int c = threadIdx.x; c < nchunk; c += blockDim.x) {
@@ -107,6 +120,7 @@ __global__ void k_dots_reduce(cplx *h, int ldh, const double2 *part, int ni, int
     } else {
       o = make_double2(re, im);
     }
+    y[(int64_t)r * ldy + i] = make_double2(re, im);
   }
 }
 
@@ -116,6 +130,7 @@ __global__ void k_subtract(cplx *w, const cplx *V, const cplx *coef, int ldc, in
   const cplx *cr = coef + (int64_t)r * ldc;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     cplx acc = w[(int64_t)r * n + e];
+#pragma unroll 4
     for (int i = 0; i < ni; ++i) {
       cplx v = V[((int64_t)i * nrhs + r) * n + e];
       cplx c = cr[i];
@@ -132,6 +147,7 @@ __global__ void k_update_x(cplx *x, const cplx *V, const cplx *y, int ldy, const
   const int k = steps[r];
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     cplx acc = x[(int64_t)r * n + e];
+#pragma unroll 4
     for (int i = 0; i < k; ++i) cfma(acc, V[((int64_t)i * nrhs + r) * n + e], y[(int64_t)r * ldy + i]);
     x[(int64_t)r * n + e] = acc;
   }
@@ -388,11 +404,11 @@ static int gmres_run(nesa_ctx *c, const cplx *b, cplx *x, int nrhs, double tol, 
         I.matvecs += 1;
         // CGS2: two rounds of projection onto V_0..V_j
         for (int pass = 0; pass < 2; ++pass) {
-          k_dots<<<dim3(nchunk, nrhs), 256, 0, st>>>((double2 *)W->part, W->V, W->w, j + 1, n, nrhs, nchunk);
-          k_dots_reduce<<<dim3(j + 1, nrhs), 32, 0, st>>>(W->h + 0, m + 1, (const double2 *)W->part, j + 1, nchunk,
-                                                           pass);
-          // subtract with this pass's coefficients: use y as scratch for them
-          k_dots_reduce<<<dim3(j + 1, nrhs), 32, 0, st>>>(W->y, m, (const double2 *)W->part, j + 1, nchunk, 0);
+          k_dots<<<dim3(nchunk, (j + kDotTile) / kDotTile, nrhs), 256, 0, st>>>((double2 *)W->part, W->V, W->w,
+                                                                               j + 1, n, nrhs, nchunk);
+          // h accumulates both passes; y holds this pass's coefficients for the subtraction
+          k_dots_reduce<<<dim3(j + 1, nrhs), 32, 0, st>>>(W->h, m + 1, W->y, m, (const double2 *)W->part, j + 1,
+                                                           nchunk, pass);
           k_subtract<<<vgrid, 256, 0, st>>>(W->w, W->V, W->y, m, j + 1, n, nrhs);
         }
         norms(W->w, W->nrm);

@@ -43,6 +43,8 @@ struct TcLevel {
   __nv_bfloat16 *o_hi = nullptr, *o_lo = nullptr;  // [parent boxes][rc][dn.nkc][256]
   cplxf *P = nullptr;                              // [nil + nbox][4 rc][q]
   cplxf *P_up = nullptr;                           // [nbox][4 rc][q of the parent level]
+  bool s_split = false;  // s_hi/s_lo hold the split of all right-hand sides of the current
+                         // product (set by the source transfer, used by the translation)
 };
 
 struct TcState {
@@ -353,8 +355,9 @@ void tc_translate_level(nesa_ctx *c, int l, const cplxf *s, cplxf *o, const cplx
   const int rc = level_rc(c, l, nrhs);  // right-hand sides go through in equal chunks
   prepare_rc(c, t, l, rc);
   for (int r0 = 0; r0 < nrhs; r0 += rc) {
-    k_split<<<grid_of(d.nbox * rc * t.tr.nkc * (int64_t)tc::GROUP_ELEMS), 256, 0, st>>>(t.s_hi, t.s_lo, s, d.nbox,
-                                                                                       nrhs, r0, rc, d.q, t.tr.nkc);
+    if (!(t.s_split && rc == nrhs))
+      k_split<<<grid_of(d.nbox * rc * t.tr.nkc * (int64_t)tc::GROUP_ELEMS), 256, 0, st>>>(t.s_hi, t.s_lo, s, d.nbox,
+                                                                                         nrhs, r0, rc, d.q, t.tr.nkc);
     if (down) {
       const DevLevel &p = c->lev[l - 1];
       k_split<<<grid_of(p.nbox * rc * t.dn.nkc * (int64_t)tc::GROUP_ELEMS), 256, 0, st>>>(
@@ -390,6 +393,7 @@ void tc_translate_level(nesa_ctx *c, int l, const cplxf *s, cplxf *o, const cplx
     k_pair_reduce<<<dim3((unsigned)d.nbox, (unsigned)((4 * rc * d.q + 255) / 256)), 256, 0, st>>>(
         o, t.P, d.il_ptr, down ? d.nil : -1, nrhs, r0, rc, d.q);
   }
+  t.s_split = false;
 }
 
 // Source transfer from level l to its parent level on the tensor cores (Eq. 11):
@@ -410,6 +414,7 @@ void tc_upward_level(nesa_ctx *c, int l, const cplxf *s, cplxf *sp, int nrhs) {
     k_pair_reduce<<<dim3((unsigned)p.nbox, (unsigned)((4 * rc * p.q + 255) / 256)), 256, 0, st>>>(
         sp, t.P_up, p.child_ptr, -1, nrhs, r0, rc, p.q);
   }
+  t.s_split = rc == nrhs;  // one chunk: the translation of this level can reuse the split
 }
 
 // tile widths chosen per level (0 where the level has no tensor work), for nesa_get_tuning
