@@ -89,13 +89,17 @@ static Tiling tiling(int q) {
   return {ntile, tr, threads};
 }
 
+// Source columns pass through shared memory in chunks of JC values per channel, so any
+// Q fits (the summation order over j is the same as with the whole column).
+constexpr int JC = 512;
+
 // ------------------------------------------------------------------ radiation (Eq. 10)
 template <typename CT>
 __global__ void __launch_bounds__(512) k_radiate(CT *__restrict__ s, const CT *__restrict__ V,
                                                  const int32_t *__restrict__ vc_ptr, const int32_t *__restrict__ vc_rwg,
                                                  const cplx *__restrict__ x, int64_t n, int nrhs, int q, int tr) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  CT *xs = (CT *)smem_raw;
+  CT *xs = (CT *)smem_raw;  // [JC]
   const int32_t b = blockIdx.x;
   const int tile = blockIdx.y;
   const int ch = threadIdx.x / tr;
@@ -104,15 +108,36 @@ __global__ void __launch_bounds__(512) k_radiate(CT *__restrict__ s, const CT *_
   const int32_t g0 = vc_ptr[b], ns = vc_ptr[b + 1] - g0;
   const CT *Vb = V + (int64_t)4 * g0 * q;
   for (int r = 0; r < nrhs; ++r) {
+    CT acc = {0, 0};
+    for (int j0 = 0; j0 < ns; j0 += JC) {
+      const int len = min(JC, ns - j0);
+      __syncthreads();
+      for (int j = threadIdx.x; j < len; j += blockDim.x) xs[j] = from64<CT>(x[(int64_t)r * n + vc_rwg[g0 + j0 + j]]);
+      __syncthreads();
+      if (!active) continue;
+      const CT *vp = Vb + (int64_t)4 * j0 * q + (int64_t)ch * q + i;
+#pragma unroll 4
+      for (int j = 0; j < len; ++j) cfma(acc, vp[(int64_t)4 * j * q], xs[j]);
+    }
+    if (active) s[((int64_t)b * 4 * nrhs + 4 * r + ch) * q + i] = acc;
+  }
+}
+
+// acc += M[i + j*ld] * col(ch)[j] over j < kdim, with the column (4 channels of kdim
+// values at src, channel stride kdim) staged through shared memory in chunks of JC
+template <typename CT>
+__device__ __forceinline__ void matvec_chunked(CT &acc, CT *col, const CT *__restrict__ src,
+                                               const CT *__restrict__ M, int64_t ld, int kdim, int ch, bool active) {
+  for (int j0 = 0; j0 < kdim; j0 += JC) {
+    const int len = min(JC, kdim - j0);
     __syncthreads();
-    for (int j = threadIdx.x; j < ns; j += blockDim.x) xs[j] = from64<CT>(x[(int64_t)r * n + vc_rwg[g0 + j]]);
+    for (int t = threadIdx.x; t < 4 * len; t += blockDim.x) col[t] = src[(int64_t)(t / len) * kdim + j0 + t % len];
     __syncthreads();
     if (!active) continue;
-    CT acc = {0, 0};
-    const CT *vp = Vb + (int64_t)ch * q + i;
+    const CT *Mj = M + (int64_t)j0 * ld;
+    const CT *cs = col + ch * len;
 #pragma unroll 4
-    for (int j = 0; j < ns; ++j) cfma(acc, vp[(int64_t)4 * j * q], xs[j]);
-    s[((int64_t)b * 4 * nrhs + 4 * r + ch) * q + i] = acc;
+    for (int j = 0; j < len; ++j) cfma(acc, Mj[(int64_t)j * ld], cs[j]);
   }
 }
 
@@ -123,7 +148,7 @@ __global__ void __launch_bounds__(512) k_upward(CT *__restrict__ sp, const CT *_
                                                 const CT *__restrict__ C, const int32_t *__restrict__ child_ptr,
                                                 const int32_t *__restrict__ octant, int nrhs, int qp, int q, int tr) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  CT *col = (CT *)smem_raw;  // [4][q]
+  CT *col = (CT *)smem_raw;  // [4][JC]
   const int32_t P = blockIdx.x;
   const int tile = blockIdx.y;
   const int ch = threadIdx.x / tr;
@@ -132,17 +157,9 @@ __global__ void __launch_bounds__(512) k_upward(CT *__restrict__ sp, const CT *_
   const int32_t c0 = child_ptr[P], c1 = child_ptr[P + 1];
   for (int r = 0; r < nrhs; ++r) {
     CT acc = {0, 0};
-    for (int32_t cb = c0; cb < c1; ++cb) {
-      __syncthreads();
-      const CT *src = sc + ((int64_t)cb * 4 * nrhs + 4 * r) * q;
-      for (int j = threadIdx.x; j < 4 * q; j += blockDim.x) col[j] = src[j];
-      __syncthreads();
-      if (!active) continue;
-      const CT *Cm = C + (int64_t)octant[cb] * qp * q + i;
-      const CT *cs = col + ch * q;
-#pragma unroll 4
-      for (int j = 0; j < q; ++j) cfma(acc, Cm[(int64_t)j * qp], cs[j]);
-    }
+    for (int32_t cb = c0; cb < c1; ++cb)
+      matvec_chunked(acc, col, sc + ((int64_t)cb * 4 * nrhs + 4 * r) * q, C + (int64_t)octant[cb] * qp * q + i,
+                     qp, q, ch, active);
     if (active) sp[((int64_t)P * 4 * nrhs + 4 * r + ch) * qp + i] = acc;
   }
 }
@@ -157,7 +174,7 @@ __global__ void __launch_bounds__(512) k_translate(CT *__restrict__ o, const CT 
                                                    const int32_t *__restrict__ octant, int nrhs, int q, int qp,
                                                    int tr) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  CT *col = (CT *)smem_raw;  // [4][max(q, qp)]
+  CT *col = (CT *)smem_raw;  // [4][JC]
   const int32_t a = blockIdx.x;
   const int tile = blockIdx.y;
   const int ch = threadIdx.x / tr;
@@ -166,30 +183,12 @@ __global__ void __launch_bounds__(512) k_translate(CT *__restrict__ o, const CT 
   const int32_t e0 = il_ptr[a], e1 = il_ptr[a + 1];
   for (int r = 0; r < nrhs; ++r) {
     CT acc = {0, 0};
-    if (op) {  // potential transfer from the parent (Eq. 13): o_a += C^T o_P
-      __syncthreads();
-      const int32_t P = parent[a];
-      const CT *src = op + ((int64_t)P * 4 * nrhs + 4 * r) * qp;
-      for (int j = threadIdx.x; j < 4 * qp; j += blockDim.x) col[j] = src[j];
-      __syncthreads();
-      if (active) {
-        const CT *Bm = Ct + (int64_t)octant[a] * q * qp + i;
-        const CT *cs = col + ch * qp;
-#pragma unroll 4
-        for (int j = 0; j < qp; ++j) cfma(acc, Bm[(int64_t)j * q], cs[j]);
-      }
-    }
-    for (int32_t e = e0; e < e1; ++e) {  // translations (Eq. 12)
-      __syncthreads();
-      const CT *src = s + ((int64_t)il_src[e] * 4 * nrhs + 4 * r) * q;
-      for (int j = threadIdx.x; j < 4 * q; j += blockDim.x) col[j] = src[j];
-      __syncthreads();
-      if (!active) continue;
-      const CT *Dm = D + (int64_t)il_slot[e] * q * q + i;
-      const CT *cs = col + ch * q;
-#pragma unroll 4
-      for (int j = 0; j < q; ++j) cfma(acc, Dm[(int64_t)j * q], cs[j]);
-    }
+    if (op)  // potential transfer from the parent (Eq. 13): o_a += C^T o_P
+      matvec_chunked(acc, col, op + ((int64_t)parent[a] * 4 * nrhs + 4 * r) * qp,
+                     Ct + (int64_t)octant[a] * q * qp + i, q, qp, ch, active);
+    for (int32_t e = e0; e < e1; ++e)  // translations (Eq. 12)
+      matvec_chunked(acc, col, s + ((int64_t)il_src[e] * 4 * nrhs + 4 * r) * q, D + (int64_t)il_slot[e] * q * q + i,
+                     q, q, ch, active);
     if (active) o[((int64_t)a * 4 * nrhs + 4 * r + ch) * q + i] = acc;
   }
 }
@@ -417,7 +416,7 @@ static void run_product(nesa_ctx *c, const OpView<CT> &op, const cplx *x, cplx *
     {  // radiation
       DevLevel &d = c->lev[L];
       Tiling t = tiling(d.q);
-      size_t smem = sizeof(CT) * (size_t)std::max(1, c->max_leaf_cols);
+      size_t smem = sizeof(CT) * (size_t)std::min(JC, std::max(1, c->max_leaf_cols));
       StageScope sc(c, 0, 32.0 * nrhs * ncol * d.q,
                     B * (4.0 * ncol * d.q + 4.0 * nrhs * d.nbox * d.q) + 16.0 * nrhs * c->n);
       k_radiate<CT><<<dim3((unsigned)d.nbox, t.ntile), t.threads, smem, st>>>(op.s[L], op.V, c->d_vc_ptr, c->d_vc_rwg,
@@ -426,7 +425,7 @@ static void run_product(nesa_ctx *c, const OpView<CT> &op, const cplx *x, cplx *
     for (int l = L; l > l0; --l) {  // source transfer
       DevLevel &d = c->lev[l], &p = c->lev[l - 1];
       Tiling t = tiling(p.q);
-      size_t smem = sizeof(CT) * 4 * (size_t)d.q;
+      size_t smem = sizeof(CT) * 4 * (size_t)std::min(JC, d.q);
       StageScope sc(c, 1, 32.0 * nrhs * d.nbox * (double)p.q * d.q,
                     B * (8.0 * p.q * d.q + 4.0 * nrhs * ((double)d.nbox * d.q + (double)p.nbox * p.q)));
       if constexpr (std::is_same<CT, cplxf>::value) {
@@ -444,7 +443,7 @@ static void run_product(nesa_ctx *c, const OpView<CT> &op, const cplx *x, cplx *
       Tiling t = tiling(d.q);
       const bool down = l > l0;
       const int qp = down ? c->lev[l - 1].q : 0;
-      size_t smem = sizeof(CT) * 4 * (size_t)std::max(d.q, qp);
+      size_t smem = sizeof(CT) * 4 * (size_t)std::min(JC, std::max(d.q, qp));
       double fl = 32.0 * nrhs * ((double)d.nil * d.q * d.q + (down ? (double)d.nbox * d.q * qp : 0.0));
       double by = B * ((double)d.noff * d.q * d.q + (down ? 8.0 * d.q * qp : 0.0) +
                        4.0 * nrhs * (2.0 * d.nbox * d.q + (down ? (double)c->lev[l - 1].nbox * qp : 0.0)));

@@ -25,6 +25,9 @@ CONFIGS = {
             "3:1 prolate spheroid (3,1,1), geodesic frequency 45 (40,500 triangles, 60,750 RWG)"),
     "C3c": (lambda: meshes.plate(120, 120, 4.0, 4.0, (-2.0, -2.0, 0.0)), 0.25, 5, 64,
             "4x4 plate, 120x120 squares split on a diagonal (28,800 triangles, 42,960 RWG)"),
+    "C4": (lambda: meshes.aircraft(edge=0.1, length=10.0, seed=4), 0.25, 7, 8,
+           "aircraft-like PEC body: 10 wavelength prolate fuselage, two wing plates and a tail plate, "
+           "edges about 0.1 wavelength (12,560 triangles, 18,727 RWG)"),
     "C5": (lambda: meshes.icosphere(8, 16.0), 0.25, 9, 16,
            "PEC sphere r=16, icosphere subdiv 8 (1,310,720 triangles, 1,966,080 RWG), 9 levels"),
 }

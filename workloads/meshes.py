@@ -130,6 +130,39 @@ def _merge(parts):
     return np.concatenate(vs), np.concatenate(fs).astype(np.int32)
 
 
+def ring_ellipsoid(a, b, edge):
+    """Prolate ellipsoid x^2/a^2 + (y^2 + z^2)/b^2 = 1 meshed by rings: meridian nodes at
+    equal arc length (about ``edge`` apart), the same number of points on every ring
+    (about ``edge`` apart on the widest one), poles closed by fans."""
+    phi = np.linspace(0.0, np.pi, 4001)
+    ds = np.sqrt((a * np.sin(phi)) ** 2 + (b * np.cos(phi)) ** 2)
+    arc = np.concatenate([[0.0], np.cumsum(0.5 * (ds[1:] + ds[:-1]) * np.diff(phi))])
+    nring = max(2, int(round(arc[-1] / edge))) - 1
+    phis = np.interp(np.linspace(0.0, arc[-1], nring + 2)[1:-1], arc, phi)
+    nth = max(3, int(round(2.0 * np.pi * b / edge)))
+    th = 2.0 * np.pi * np.arange(nth) / nth
+    verts = [[a, 0.0, 0.0]]
+    for p in phis:
+        r = b * np.sin(p)
+        for t in th:
+            verts.append([a * np.cos(p), r * np.cos(t), r * np.sin(t)])
+    verts.append([-a, 0.0, 0.0])
+    v = np.array(verts)
+    f = []
+    ring = lambda j, i: 1 + j * nth + (i % nth)
+    for i in range(nth):
+        f.append([0, ring(0, i), ring(0, i + 1)])
+    for j in range(nring - 1):
+        for i in range(nth):
+            f.append([ring(j, i), ring(j + 1, i), ring(j + 1, i + 1)])
+            f.append([ring(j, i), ring(j + 1, i + 1), ring(j, i + 1)])
+    last = len(v) - 1
+    for i in range(nth):
+        f.append([last, ring(nring - 1, i + 1), ring(nring - 1, i)])
+    f = np.array(f, dtype=np.int64)
+    return v, _orient_outward(v, f).astype(np.int32)
+
+
 def aircraft(edge=0.1, length=10.0, seed=0):
     """Aircraft-like PEC body: a prolate fuselage ``length`` long, two thin wing plates
     and a tail plate, all separate closed/open surfaces (no junctions), mesh edge about
@@ -137,11 +170,7 @@ def aircraft(edge=0.1, length=10.0, seed=0):
     rng = np.random.default_rng(seed)
     a = length / 2.0
     b = length / 12.0
-    freq = max(2, int(round(np.pi * b / edge / 1.2)))
-    fv, ff = geodesic_ellipsoid(freq, (1.0, 1.0, 1.0))
-    # stretch the sphere into the fuselage, refining along x by a second pass is not
-    # needed for the benchmark workload: edges along x are ``a/b`` longer
-    fv = fv * np.array([a, b, b])
+    fv, ff = ring_ellipsoid(a, b, edge)
     span = 0.45 * length
     chord = 0.12 * length
     sweep = 0.05 * length * (1.0 + 0.1 * rng.standard_normal())
