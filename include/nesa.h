@@ -257,20 +257,32 @@ int nesa_solve(nesa_ctx *ctx, const nesa_c128 *b_dev, nesa_c128 *x_dev, int nrhs
  * backward, Adam) minimises L = sum_s |M(u_s) - v_s|^2 / sum_s |v_s|^2 over pairs
  * u_s = Z~ v_s, v_s the Arnoldi vectors of S-preconditioned GMRES for the training
  * right-hand sides.  Inference uses an FP16 copy of the weights with FP32 arithmetic.
+ * Training always starts from the initial weights.  A lower L does not always mean
+ * faster GMRES (on the aircraft body the trained map lowered L on held-out Krylov
+ * vectors 8x and still stalled GMRES), so training ends with a validation: val_iters
+ * steps of right-preconditioned GMRES on the last training right-hand side with the
+ * trained weights and with the initial ones (M = S); the trained weights are kept only
+ * if their true relative residual is lower, otherwise the initial weights are restored
+ * (fallback = 1).
  */
 #define NESA_LEARN_PARAMS 1542
 typedef struct {
-  int32_t samples; /* Arnoldi vectors per training right-hand side (default 48) */
-  int32_t steps;   /* Adam steps (default 300) */
-  float lr;        /* Adam learning rate (default 3e-3) */
-  int32_t reserved[5];
+  int32_t samples;   /* Arnoldi vectors per training right-hand side (default 48) */
+  int32_t steps;     /* Adam steps (default 300) */
+  float lr;          /* Adam learning rate (default 3e-3) */
+  int32_t val_iters; /* GMRES steps of the validation (default 100; 0: keep the trained weights) */
+  int32_t reserved[4];
 } nesa_learn_opts;
 typedef struct {
-  double loss_initial; /* L with the initial (block-Jacobi) weights */
+  double loss_initial; /* L with the initial (overlapping block-Jacobi) weights */
   double loss_final;   /* L after training */
   int32_t samples;     /* training pairs */
   int32_t steps;
-  double seconds;
+  double seconds;      /* training and validation */
+  double val_res_learned; /* validation: true relative residual with the trained weights */
+  double val_res_base;    /* validation: the same with the initial weights (M = S) */
+  int32_t fallback;       /* 1: the initial weights were restored */
+  int32_t val_iters;
 } nesa_learn_info;
 /* Build the block-Jacobi blocks and the features (idempotent; also done on demand). */
 int nesa_precond_setup(nesa_ctx *ctx);

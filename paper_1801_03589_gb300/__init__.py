@@ -75,12 +75,13 @@ class SolveOpts(ctypes.Structure):
 
 class LearnOpts(ctypes.Structure):
     _fields_ = [("samples", ctypes.c_int32), ("steps", ctypes.c_int32), ("lr", ctypes.c_float),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("val_iters", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class LearnInfo(ctypes.Structure):
     _fields_ = [("loss_initial", ctypes.c_double), ("loss_final", ctypes.c_double), ("samples", ctypes.c_int32),
-                ("steps", ctypes.c_int32), ("seconds", ctypes.c_double)]
+                ("steps", ctypes.c_int32), ("seconds", ctypes.c_double), ("val_res_learned", ctypes.c_double),
+                ("val_res_base", ctypes.c_double), ("fallback", ctypes.c_int32), ("val_iters", ctypes.c_int32)]
 
 
 PRECOND_NONE, PRECOND_BLOCK_JACOBI, PRECOND_LEARNED, PRECOND_OVERLAP = 0, 1, 2, 3
@@ -297,15 +298,16 @@ class Nesa:
         _check(lib().nesa_precond_apply(self._h, kind, pr, z.data_ptr(), nrhs))
         return z
 
-    def precond_train(self, b, samples=48, steps=300, lr=3e-3):
+    def precond_train(self, b, samples=48, steps=300, lr=3e-3, val_iters=100):
         b, pb, nrhs = _dev_ptr(b, self.n, "b")
         o = LearnOpts()
         lib().nesa_default_learn_opts(ctypes.byref(o))
-        o.samples, o.steps, o.lr = int(samples), int(steps), float(lr)
+        o.samples, o.steps, o.lr, o.val_iters = int(samples), int(steps), float(lr), int(val_iters)
         i = LearnInfo()
         _check(lib().nesa_precond_train(self._h, pb, nrhs, ctypes.byref(o), ctypes.byref(i)))
         return dict(loss_initial=i.loss_initial, loss_final=i.loss_final, samples=i.samples, steps=i.steps,
-                    seconds=i.seconds)
+                    seconds=i.seconds, val_res_learned=i.val_res_learned, val_res_base=i.val_res_base,
+                    fallback=i.fallback, val_iters=i.val_iters)
 
     def precond_params(self, values=None):
         """Get the learned weights (values None) or set them (marks the network trained)."""

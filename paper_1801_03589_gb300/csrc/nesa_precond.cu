@@ -809,6 +809,7 @@ using namespace nesa;
 // Arnoldi vectors of block-Jacobi GMRES for the training right-hand sides (declared
 // in nesa_solve.cu): ns vectors per right-hand side into V (ns * nrhs columns)
 int nesa_collect_krylov(nesa_ctx *c, const cplx *b, int nrhs, int ns, cplx *V);
+double nesa_precond_validate(nesa_ctx *c, const cplx *b, int iters);
 
 extern "C" {
 
@@ -889,6 +890,7 @@ void nesa_default_learn_opts(nesa_learn_opts *o) {
   o->samples = 48;
   o->steps = 300;
   o->lr = 3e-3f;
+  o->val_iters = 100;
 }
 
 int nesa_precond_train(nesa_ctx *c, const nesa_c128 *b, int nrhs, const nesa_learn_opts *opts, nesa_learn_info *info) {
@@ -896,7 +898,8 @@ int nesa_precond_train(nesa_ctx *c, const nesa_c128 *b, int nrhs, const nesa_lea
   nesa_learn_opts o;
   nesa_default_learn_opts(&o);
   if (opts) o = *opts;
-  if (o.samples < 2 || o.samples > 512 || o.steps < 0 || !(o.lr > 0.0f)) return NESA_ERR_INVALID_ARG;
+  if (o.samples < 2 || o.samples > 512 || o.steps < 0 || !(o.lr > 0.0f) || o.val_iters < 0 || o.val_iters > 1000)
+    return NESA_ERR_INVALID_ARG;
   auto t0 = std::chrono::steady_clock::now();
   nesa_learn_info I;
   std::memset(&I, 0, sizeof(I));
@@ -916,6 +919,10 @@ int nesa_precond_train(nesa_ctx *c, const nesa_c128 *b, int nrhs, const nesa_lea
       launch_matvec(c, V + (size_t)c0 * n, U + (size_t)c0 * n, nc, NESA_PART_ALL);
     }
     I.samples = ns;
+    // training starts from the initial weights (M = S)
+    std::vector<float> th0;
+    init_theta(th0, 1801);
+    check_cuda(cudaMemcpy(P->theta, th0.data(), sizeof(float) * NPARAM, cudaMemcpyHostToDevice), "theta");
     check_cuda(cudaMemset(P->adam_m, 0, sizeof(float) * NPARAM), "adam");
     check_cuda(cudaMemset(P->adam_v, 0, sizeof(float) * NPARAM), "adam");
     // the features of the samples do not depend on the weights: computed once inside
@@ -934,11 +941,30 @@ int nesa_precond_train(nesa_ctx *c, const nesa_c128 *b, int nrhs, const nesa_lea
     // final loss with the trained weights
     I.loss_final = loss_grad(c, U, V, ns, false);
     I.steps = o.steps;
-    refresh_coef(c);
-    check_cuda(cudaStreamSynchronize(c->stream), "train");
-    P->trained = true;
     dfree(c, V);
     dfree(c, U);
+    refresh_coef(c);
+    P->trained = true;
+    if (o.val_iters > 0) {
+      // validation on the last training right-hand side: trained weights against the
+      // initial ones; the lower true residual after val_iters GMRES steps wins
+      const cplx *bv = (const cplx *)b + (size_t)(nrhs - 1) * n;
+      std::vector<float> th_trained(NPARAM);
+      check_cuda(cudaMemcpy(th_trained.data(), P->theta, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost), "theta");
+      I.val_iters = o.val_iters;
+      I.val_res_learned = nesa_precond_validate(c, bv, o.val_iters);
+      check_cuda(cudaMemcpy(P->theta, th0.data(), sizeof(float) * NPARAM, cudaMemcpyHostToDevice), "theta");
+      refresh_coef(c);
+      I.val_res_base = nesa_precond_validate(c, bv, o.val_iters);
+      if (I.val_res_learned < I.val_res_base) {
+        check_cuda(cudaMemcpy(P->theta, th_trained.data(), sizeof(float) * NPARAM, cudaMemcpyHostToDevice),
+                   "theta");
+        refresh_coef(c);
+      } else {
+        I.fallback = 1;
+      }
+    }
+    check_cuda(cudaStreamSynchronize(c->stream), "train");
   } catch (const Error &e) {
     set_last_error(e.what);
     return e.status;

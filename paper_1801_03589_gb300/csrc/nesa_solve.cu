@@ -527,6 +527,20 @@ static int refine_run(nesa_ctx *c, const cplx *b, cplx *x, int nrhs, double tol,
 // Arnoldi vectors v_0..v_{ns-1} of block-Jacobi-preconditioned GMRES (one cycle of ns
 // steps from x0 = 0) for each of the nrhs right-hand sides, into V [nrhs * ns][n]
 // (right-hand side major).  Columns past a breakdown are zero.
+// True relative residual after `iters` steps of GMRES(iters) with the learned
+// preconditioner on one right-hand side (the mixed product when it was built);
+// used to validate trained weights.  Throws Error on CUDA failures.
+double nesa_precond_validate(nesa_ctx *c, const cplx *b, int iters) {
+  SolveWork *W = get_work(c, iters, 1);
+  nesa_solve_info I;
+  std::memset(&I, 0, sizeof(I));
+  const int parts = NESA_PART_ALL | (c->mixed ? NESA_PART_MIXED : 0);
+  int st = gmres_run(c, b, W->dx, 1, 0.0, iters, iters, parts, NESA_PRECOND_LEARNED, I);
+  if (st == NESA_ERR_NUMERIC) return INFINITY;
+  const double r = I.rel_residual[0];
+  return std::isfinite(r) ? r : INFINITY;
+}
+
 int nesa_collect_krylov(nesa_ctx *c, const cplx *b, int nrhs, int ns, cplx *V) {
   SolveWork *W = get_work(c, ns, nrhs);
   nesa_solve_info I;

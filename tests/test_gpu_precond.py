@@ -107,9 +107,13 @@ def test_trained_network_gain_on_held_out_rhs():
     _, inone = g.solve(held, tol=1e-5, restart=60, max_iters=3000)
     _, iov = g.solve(held, tol=1e-5, restart=60, max_iters=3000, precond=nesa.PRECOND_OVERLAP)
     info = g.precond_train(B[:2].contiguous(), samples=48, steps=300)
-    print("training: loss %.4f -> %.4f (%d pairs, %.2f s)" % (info["loss_initial"], info["loss_final"],
-                                                              info["samples"], info["seconds"]))
+    print("training: loss %.4f -> %.4f (%d pairs, %.2f s); validation after %d steps: trained %.2e, "
+          "initial %.2e, fallback %d" % (info["loss_initial"], info["loss_final"], info["samples"], info["seconds"],
+                                         info["val_iters"], info["val_res_learned"], info["val_res_base"],
+                                         info["fallback"]))
     assert info["loss_final"] < info["loss_initial"]
+    # on this sphere the trained weights win the validation (no fallback to S)
+    assert info["fallback"] == 0 and info["val_res_learned"] < info["val_res_base"]
     x, ilr = g.solve(held, tol=1e-5, restart=60, max_iters=3000, precond=nesa.PRECOND_LEARNED)
     print("C1b held-out RHS iterations to 1e-5: none %d, overlapping block-Jacobi %d, learned %d "
           "(true residual %.2e)" % (inone["iterations"], iov["iterations"], ilr["iterations"],
