@@ -37,7 +37,7 @@ import numpy as np  # noqa: E402
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from workloads import get_config, random_coefficients  # noqa: E402
+from workloads import get_config, plane_wave_directions, random_coefficients  # noqa: E402
 
 CONFIG = "C2"
 METRIC = "nesa_matvec_per_s"
@@ -45,6 +45,9 @@ UNIT = "matvec/s"
 # GB300: 152 SMs at 2070 MHz; per SM and clock 2 FP64 FMA and 128 FP32 FMA
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# DRAM traffic of the translation / potential-transfer GEMM launches of one product of
+# the r = 3 sphere (ncu, dram__bytes_read.sum + dram__bytes_write.sum); null elsewhere
+GEMM_DRAM_BYTES_C2 = 1.5071e9
 SPEC = ("PEC sphere r=3 wavelengths, icosphere subdiv 6 (81,920 triangles, 122,880 RWG), "
         "6-level octree, leaf 0.25 wavelength, 1 RHS")
 
@@ -342,6 +345,41 @@ def run_ours(args, world, rank, local):
         if args.fp64_solve:
             solve["fp64_none"] = one()
 
+    # learned preconditioner on the aircraft-like body: trained on the GMRES vectors of
+    # two plane waves, judged by iterations and true residual on six held-out ones
+    learned = None
+    if not args.no_learned:
+        cf = get_config("C4")
+        ga = nesa.Nesa(cf["vertices"], cf["triangles"], cf["k"], leaf_size=cf["leaf_size"],
+                       n_levels=cf["n_levels"], precision=nesa.MIXED, translate=nesa.TRANSLATE_TENSOR)
+        ga.set_stream(stream)
+        kh, pol = plane_wave_directions(8, seed=180103589)
+        B8 = ga.rhs_planewave(kh, pol)
+        held = B8[2:].contiguous()
+        torch.cuda.synchronize()
+
+        def lsolve(bb, **kw):
+            _, si = ga.solve(bb, tol=1e-5, restart=100, max_iters=3000, check=False, **kw)
+            return {"seconds": si["seconds"], "status": si["status"], "iterations": si["iterations"],
+                    "converged": si["converged"], "true_rel_residual_max": max(si["rel_residual"][:bb.shape[0]])}
+
+        ga.precond_apply(held[:1], nesa.PRECOND_OVERLAP)  # setup outside the timed solves
+        learned = {"workload": "C4: %s; 8 plane waves (seed 180103589), trained on 2, solved together on the "
+                               "other 6 to 1e-5" % cf["description"],
+                   "n_unknowns": ga.n,
+                   "mixed_none": lsolve(held, mixed=True, inner_tol=1e-2),
+                   "mixed_block_jacobi": lsolve(held, mixed=True, inner_tol=1e-2,
+                                                precond=nesa.PRECOND_BLOCK_JACOBI),
+                   "mixed_overlap": lsolve(held, mixed=True, inner_tol=1e-2, precond=nesa.PRECOND_OVERLAP)}
+        learned["training"] = ga.precond_train(B8[:2].contiguous(), samples=48, steps=300)
+        learned["mixed_learned"] = lsolve(held, mixed=True, inner_tol=1e-2, precond=nesa.PRECOND_LEARNED)
+        # the plain FP64 form with block-Jacobi on one of them, capped at 300 steps
+        _, si = ga.solve(held[:1].contiguous(), tol=1e-5, restart=100, max_iters=300, check=False,
+                         precond=nesa.PRECOND_BLOCK_JACOBI)
+        learned["fp64_block_jacobi_1rhs_300_steps"] = {"seconds": si["seconds"], "iterations": si["iterations"],
+                                                        "true_rel_residual": si["rel_residual"][0]}
+        del ga
+
     # batched sweep: three meshes of uneven size with 64 right-hand sides each, one CUDA
     # graph launch per pass over all of them (mixed product, autotuned tile widths)
     batch = None
@@ -407,12 +445,18 @@ def run_ours(args, world, rank, local):
     else:
         roof = {"bound": "alu", "achieved": d["flops"] / sec / 1e12, "unit": "TFLOP/s", "peak": FP32_PEAK_TFLOPS,
                 "peak_note": "FP32: 152 SMs x 256 flop/clk x 2070 MHz (derived)"}
-    roof.update({"kernel": kernel, "frac": roof["achieved"] / roof["peak"], "traffic": None,
+    # DRAM bytes (read + written) per product of the stage-4 launches, from the ncu capture
+    # in profiles/k_tc_gemm_C2_dram.md (r = 3 sphere, 1 RHS, this kernel version)
+    traffic = GEMM_DRAM_BYTES_C2 if (kernel == "k_tc_gemm" and args.workload == CONFIG and nrhs == 1) else None
+    roof.update({"kernel": kernel, "frac": roof["achieved"] / roof["peak"], "traffic": traffic,
+                 "traffic_unit": "bytes per product (all launches of the kernel in one product)",
                  "ms_per_step": d["ms"] / args.steps})
-    # kernels launched: the tensor translation is split + GEMM + reduce at the coarsest
-    # far level and two splits + two GEMMs + reduce below it
-    launches = (prof_mx["radiation"]["launches"] + prof_mx["source_transfer"]["launches"] +
-                prof_mx["near_reception"]["launches"] + 5 * prof_mx["translation"]["launches"] - 2 * args.steps)
+    # kernels launched in the timed region: one product captured into a CUDA graph by the
+    # library's batch API, its kernel nodes counted, times the timed products
+    b1 = nesa.Batch([g], [x], [y], parts=mixed)
+    per_product = b1.kernel_nodes
+    b1.close()
+    launches = per_product * args.steps
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -453,6 +497,7 @@ def run_ours(args, world, rank, local):
                               / FP64_PEAK_TFLOPS}},
         "mixed_vs_fp64": ms64 / ms_mx,
         "solve": solve,
+        "learned": learned,
         "batch": batch,
         "cpu_baseline": cpu,
     }
@@ -471,6 +516,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner block (aircraft body)")
     ap.add_argument("--fp64-solve", action="store_true", help="also time the plain FP64 solve (about 2 minutes)")
     ap.add_argument("--workload", default=CONFIG, help="workload name (smaller ones are for profiling runs)")
     ap.add_argument("--tile-n", type=int, default=0, choices=[0, 64, 128, 256],
