@@ -125,6 +125,45 @@ def dist_setup():
     return world, rank, local
 
 
+class Ranks:
+    """Barrier and max-over-ranks for the timing (no process group with one rank).
+    backend "nccl" on the GPUs for the benchmark; "gloo" on the host for tests."""
+
+    def __init__(self, world, backend="nccl", device="cuda"):
+        import torch
+        self.device = torch.device(device)
+        self.pg = None
+        if world > 1:
+            import torch.distributed as dist
+            if backend == "nccl":
+                dist.init_process_group(backend, device_id=self.device)
+            else:
+                dist.init_process_group(backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg is not None:
+            self.pg.barrier()
+
+    def max(self, v):
+        import torch
+        t = torch.tensor([float(v)], dtype=torch.float64, device=self.device)
+        if self.pg is not None:
+            self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg is not None:
+            self.pg.destroy_process_group()
+            self.pg = None
+
+
+def job_throughput(world, units_per_rank_step, ms_per_step_max):
+    """Whole-job units per second: every rank processes units_per_rank_step per step,
+    the step time is the slowest rank's."""
+    return world * units_per_rank_step * 1e3 / ms_per_step_max
+
+
 def oracle_sampled_product(o, x, n_leaves=12, n_boxes=12, n_rows=48, seed=0):
     """Seconds the oracle needs for one full product, estimated stage by stage on a
     bounded sample: every stage (channel sources, near rows, radiation, source
@@ -268,11 +307,7 @@ def run_ours(args, world, rank, local):
     import paper_1801_03589_gb300 as nesa
 
     torch.cuda.set_device(local)
-    pg = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-        pg = dist
+    ranks = Ranks(world, "nccl", torch.device("cuda", local))
     cfg = get_config(args.workload)
     g = nesa.Nesa(cfg["vertices"], cfg["triangles"], cfg["k"], leaf_size=cfg["leaf_size"], n_levels=cfg["n_levels"],
                   precision=nesa.MIXED, translate=nesa.TRANSLATE_TENSOR, tile_n=args.tile_n)
@@ -285,22 +320,14 @@ def run_ours(args, world, rank, local):
     y = torch.empty_like(x)
     torch.cuda.synchronize()
 
-    def barrier():
-        if pg is not None:
-            pg.barrier()
-
-    def max_over_ranks(v):
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        if pg is not None:
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        return float(t.item())
+    barrier, max_over_ranks = ranks.barrier, ranks.max
 
     mixed = nesa.PART_ALL | nesa.PART_MIXED
     with ClockSampler(local) as clk:
         ms64, prof64 = _time_products(g, x, y, nesa.PART_ALL, args.steps, args.warmup, stream, barrier)
         ms_mx, prof_mx = _time_products(g, x, y, mixed, args.steps, args.warmup, stream, barrier)
     ms64, ms_mx = max_over_ranks(ms64), max_over_ranks(ms_mx)
-    value = world * nrhs * 1e3 / ms_mx
+    value = job_throughput(world, nrhs, ms_mx)
     # accuracy of the mixed product against the FP64 product on this input
     y64 = g.matvec(x)
     ymx = g.matvec(x, parts=mixed)
@@ -409,14 +436,13 @@ def run_ours(args, world, rank, local):
         pass_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
         batch = {"workload": "sphere r=2 (30,720 RWG), 3:1 spheroid (60,750 RWG), 4x4 plate (42,960 RWG); "
                              "64 right-hand sides each; mixed product",
-                 "pass_ms": pass_ms, "matvec_per_s": world * 3 * 64 * 1e3 / pass_ms,
+                 "pass_ms": pass_ms, "matvec_per_s": job_throughput(world, 3 * 64, pass_ms),
                  "graph_kernel_nodes": bt.kernel_nodes, "launches_per_pass": 1, "build_and_capture_s": build_s,
                  "tile_n": [{l: t["tile_n"] for l, t in m.tuning().items()} for m in members]}
         bt.close()
 
     if rank != 0:
-        if pg is not None:
-            pg.destroy_process_group()
+        ranks.close()
         return 0
 
     # roofline of the dominant kernel of the mixed product (largest device time); the
@@ -482,13 +508,13 @@ def run_ours(args, world, rank, local):
                        sum(v["bytes"] for v in prof_mx.values()) / args.steps / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "clocks": clk.summary(),
-        "e2e": {"value": world * nrhs * 1e3 / e2e_ms, "unit": UNIT, "h2d_bytes_per_step": 16 * n * nrhs,
+        "e2e": {"value": job_throughput(world, nrhs, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": 16 * n * nrhs,
                 "d2h_bytes_per_step": 16 * n * nrhs, "ms_per_step": e2e_ms},
         "gpu_launches": launches,
         "roofline": roof,
         "stages": _stages(prof_mx, args.steps),
         "tensor_tiles": {str(l): t for l, t in g.tuning().items()},
-        "fp64": {"value": world * nrhs * 1e3 / ms64, "unit": UNIT, "ms_per_step": ms64, "dtype": "f64",
+        "fp64": {"value": job_throughput(world, nrhs, ms64), "unit": UNIT, "ms_per_step": ms64, "dtype": "f64",
                  "stages": _stages(prof64, args.steps),
                  "roofline": {"kernel": "k_translate<double2>", "bound": "alu",
                               "achieved": prof64["translation"]["flops"] / (prof64["translation"]["ms"] * 1e-3) / 1e12,
@@ -502,8 +528,7 @@ def run_ours(args, world, rank, local):
         "cpu_baseline": cpu,
     }
     print(json.dumps(line))
-    if pg is not None:
-        pg.destroy_process_group()
+    ranks.close()
     return 0
 
 
