@@ -33,6 +33,8 @@ struct SolveWork {
   cplx *y = nullptr;     // [nrhs][m]
   double *part = nullptr;  // partial sums [nrhs][m+1][nchunk] (complex as 2 doubles)
   double *nrm = nullptr;   // [nrhs] norms
+  double *nrm0 = nullptr;  // [nrhs] norm of Z v_j before the projections
+  int *flag = nullptr;     // [nrhs] 1: second projection pass needed
   double *bnorm = nullptr; // [nrhs]
   int *steps = nullptr;    // [nrhs] Arnoldi steps in this cycle
   int *state = nullptr;    // [nrhs] 0 running, 1 converged, 2 breakdown (lucky), 3 numeric
@@ -54,8 +56,9 @@ static const int kChunk = 2048;  // vector elements per partial-sum block
 // additions is the same as one dot at a time (thread strides, warp tree, warps in order).
 static const int kDotTile = 8;
 __global__ void __launch_bounds__(256) k_dots(double2 *part, const cplx *V, const cplx *w, int ni, int64_t n,
-                                              int nrhs, int nchunk) {
+                                              int nrhs, int nchunk, const int *flag) {
   const int c = blockIdx.x, i0 = blockIdx.y * kDotTile, r = blockIdx.z;
+  if (flag && !flag[r]) return;  // second pass not needed for this column
   const int nt = min(kDotTile, ni - i0);
   const int64_t lo = (int64_t)c * kChunk, hi = min(n, lo + kChunk);
   __shared__ double sre[8][kDotTile], sim[8][kDotTile];
@@ -100,8 +103,10 @@ __global__ void __launch_bounds__(256) k_dots(double2 *part, const cplx *V, cons
 }
 
 // h[r][i] (+)= sum_c part (accumulate when add != 0); y[r][i] = the same sum
-__global__ void k_dots_reduce(cplx *h, int ldh, cplx *y, int ldy, const double2 *part, int ni, int nchunk, int add) {
+__global__ void k_dots_reduce(cplx *h, int ldh, cplx *y, int ldy, const double2 *part, int ni, int nchunk, int add,
+                              const int *flag) {
   const int i = blockIdx.x, r = blockIdx.y;
+  if (flag && !flag[r]) return;
   double re = 0.0, im = 0.0;
   for (int c = threadIdx.x; c < nchunk; c += blockDim.x) {
     double2 v = part[((int64_t)r * ni + i) * nchunk + c];
@@ -124,21 +129,33 @@ __global__ void k_dots_reduce(cplx *h, int ldh, cplx *y, int ldy, const double2 
   }
 }
 
-// w[r] -= sum_{i<ni} V_i[r] * coef[r][i]
-__global__ void k_subtract(cplx *w, const cplx *V, const cplx *coef, int ldc, int ni, int64_t n, int nrhs) {
+// w[r] -= sum_{i<ni} V_i[r] * coef[r][i]   (four FP64 FMAs per term: the pass is bound
+// by the FP64 pipe)
+__global__ void k_subtract(cplx *w, const cplx *V, const cplx *coef, int ldc, int ni, int64_t n, int nrhs,
+                           const int *flag) {
   const int r = blockIdx.y;
+  if (flag && !flag[r]) return;
   const cplx *cr = coef + (int64_t)r * ldc;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     cplx acc = w[(int64_t)r * n + e];
 #pragma unroll 4
     for (int i = 0; i < ni; ++i) {
-      cplx v = V[((int64_t)i * nrhs + r) * n + e];
-      cplx c = cr[i];
-      acc.x -= v.x * c.x - v.y * c.y;
-      acc.y -= v.x * c.y + v.y * c.x;
+      const cplx v = V[((int64_t)i * nrhs + r) * n + e];
+      const cplx c = cr[i];
+      acc.x = fma(-v.x, c.x, acc.x);
+      acc.x = fma(v.y, c.y, acc.x);
+      acc.y = fma(-v.x, c.y, acc.y);
+      acc.y = fma(-v.y, c.x, acc.y);
     }
     w[(int64_t)r * n + e] = acc;
   }
+}
+
+// second CGS pass only where the first one removed most of w: |w| after < eta |w| before
+// ("twice is enough": one more pass restores orthogonality to working precision)
+__global__ void k_reorth_flag(int *flag, const double *after, const double *before, double eta, int nrhs) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < nrhs) flag[r] = after[r] < eta * before[r] ? 1 : 0;
 }
 
 // x[r] += sum_{i<k_r} V_i[r] y[r][i]
@@ -153,9 +170,10 @@ __global__ void k_update_x(cplx *x, const cplx *V, const cplx *y, int ldy, const
   }
 }
 
-// partial sums of |v|^2 per column
-__global__ void k_norm2(double2 *part, const cplx *v, int64_t n, int nchunk) {
+// partial sums of |v|^2 per column (columns with flag 0 skipped when flag is given)
+__global__ void k_norm2(double2 *part, const cplx *v, int64_t n, int nchunk, const int *flag) {
   const int c = blockIdx.x, r = blockIdx.y;
+  if (flag && !flag[r]) return;
   const int64_t lo = (int64_t)c * kChunk, hi = min(n, lo + kChunk);
   double s = 0.0;
   for (int64_t e = lo + threadIdx.x; e < hi; e += blockDim.x) {
@@ -174,8 +192,9 @@ __global__ void k_norm2(double2 *part, const cplx *v, int64_t n, int nchunk) {
   }
 }
 
-__global__ void k_norm_reduce(double *out, const double2 *part, int nchunk) {
+__global__ void k_norm_reduce(double *out, const double2 *part, int nchunk, const int *flag) {
   const int r = blockIdx.x;
+  if (flag && !flag[r]) return;
   double s = 0.0;
   for (int c = threadIdx.x; c < nchunk; c += blockDim.x) s += part[(int64_t)r * nchunk + c].x;
   for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
@@ -310,8 +329,8 @@ static SolveWork *get_work(nesa_ctx *c, int m, int nrhs) {
   if (!c->solve_work) c->solve_work = new SolveWork();
   SolveWork *W = (SolveWork *)c->solve_work;
   if (W->m >= m && W->nrhs >= nrhs) return W;
-  void *old[] = {W->V, W->w, W->r, W->H, W->h, W->cs, W->sn, W->g, W->y, W->part, W->nrm, W->bnorm, W->steps,
-                 W->state, W->est, W->ro, W->dx, W->onrm, W->zt, W->zt2};
+  void *old[] = {W->V, W->w, W->r, W->H, W->h, W->cs, W->sn, W->g, W->y, W->part, W->nrm, W->nrm0, W->flag,
+                 W->bnorm, W->steps, W->state, W->est, W->ro, W->dx, W->onrm, W->zt, W->zt2};
   for (void *p : old) dfree(c, p);
   if (W->h_state) cudaFreeHost(W->h_state);
   if (W->h_est) cudaFreeHost(W->h_est);
@@ -331,6 +350,8 @@ static SolveWork *get_work(nesa_ctx *c, int m, int nrhs) {
   W->y = (cplx *)dalloc(c, sizeof(cplx) * (size_t)nrhs * m);
   W->part = (double *)dalloc(c, sizeof(double2) * (size_t)nrhs * (m + 1) * nchunk);
   W->nrm = (double *)dalloc(c, sizeof(double) * nrhs);
+  W->nrm0 = (double *)dalloc(c, sizeof(double) * nrhs);
+  W->flag = (int *)dalloc(c, sizeof(int) * nrhs);
   W->bnorm = (double *)dalloc(c, sizeof(double) * nrhs);
   W->steps = (int *)dalloc(c, sizeof(int) * nrhs);
   W->state = (int *)dalloc(c, sizeof(int) * nrhs);
@@ -368,9 +389,9 @@ static int gmres_run(nesa_ctx *c, const cplx *b, cplx *x, int nrhs, double tol, 
     const int64_t n = c->n;
     const int nchunk = (int)((n + kChunk - 1) / kChunk);
     const dim3 vgrid(blocks_for(n, 256, 4096), nrhs);
-    auto norms = [&](const cplx *v, double *out) {
-      k_norm2<<<dim3(nchunk, nrhs), 256, 0, st>>>((double2 *)W->part, v, n, nchunk);
-      k_norm_reduce<<<nrhs, 32, 0, st>>>(out, (const double2 *)W->part, nchunk);
+    auto norms = [&](const cplx *v, double *out, const int *flag = nullptr) {
+      k_norm2<<<dim3(nchunk, nrhs), 256, 0, st>>>((double2 *)W->part, v, n, nchunk, flag);
+      k_norm_reduce<<<nrhs, 32, 0, st>>>(out, (const double2 *)W->part, nchunk, flag);
     };
     norms(b, W->bnorm);
     check_cuda(cudaMemsetAsync(x, 0, sizeof(cplx) * (size_t)nrhs * n, st), "x0");
@@ -402,16 +423,21 @@ static int gmres_run(nesa_ctx *c, const cplx *b, cplx *x, int nrhs, double tol, 
           launch_matvec(c, Vj, W->w, nrhs, parts);
         }
         I.matvecs += 1;
-        // CGS2: two rounds of projection onto V_0..V_j
+        // classical Gram-Schmidt onto V_0..V_j; a second pass for the columns whose
+        // norm fell below 0.7 of its value before (CGS2 where needed; the projections
+        // are bound by the FP64 pipe, so the pass is skipped on the device elsewhere)
+        norms(W->w, W->nrm0);
         for (int pass = 0; pass < 2; ++pass) {
+          const int *fl = pass ? W->flag : nullptr;
           k_dots<<<dim3(nchunk, (j + kDotTile) / kDotTile, nrhs), 256, 0, st>>>((double2 *)W->part, W->V, W->w,
-                                                                               j + 1, n, nrhs, nchunk);
+                                                                               j + 1, n, nrhs, nchunk, fl);
           // h accumulates both passes; y holds this pass's coefficients for the subtraction
           k_dots_reduce<<<dim3(j + 1, nrhs), 32, 0, st>>>(W->h, m + 1, W->y, m, (const double2 *)W->part, j + 1,
-                                                           nchunk, pass);
-          k_subtract<<<vgrid, 256, 0, st>>>(W->w, W->V, W->y, m, j + 1, n, nrhs);
+                                                           nchunk, pass, fl);
+          k_subtract<<<vgrid, 256, 0, st>>>(W->w, W->V, W->y, m, j + 1, n, nrhs, fl);
+          norms(W->w, W->nrm, fl);
+          if (pass == 0) k_reorth_flag<<<(nrhs + 63) / 64, 64, 0, st>>>(W->flag, W->nrm, W->nrm0, 0.7, nrhs);
         }
-        norms(W->w, W->nrm);
         k_givens<<<(nrhs + 63) / 64, 64, 0, st>>>(W->H, W->h, W->nrm, W->cs, W->sn, W->g, W->steps, W->state, W->est,
                                                   W->bnorm, j, m, tol, nrhs);
         k_scale<<<vgrid, 256, 0, st>>>(Vn, W->w, W->nrm, n, nrhs);
@@ -479,8 +505,8 @@ static int refine_run(nesa_ctx *c, const cplx *b, cplx *x, int nrhs, double tol,
   const int64_t n = c->n, total = n * nrhs;
   const int nchunk = (int)((n + kChunk - 1) / kChunk);
   auto norms = [&](const cplx *v, double *out_dev, std::vector<double> &host) {
-    k_norm2<<<dim3(nchunk, nrhs), 256, 0, st>>>((double2 *)W->part, v, n, nchunk);
-    k_norm_reduce<<<nrhs, 32, 0, st>>>(out_dev, (const double2 *)W->part, nchunk);
+    k_norm2<<<dim3(nchunk, nrhs), 256, 0, st>>>((double2 *)W->part, v, n, nchunk, nullptr);
+    k_norm_reduce<<<nrhs, 32, 0, st>>>(out_dev, (const double2 *)W->part, nchunk, nullptr);
     host.resize(nrhs);
     check_cuda(cudaMemcpyAsync(host.data(), out_dev, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st), "norm");
     check_cuda(cudaStreamSynchronize(st), "norm");
