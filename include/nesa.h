@@ -217,7 +217,8 @@ typedef struct {
                          correction to inner_tol, x += d - until ||r||/||b|| <= tol
                          (context built with NESA_MIXED); Arnoldi and Givens stay FP64 */
   int32_t max_refine; /* refinement steps (default 10) */
-  double inner_tol;   /* relative tolerance of each inner solve (default 1e-3) */
+  double inner_tol;   /* relative tolerance of each inner solve (default 3e-3); a step that
+                         needs less to reach tol/2 asks only for that */
   int32_t reserved[3];
 } nesa_solve_opts;
 typedef struct {

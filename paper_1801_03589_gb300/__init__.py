@@ -331,7 +331,7 @@ class Nesa:
         return loss.value, g
 
     def solve(self, b, tol, x=None, restart=50, max_iters=1000, check=True, mixed=False, max_refine=10,
-              inner_tol=1e-3, precond=PRECOND_NONE):
+              inner_tol=3e-3, precond=PRECOND_NONE):
         """Restarted GMRES on the device for Z~ x = b (b: [nrhs, N] complex128 CUDA).
         mixed=True: FP64 iterative refinement around GMRES on the low-precision product.
         Returns (x, info dict).  With check=False a non-converged solve returns instead

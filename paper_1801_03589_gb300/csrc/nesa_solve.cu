@@ -11,6 +11,7 @@
 //
 // Every step of the iteration runs in kernels; the host only launches them and reads
 // back one flag per right-hand side after each Arnoldi step.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -519,15 +520,20 @@ static int refine_run(nesa_ctx *c, const cplx *b, cplx *x, int nrhs, double tol,
   for (int it = 0;; ++it) {
     norms(W->ro, W->onrm, rn);
     bool done = true;
+    double emax = 0.0;
     for (int r = 0; r < nrhs; ++r) {
       double e = bn[r] > 0.0 ? rn[r] / bn[r] : 0.0;
       if (!std::isfinite(e)) return NESA_ERR_NUMERIC;
       done &= e <= tol;
+      emax = std::max(emax, e);
     }
     if (done || it >= o.max_refine || I.iterations >= o.max_iters) break;
+    // the inner solve reduces the residual by inner_tol, or only by what is left to
+    // reach half the target when that is less
+    const double inner = std::min(0.5, std::max(o.inner_tol, 0.5 * tol / emax));
     nesa_solve_info Ii;
     std::memset(&Ii, 0, sizeof(Ii));
-    int si = gmres_run(c, W->ro, W->dx, nrhs, o.inner_tol, o.restart, o.max_iters - I.iterations,
+    int si = gmres_run(c, W->ro, W->dx, nrhs, inner, o.restart, o.max_iters - I.iterations,
                        NESA_PART_ALL | NESA_PART_MIXED, o.precond, Ii);
     I.iterations += Ii.iterations;
     I.matvecs += Ii.matvecs;
@@ -599,7 +605,7 @@ void nesa_default_solve_opts(nesa_solve_opts *o) {
   o->max_iters = 1000;
   o->mixed = 0;
   o->max_refine = 10;
-  o->inner_tol = 1e-3;
+  o->inner_tol = 3e-3;
 }
 
 int nesa_solve(nesa_ctx *c, const nesa_c128 *b_dev, nesa_c128 *x_dev, int nrhs, double tol,
