@@ -332,12 +332,12 @@ static void prepare_rc(nesa_ctx *c, TcLevel &t, int l, int rc) {
 }
 
 // Right-hand sides per chunk at level l: the largest divisor of nrhs for which the
-// per-pair output P stays within about 1 GB.
+// per-pair output P stays within about 4 GB.
 static int level_rc(nesa_ctx *c, int l, int nrhs) {
   const DevLevel &d = c->lev[l];
   const bool down = l > c->l0;
   const double per_rhs = 4.0 * 8.0 * d.q * (double)std::max<int64_t>(1, d.nil + (down ? d.nbox : 0));
-  int rc = (int)std::max(1.0, std::min((double)nrhs, 1.0e9 / per_rhs));
+  int rc = (int)std::max(1.0, std::min((double)nrhs, 4.0e9 / per_rhs));
   while (nrhs % rc) --rc;
   return rc;
 }
