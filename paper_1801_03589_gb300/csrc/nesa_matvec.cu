@@ -94,12 +94,16 @@ static Tiling tiling(int q) {
 constexpr int JC = 512;
 
 // ------------------------------------------------------------------ radiation (Eq. 10)
-template <typename CT>
+// Right-hand sides in blocks of RB: every V value is loaded once per block (the x values
+// of the block's columns, jc at a time, sit in shared memory as [jc][RB]).  Per
+// right-hand side the summation order over the columns is that of one at a time.
+template <typename CT, int RB>
 __global__ void __launch_bounds__(512) k_radiate(CT *__restrict__ s, const CT *__restrict__ V,
                                                  const int32_t *__restrict__ vc_ptr, const int32_t *__restrict__ vc_rwg,
-                                                 const cplx *__restrict__ x, int64_t n, int nrhs, int q, int tr) {
+                                                 const cplx *__restrict__ x, int64_t n, int nrhs, int q, int tr,
+                                                 int jc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  CT *xs = (CT *)smem_raw;  // [JC]
+  CT *xs = (CT *)smem_raw;  // [jc][RB]
   const int32_t b = blockIdx.x;
   const int tile = blockIdx.y;
   const int ch = threadIdx.x / tr;
@@ -107,19 +111,48 @@ __global__ void __launch_bounds__(512) k_radiate(CT *__restrict__ s, const CT *_
   const bool active = ch < 4 && i < q;
   const int32_t g0 = vc_ptr[b], ns = vc_ptr[b + 1] - g0;
   const CT *Vb = V + (int64_t)4 * g0 * q;
-  for (int r = 0; r < nrhs; ++r) {
-    CT acc = {0, 0};
-    for (int j0 = 0; j0 < ns; j0 += JC) {
-      const int len = min(JC, ns - j0);
+  if constexpr (RB == 1) {  // one right-hand side at a time
+    for (int r = 0; r < nrhs; ++r) {
+      CT acc = {0, 0};
+      for (int j0 = 0; j0 < ns; j0 += jc) {
+        const int len = min(jc, ns - j0);
+        __syncthreads();
+        for (int j = threadIdx.x; j < len; j += blockDim.x)
+          xs[j] = from64<CT>(x[(int64_t)r * n + vc_rwg[g0 + j0 + j]]);
+        __syncthreads();
+        if (!active) continue;
+        const CT *vp = Vb + (int64_t)4 * j0 * q + (int64_t)ch * q + i;
+#pragma unroll 4
+        for (int j = 0; j < len; ++j) cfma(acc, vp[(int64_t)4 * j * q], xs[j]);
+      }
+      if (active) s[((int64_t)b * 4 * nrhs + 4 * r + ch) * q + i] = acc;
+    }
+    return;
+  }
+  for (int r0 = 0; r0 < nrhs; r0 += RB) {
+    const int rb = min(RB, nrhs - r0);
+    CT acc[RB] = {};
+    for (int j0 = 0; j0 < ns; j0 += jc) {
+      const int len = min(jc, ns - j0);
       __syncthreads();
-      for (int j = threadIdx.x; j < len; j += blockDim.x) xs[j] = from64<CT>(x[(int64_t)r * n + vc_rwg[g0 + j0 + j]]);
+      for (int t = threadIdx.x; t < len * RB; t += blockDim.x) {
+        const int j = t / RB, rr = t % RB;
+        xs[t] = rr < rb ? from64<CT>(x[(int64_t)(r0 + rr) * n + vc_rwg[g0 + j0 + j]]) : CT{};
+      }
       __syncthreads();
       if (!active) continue;
       const CT *vp = Vb + (int64_t)4 * j0 * q + (int64_t)ch * q + i;
 #pragma unroll 4
-      for (int j = 0; j < len; ++j) cfma(acc, vp[(int64_t)4 * j * q], xs[j]);
+      for (int j = 0; j < len; ++j) {
+        const CT v = vp[(int64_t)4 * j * q];
+#pragma unroll
+        for (int rr = 0; rr < RB; ++rr) cfma(acc[rr], v, xs[j * RB + rr]);
+      }
     }
-    if (active) s[((int64_t)b * 4 * nrhs + 4 * r + ch) * q + i] = acc;
+    if (active)
+#pragma unroll
+      for (int rr = 0; rr < RB; ++rr)
+        if (rr < rb) s[((int64_t)b * 4 * nrhs + 4 * (r0 + rr) + ch) * q + i] = acc[rr];
   }
 }
 
@@ -416,11 +449,14 @@ static void run_product(nesa_ctx *c, const OpView<CT> &op, const cplx *x, cplx *
     {  // radiation
       DevLevel &d = c->lev[L];
       Tiling t = tiling(d.q);
-      size_t smem = sizeof(CT) * (size_t)std::min(JC, std::max(1, c->max_leaf_cols));
+      const int rbk = nrhs >= 8 ? 8 : 1;  // right-hand sides per V pass
+      const int jc = std::min(JC, (int)(32768 / (rbk * sizeof(CT))));
+      size_t smem = sizeof(CT) * rbk * (size_t)std::min(jc, std::max(1, c->max_leaf_cols));
       StageScope sc(c, 0, 32.0 * nrhs * ncol * d.q,
                     B * (4.0 * ncol * d.q + 4.0 * nrhs * d.nbox * d.q) + 16.0 * nrhs * c->n);
-      k_radiate<CT><<<dim3((unsigned)d.nbox, t.ntile), t.threads, smem, st>>>(op.s[L], op.V, c->d_vc_ptr, c->d_vc_rwg,
-                                                                              x, c->n, nrhs, d.q, t.tr);
+      auto rad = rbk == 8 ? k_radiate<CT, 8> : k_radiate<CT, 1>;
+      rad<<<dim3((unsigned)d.nbox, t.ntile), t.threads, smem, st>>>(op.s[L], op.V, c->d_vc_ptr, c->d_vc_rwg, x, c->n,
+                                                                    nrhs, d.q, t.tr, jc);
     }
     for (int l = L; l > l0; --l) {  // source transfer
       DevLevel &d = c->lev[l], &p = c->lev[l - 1];
