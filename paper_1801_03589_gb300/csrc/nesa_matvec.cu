@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(256) k_near_receive(cplx *__restrict__ y, cons
 // entries per lane and step (16- and 32-byte streaming loads) and gathers x from its
 // internal-order complex64 copy xp; reception reads each V column and the leaf's
 // outgoing field as contiguous 4Q-value blocks, two values per lane and load.
-template <int RB>
+template <int RB, bool ACC>
 __global__ void __launch_bounds__(256) k_near_receive_v(cplx *__restrict__ y, const cplxf *__restrict__ xp, int64_t n,
                                                         int nrhs, const int32_t *__restrict__ perm,
                                                         const int64_t *__restrict__ nz_ptr,
@@ -374,8 +374,62 @@ __global__ void __launch_bounds__(256) k_near_receive_v(cplx *__restrict__ y, co
         v.x += __shfl_down_sync(0xffffffffu, v.x, off);
         v.y += __shfl_down_sync(0xffffffffu, v.y, off);
       }
-      if (lane == 0 && rr < rb) y[(int64_t)(r0 + rr) * n + m] = v;
+      if (lane == 0 && rr < rb) {
+        cplx &out = y[(int64_t)(r0 + rr) * n + m];
+        if (ACC) {  // add to the near field written by k_near_wide
+          out.x += v.x;
+          out.y += v.y;
+        } else {
+          out = v;
+        }
+      }
     }
+  }
+}
+
+// Near field of the mixed product for many right-hand sides (nrhs >= 32): one warp per
+// (internal row, group of 32 right-hand sides), lane = right-hand side.  Every entry's
+// value and column are read once per group (the lanes load the same address), and the
+// x values of a column for the group are one coalesced 256-byte load (xw is [n][nrhs]).
+// Four FP32 partial sums per lane (one per entry of a group of four), added in FP64.
+__global__ void __launch_bounds__(256) k_near_wide(cplx *__restrict__ y, const cplxf *__restrict__ xw, int64_t n,
+                                                   int nrhs, const int32_t *__restrict__ perm,
+                                                   const int64_t *__restrict__ nz_ptr,
+                                                   const int32_t *__restrict__ nz_col,
+                                                   const cplxf *__restrict__ nz_val) {
+  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int ngrp = (nrhs + 31) >> 5;
+  const int64_t r = wid / ngrp;
+  if (r >= n) return;
+  const int rr = (int)(wid % ngrp) * 32 + lane;
+  const bool on = rr < nrhs;
+  const cplxf *xc = xw + (on ? rr : 0);
+  const int64_t z0 = nz_ptr[r], z1 = nz_ptr[r + 1];
+  cplxf a0 = {0.0f, 0.0f}, a1 = a0, a2 = a0, a3 = a0;
+#pragma unroll 2
+  for (int64_t e = z0; e < z1; e += 4) {  // rows are padded to multiples of four
+    const int4 k = *(const int4 *)(nz_col + e);
+    const float4 va = *(const float4 *)(nz_val + e);
+    const float4 vb = *(const float4 *)(nz_val + e + 2);
+    cfma(a0, make_float2(va.x, va.y), xc[(int64_t)k.x * nrhs]);
+    cfma(a1, make_float2(va.z, va.w), xc[(int64_t)k.y * nrhs]);
+    cfma(a2, make_float2(vb.x, vb.y), xc[(int64_t)k.z * nrhs]);
+    cfma(a3, make_float2(vb.z, vb.w), xc[(int64_t)k.w * nrhs]);
+  }
+  if (on)
+    y[(int64_t)rr * n + perm[r]] = make_double2(((double)a0.x + (double)a1.x) + ((double)a2.x + (double)a3.x),
+                                                ((double)a0.y + (double)a1.y) + ((double)a2.y + (double)a3.y));
+}
+
+// xw[i][r] = complex64(x[r][perm[i]])   (right-hand sides innermost, for k_near_wide)
+__global__ void k_perm_x_wide(cplxf *__restrict__ xw, const cplx *__restrict__ x, const int32_t *__restrict__ perm,
+                              int64_t n, int nrhs) {
+  const int64_t total = n * nrhs;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / nrhs, r = t % nrhs;  // consecutive threads write consecutive xw
+    const cplx v = x[r * n + perm[i]];
+    xw[t] = make_float2((float)v.x, (float)v.y);
   }
 }
 
@@ -504,13 +558,22 @@ static void run_product(nesa_ctx *c, const OpView<CT> &op, const cplx *x, cplx *
               16.0 * 2.0 * nrhs * c->n;
   StageScope sc(c, 3, fl, by);
   if constexpr (std::is_same<CT, cplxf>::value) {
-    if (parts & NESA_PART_NEAR)
-      k_perm_x<<<(unsigned)std::min<int64_t>((c->n * nrhs + 255) / 256, 1 << 16), 256, 0, st>>>(c->d_xp, x, c->d_perm,
-                                                                                            c->n, nrhs);
-    auto near = nrhs == 1 ? k_near_receive_v<1> : k_near_receive_v<4>;
-    near<<<grid_for(c->n * 32, 256), 256, 0, st>>>(y, c->d_xp, c->n, nrhs, c->d_perm, c->d_nz_ptr4, c->d_nz_col4,
-                                                  op.nz_val, c->d_rx_ptr, c->d_rx_col, c->d_vc_leaf, op.V, op.o[L],
-                                                  dL.q, c->eta * c->k, 1.0 / (c->k * c->k), parts);
+    const unsigned pgrid = (unsigned)std::min<int64_t>((c->n * nrhs + 255) / 256, 1 << 16);
+    if (nrhs >= 32 && (parts & NESA_PART_NEAR)) {  // many right-hand sides: lane per right-hand side
+      k_perm_x_wide<<<pgrid, 256, 0, st>>>(c->d_xp, x, c->d_perm, c->n, nrhs);
+      k_near_wide<<<grid_for(c->n * ((nrhs + 31) / 32) * 32, 256), 256, 0, st>>>(
+          y, c->d_xp, c->n, nrhs, c->d_perm, c->d_nz_ptr4, c->d_nz_col4, op.nz_val);
+      if (parts & NESA_PART_FAR)
+        k_near_receive_v<4, true><<<grid_for(c->n * 32, 256), 256, 0, st>>>(
+            y, c->d_xp, c->n, nrhs, c->d_perm, c->d_nz_ptr4, c->d_nz_col4, op.nz_val, c->d_rx_ptr, c->d_rx_col,
+            c->d_vc_leaf, op.V, op.o[L], dL.q, c->eta * c->k, 1.0 / (c->k * c->k), NESA_PART_FAR);
+    } else {
+      if (parts & NESA_PART_NEAR) k_perm_x<<<pgrid, 256, 0, st>>>(c->d_xp, x, c->d_perm, c->n, nrhs);
+      auto near = nrhs == 1 ? k_near_receive_v<1, false> : k_near_receive_v<4, false>;
+      near<<<grid_for(c->n * 32, 256), 256, 0, st>>>(y, c->d_xp, c->n, nrhs, c->d_perm, c->d_nz_ptr4, c->d_nz_col4,
+                                                    op.nz_val, c->d_rx_ptr, c->d_rx_col, c->d_vc_leaf, op.V, op.o[L],
+                                                    dL.q, c->eta * c->k, 1.0 / (c->k * c->k), parts);
+    }
   } else {
     auto near = nrhs == 1 ? k_near_receive<CT, 1> : k_near_receive<CT, 4>;
     near<<<grid_for(c->n * 32, 256), 256, 0, st>>>(y, x, c->n, nrhs, c->d_nz_ptr, c->d_nz_col, op.nz_val,
