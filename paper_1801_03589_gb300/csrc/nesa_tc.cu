@@ -87,28 +87,36 @@ __global__ void k_prep_A(__nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo, const cplx *M
 
 // x (complex64, [box][4 nrhs][q], column 4r + ch) -> hi/lo blocks [box][rc][nkc][256]
 // for the right-hand sides r0 .. r0+rc-1: block (box, r, kc) holds the 8 columns
-// 2ch + part (part 0: Re x_ch, 1: Im x_ch) at K = 32 kc .. 32 kc + 31 (zero past q)
+// 2ch + part (part 0: Re x_ch, 1: Im x_ch) at K = 32 kc .. 32 kc + 31 (zero past q).
+// One thread per 16-byte row of a core matrix: 8 consecutive K of one column.
 __global__ void k_split(__nv_bfloat16 *x_hi, __nv_bfloat16 *x_lo, const cplxf *x, int64_t nbox, int nrhs, int r0,
                         int rc, int q, int nkc) {
-  const int64_t total = nbox * rc * nkc * (int64_t)tc::GROUP_ELEMS;
+  const int64_t total = nbox * rc * nkc * 32;  // (kq, column) rows per block
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
-    const int e = (int)(idx % tc::GROUP_ELEMS);  // (column, k) with k fastest
-    int64_t rest = idx / tc::GROUP_ELEMS;
+    const int row = (int)(idx % 32);  // kq * 8 + column
+    int64_t rest = idx / 32;
     const int kc = (int)(rest % nkc);
     rest /= nkc;
     const int r = (int)(rest % rc);
     const int64_t box = rest / rc;
-    const int col = e / tc::TK, kloc = e % tc::TK, k = kc * tc::TK + kloc;
-    float v = 0.0f;
-    if (k < q) {
-      const cplxf z = x[(box * 4 * nrhs + 4 * (r0 + r) + (col >> 1)) * q + k];
-      v = (col & 1) ? z.y : z.x;
+    const int kq = row >> 3, col = row & 7, k0 = kc * tc::TK + kq * 8;
+    const cplxf *src = x + (box * 4 * nrhs + 4 * (r0 + r) + (col >> 1)) * q;
+    __align__(16) __nv_bfloat16 hi[8], lo[8];
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) {
+      const int k = k0 + kk;
+      float v = 0.0f;
+      if (k < q) {
+        const cplxf z = src[k];
+        v = (col & 1) ? z.y : z.x;
+      }
+      hi[kk] = __float2bfloat16_rn(v);
+      lo[kk] = __float2bfloat16_rn(v - __bfloat162float(hi[kk]));
     }
-    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-    const int64_t out = ((box * rc + r) * nkc + kc) * tc::GROUP_ELEMS + tc::b_group_elem(col, kloc);
-    x_hi[out] = hi;
-    x_lo[out] = __float2bfloat16_rn(v - __bfloat162float(hi));
+    const int64_t out = ((box * rc + r) * nkc + kc) * tc::GROUP_ELEMS + tc::b_group_elem(col, kq * 8);
+    *(uint4 *)(x_hi + out) = *(const uint4 *)hi;
+    *(uint4 *)(x_lo + out) = *(const uint4 *)lo;
   }
 }
 
@@ -356,11 +364,11 @@ void tc_translate_level(nesa_ctx *c, int l, const cplxf *s, cplxf *o, const cplx
   prepare_rc(c, t, l, rc);
   for (int r0 = 0; r0 < nrhs; r0 += rc) {
     if (!(t.s_split && rc == nrhs))
-      k_split<<<grid_of(d.nbox * rc * t.tr.nkc * (int64_t)tc::GROUP_ELEMS), 256, 0, st>>>(t.s_hi, t.s_lo, s, d.nbox,
+      k_split<<<grid_of(d.nbox * rc * t.tr.nkc * (int64_t)32), 256, 0, st>>>(t.s_hi, t.s_lo, s, d.nbox,
                                                                                          nrhs, r0, rc, d.q, t.tr.nkc);
     if (down) {
       const DevLevel &p = c->lev[l - 1];
-      k_split<<<grid_of(p.nbox * rc * t.dn.nkc * (int64_t)tc::GROUP_ELEMS), 256, 0, st>>>(
+      k_split<<<grid_of(p.nbox * rc * t.dn.nkc * (int64_t)32), 256, 0, st>>>(
           t.o_hi, t.o_lo, op, p.nbox, nrhs, r0, rc, p.q, t.dn.nkc);
     }
     if (c->autotune) {
@@ -406,7 +414,7 @@ void tc_upward_level(nesa_ctx *c, int l, const cplxf *s, cplxf *sp, int nrhs) {
   const int rc = level_rc(c, l, nrhs);
   prepare_rc(c, t, l, rc);
   for (int r0 = 0; r0 < nrhs; r0 += rc) {
-    k_split<<<grid_of(d.nbox * rc * t.tr.nkc * (int64_t)tc::GROUP_ELEMS), 256, 0, st>>>(t.s_hi, t.s_lo, s, d.nbox,
+    k_split<<<grid_of(d.nbox * rc * t.tr.nkc * (int64_t)32), 256, 0, st>>>(t.s_hi, t.s_lo, s, d.nbox,
                                                                                        nrhs, r0, rc, d.q, t.tr.nkc);
     if (c->autotune && t.up.tuned_rc != rc) autotune(c, t.up, t.s_hi, t.s_lo, t.P_up, rc);
     make_work(c, t.up, rc, t.up.tn);
