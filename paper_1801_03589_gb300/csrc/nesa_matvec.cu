@@ -156,6 +156,45 @@ __global__ void __launch_bounds__(512) k_radiate(CT *__restrict__ s, const CT *_
   }
 }
 
+// Radiation of the mixed product with Q even: every thread owns two consecutive rows
+// i, i+1 of one channel, so each V access is one 16-byte load (same order over j).
+__global__ void __launch_bounds__(512) k_radiate2(cplxf *__restrict__ s, const cplxf *__restrict__ V,
+                                                  const int32_t *__restrict__ vc_ptr,
+                                                  const int32_t *__restrict__ vc_rwg, const cplx *__restrict__ x,
+                                                  int64_t n, int nrhs, int q, int tr2, int jc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplxf *xs = (cplxf *)smem_raw;  // [jc]
+  const int32_t b = blockIdx.x;
+  const int ch = threadIdx.x / tr2;
+  const int i = 2 * (blockIdx.y * tr2 + threadIdx.x % tr2);
+  const bool active = ch < 4 && i < q;
+  const int32_t g0 = vc_ptr[b], ns = vc_ptr[b + 1] - g0;
+  const cplxf *Vb = V + (int64_t)4 * g0 * q;
+  for (int r = 0; r < nrhs; ++r) {
+    cplxf a0 = {0.0f, 0.0f}, a1 = {0.0f, 0.0f};
+    for (int j0 = 0; j0 < ns; j0 += jc) {
+      const int len = min(jc, ns - j0);
+      __syncthreads();
+      for (int j = threadIdx.x; j < len; j += blockDim.x) {
+        const cplx v = x[(int64_t)r * n + vc_rwg[g0 + j0 + j]];
+        xs[j] = make_float2((float)v.x, (float)v.y);
+      }
+      __syncthreads();
+      if (!active) continue;
+      const cplxf *vp = Vb + (int64_t)4 * j0 * q + (int64_t)ch * q + i;
+#pragma unroll 4
+      for (int j = 0; j < len; ++j) {
+        const float4 v2 = __ldcs((const float4 *)(vp + (int64_t)4 * j * q));
+        const cplxf xj = xs[j];
+        cfma(a0, make_float2(v2.x, v2.y), xj);
+        cfma(a1, make_float2(v2.z, v2.w), xj);
+      }
+    }
+    if (active)
+      *(float4 *)(s + ((int64_t)b * 4 * nrhs + 4 * r + ch) * q + i) = make_float4(a0.x, a0.y, a1.x, a1.y);
+  }
+}
+
 // acc += M[i + j*ld] * col(ch)[j] over j < kdim, with the column (4 channels of kdim
 // values at src, channel stride kdim) staged through shared memory in chunks of JC
 template <typename CT>
@@ -508,9 +547,20 @@ static void run_product(nesa_ctx *c, const OpView<CT> &op, const cplx *x, cplx *
       size_t smem = sizeof(CT) * rbk * (size_t)std::min(jc, std::max(1, c->max_leaf_cols));
       StageScope sc(c, 0, 32.0 * nrhs * ncol * d.q,
                     B * (4.0 * ncol * d.q + 4.0 * nrhs * d.nbox * d.q) + 16.0 * nrhs * c->n);
-      auto rad = rbk == 8 ? k_radiate<CT, 8> : k_radiate<CT, 1>;
-      rad<<<dim3((unsigned)d.nbox, t.ntile), t.threads, smem, st>>>(op.s[L], op.V, c->d_vc_ptr, c->d_vc_rwg, x, c->n,
-                                                                    nrhs, d.q, t.tr, jc);
+      bool done = false;
+      if constexpr (std::is_same<CT, cplxf>::value) {
+        if (rbk == 1 && d.q % 2 == 0) {  // two rows per thread, 16-byte V loads
+          Tiling t2 = tiling(d.q / 2);
+          k_radiate2<<<dim3((unsigned)d.nbox, t2.ntile), t2.threads, smem, st>>>(
+              op.s[L], op.V, c->d_vc_ptr, c->d_vc_rwg, x, c->n, nrhs, d.q, t2.tr, jc);
+          done = true;
+        }
+      }
+      if (!done) {
+        auto rad = rbk == 8 ? k_radiate<CT, 8> : k_radiate<CT, 1>;
+        rad<<<dim3((unsigned)d.nbox, t.ntile), t.threads, smem, st>>>(op.s[L], op.V, c->d_vc_ptr, c->d_vc_rwg, x,
+                                                                      c->n, nrhs, d.q, t.tr, jc);
+      }
     }
     for (int l = L; l > l0; --l) {  // source transfer
       DevLevel &d = c->lev[l], &p = c->lev[l - 1];
