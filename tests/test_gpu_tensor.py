@@ -78,3 +78,18 @@ def test_refined_solve_with_tensor_product():
     assert info["converged"] == 1 and info["rel_residual"][0] <= 1e-5
     r = B - g.matvec(x)
     assert float(r.abs().pow(2).sum().sqrt() / B.abs().pow(2).sum().sqrt()) <= 1e-5
+
+
+def test_many_rhs_near_field_partial_group():
+    # 40 right-hand sides: the near field runs one lane per right-hand side in groups of
+    # 32 (the second group partly idle); every column must match its own single product
+    # (different summation order in FP32: bounded by the mixed tolerance)
+    import paper_1801_03589_gb300 as nesa
+    c, g = build("C1b")
+    X = torch.from_numpy(random_coefficients(g.n, 40, seed=57)).cuda()
+    for parts in (nesa.PART_ALL, nesa.PART_NEAR):
+        p = parts | nesa.PART_MIXED
+        Y = g.matvec(X, parts=p).cpu().numpy()
+        for r in (0, 31, 32, 39):
+            y1 = g.matvec(X[r:r + 1].contiguous(), parts=p).cpu().numpy()[0]
+            assert rel(Y[r], y1) < TOL_TC, (parts, r, rel(Y[r], y1))
