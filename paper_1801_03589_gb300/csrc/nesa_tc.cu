@@ -24,7 +24,7 @@ struct TcGemm {
   int q = 0, kdim = 0;  // complex rows and columns of each matrix
   int nk16 = 0, nkc = 0, nmt = 0;
   int64_t nslot = 0, nent = 0;
-  __nv_bfloat16 *A_hi = nullptr, *A_lo = nullptr;  // [slot][nmt][nkc][4096]
+  __nv_bfloat16 *A = nullptr;  // [slot][nmt][nkc][2][4096]: hi then lo plane of every tile
   std::vector<int32_t> h_ptr, h_dst, h_src;         // entries (output block, source box) by slot
   int tn = 128;                   // column-tile width (autotuned)
   int tuned_rc = 0;               // chunk size the width was tuned for
@@ -58,8 +58,7 @@ static TcState *state(nesa_ctx *c) { return (TcState *)c->tc_state; }
 // Real A tiles of nslot complex matrices M (q x kdim, column-major, complex128): row 2i
 // of A is Re M(i,:), row 2i+1 is Im M(i,:); rows >= 2q and columns >= kdim are zero.
 // Each value v is split as hi = bf16(v), lo = bf16(v - hi).
-__global__ void k_prep_A(__nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo, const cplx *M, int64_t nslot, int q, int kdim,
-                         int nmt, int nkc) {
+__global__ void k_prep_A(__nv_bfloat16 *A, const cplx *M, int64_t nslot, int q, int kdim, int nmt, int nkc) {
   const int64_t total = nslot * nmt * nkc * (int64_t)tc::TILE_ELEMS;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
@@ -79,9 +78,9 @@ __global__ void k_prep_A(__nv_bfloat16 *A_hi, __nv_bfloat16 *A_lo, const cplx *M
     }
     const __nv_bfloat16 hi = __float2bfloat16_rn((float)v);
     const __nv_bfloat16 lo = __float2bfloat16_rn((float)(v - (double)__bfloat162float(hi)));
-    const int64_t out = ((slot * nmt + mt) * nkc + kc) * tc::TILE_ELEMS + tc::a_tile_elem(rloc, kloc);
-    A_hi[out] = hi;
-    A_lo[out] = lo;
+    const int64_t out = ((slot * nmt + mt) * nkc + kc) * 2 * tc::TILE_ELEMS + tc::a_tile_elem(rloc, kloc);
+    A[out] = hi;
+    A[out + tc::TILE_ELEMS] = lo;
   }
 }
 
@@ -151,10 +150,9 @@ static void gemm_setup(nesa_ctx *c, TcGemm &g, const cplx *M, int64_t nslot, int
   g.nslot = nslot;
   g.nent = (int64_t)ent_slot.size();
   const int64_t nel = nslot * g.nmt * (int64_t)g.nkc * tc::TILE_ELEMS;
-  g.A_hi = (__nv_bfloat16 *)dalloc(c, sizeof(__nv_bfloat16) * nel);
-  g.A_lo = (__nv_bfloat16 *)dalloc(c, sizeof(__nv_bfloat16) * nel);
-  k_prep_A<<<(unsigned)std::min<int64_t>((nel + 255) / 256, 1 << 20), 256, 0, c->stream>>>(g.A_hi, g.A_lo, M, nslot,
-                                                                                         q, kdim, g.nmt, g.nkc);
+  g.A = (__nv_bfloat16 *)dalloc(c, sizeof(__nv_bfloat16) * 2 * nel);
+  k_prep_A<<<(unsigned)std::min<int64_t>((nel + 255) / 256, 1 << 20), 256, 0, c->stream>>>(g.A, M, nslot, q, kdim,
+                                                                                         g.nmt, g.nkc);
   check_cuda(cudaGetLastError(), "prep A");
   // entries grouped by slot (stable: ascending entry order within a slot)
   g.h_ptr.assign(nslot + 1, 0);
@@ -265,7 +263,7 @@ static void launch_gemm(nesa_ctx *c, const TcGemm &g, const __nv_bfloat16 *B_hi,
   TcState *S = state(c);
   if (g.nwork == 0) return;
   (void)rc;
-  tc::GemmArgs a{g.work, g.wsrc, g.wdst, g.nwork, g.A_hi, g.A_lo, B_hi, B_lo, P, g.q, g.nk16, g.nmt, S->err};
+  tc::GemmArgs a{g.work, g.wsrc, g.wdst, g.nwork, g.A, B_hi, B_lo, P, g.q, g.nk16, g.nmt, S->err};
   const unsigned grid = (unsigned)std::min<int64_t>(g.nwork, S->nsm);
   cudaStream_t st = c->stream;
   switch (g.work_tn) {
