@@ -137,6 +137,7 @@ typedef struct {
   int64_t v_columns;                /* sum over leaves of the RWG columns of V */
   int64_t device_bytes;             /* device memory held by the context */
   double build_seconds;             /* wall time of nesa_build */
+  int64_t max_leaf_columns;         /* largest number of V columns of one leaf */
 } nesa_info;
 
 /* Default parameters: leaf 0.25, 3 levels, NESA_Q_AUTO, q_fixed 100, q_digits 5,

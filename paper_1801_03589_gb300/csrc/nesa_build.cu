@@ -756,6 +756,7 @@ int nesa_build(const nesa_mesh *mesh, double k, const nesa_params *params, nesa_
     I.near_nnz = nnz;
   }
   I.v_columns = (int64_t)c->h.vc_rwg.size();
+  I.max_leaf_columns = c->max_leaf_cols;
   if (params->precision == NESA_MIXED) {
     try {
       build_mixed(c);

@@ -102,6 +102,7 @@ struct nesa_ctx {
   int32_t *d_nz_col4 = nullptr;
   int32_t *d_perm = nullptr;           // internal index -> ABI index
   nesa::cplxf *d_xp = nullptr;         // x in the internal order, complex64 [nrhs][n]
+  nesa::cplxf *d_rcv = nullptr;        // reception per V column, [ncol][nrhs] (nrhs >= 32)
   nesa::cplxf *d_V32 = nullptr;
   int nrhs_cap32 = 0;
   // levels

@@ -53,7 +53,10 @@ int ensure_workspace(nesa_ctx *c, int nrhs) {
 static void ensure_workspace32(nesa_ctx *c, int nrhs) {
   if (nrhs <= c->nrhs_cap32) return;
   dfree(c, c->d_xp);
+  dfree(c, c->d_rcv);
+  c->d_rcv = nullptr;
   c->d_xp = (cplxf *)dalloc(c, sizeof(cplxf) * (size_t)std::max<int64_t>(1, c->n * nrhs));
+  if (nrhs >= 32) c->d_rcv = (cplxf *)dalloc(c, sizeof(cplxf) * (size_t)c->info.v_columns * nrhs);
   for (int l = c->l0; l <= c->L; ++l) {
     DevLevel &d = c->lev[l];
     dfree(c, d.s32);
@@ -426,16 +429,77 @@ __global__ void __launch_bounds__(256) k_near_receive_v(cplx *__restrict__ y, co
   }
 }
 
-// Near field of the mixed product for many right-hand sides (nrhs >= 32): one warp per
-// (internal row, group of 32 right-hand sides), lane = right-hand side.  Every entry's
-// value and column are read once per group (the lanes load the same address), and the
-// x values of a column for the group are one coalesced 256-byte load (xw is [n][nrhs]).
-// Four FP32 partial sums per lane (one per entry of a group of four), added in FP64.
+// Reception of the mixed product for many right-hand sides (nrhs >= 32), one leaf b and
+// one group of 32 right-hand sides per block, as a small complex product per leaf:
+//   R[g][r] = sum_{ch,i} gamma_ch V[g][ch][i] o_b[r][ch][i]       (Eq. 14, U = V^T)
+// for the leaf's V columns g (an RWG function has one column per leaf that holds one of
+// its triangles; k_near_wide adds its columns up).  V and o go through shared memory in
+// chunks of RC_KC of the 4Q values: V as [column][k] (every lane of a warp reads the
+// same value), o transposed to [k][right-hand side] (consecutive lanes, consecutive
+// values).  Thread (warp w, lane) owns right-hand side r0 + lane and the columns
+// w, w + 8, ... of a block of RC_COLS; FP32 sums in the order k = 0 .. 4Q-1.
+constexpr int RC_KC = 32, RC_COLS = 64;
+__global__ void __launch_bounds__(256) k_receive_leaf(cplxf *__restrict__ R, const cplxf *__restrict__ V,
+                                                      const cplxf *__restrict__ oL, const int32_t *__restrict__ vc_ptr,
+                                                      int nrhs, int q, float mk2) {
+  __shared__ __align__(16) cplxf Vs[RC_COLS][RC_KC];
+  __shared__ __align__(16) cplxf Os[RC_KC][33];
+  const int64_t b = blockIdx.x;
+  const int r0 = blockIdx.y * 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int32_t g0 = vc_ptr[b], ns = vc_ptr[b + 1] - g0;
+  const int q4 = 4 * q, q3 = 3 * q;
+  const cplxf *ob = oL + b * nrhs * (int64_t)q4;  // o_b[r][ch][i] at ob + r * 4Q + ch * Q + i
+  for (int c0 = 0; c0 < ns; c0 += RC_COLS) {
+    const int nc = min(RC_COLS, ns - c0);
+    cplxf acc[RC_COLS / 8] = {};
+    for (int k0 = 0; k0 < q4; k0 += RC_KC) {
+      const int kn = min(RC_KC, q4 - k0);
+      __syncthreads();
+      for (int t = threadIdx.x; t < RC_COLS * RC_KC; t += blockDim.x) {
+        const int cc = t / RC_KC, kk = t % RC_KC;
+        cplxf v = make_float2(0.0f, 0.0f);
+        if (cc < nc && kk < kn) {
+          v = V[(int64_t)(g0 + c0 + cc) * q4 + k0 + kk];
+          const float gm = k0 + kk < q3 ? 1.0f : mk2;
+          v = make_float2(gm * v.x, gm * v.y);
+        }
+        Vs[cc][kk] = v;
+      }
+      for (int t = threadIdx.x; t < 32 * RC_KC; t += blockDim.x) {
+        const int rr = t / RC_KC, kk = t % RC_KC;
+        Os[kk][rr] = r0 + rr < nrhs && kk < kn ? ob[(int64_t)(r0 + rr) * q4 + k0 + kk] : make_float2(0.0f, 0.0f);
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int kk = 0; kk < RC_KC; ++kk) {  // zeros past kn
+        const cplxf o = Os[kk][lane];
+#pragma unroll
+        for (int j = 0; j < RC_COLS / 8; ++j) cfma(acc[j], Vs[warp + 8 * j][kk], o);
+      }
+    }
+    if (r0 + lane < nrhs)
+#pragma unroll
+      for (int j = 0; j < RC_COLS / 8; ++j)
+        if (warp + 8 * j < nc) R[(int64_t)(g0 + c0 + warp + 8 * j) * nrhs + r0 + lane] = acc[j];
+  }
+}
+
+// Near field and reception sum of the mixed product for many right-hand sides
+// (nrhs >= 32): one warp per (internal row, group of 32 right-hand sides), lane = right-
+// hand side.  Every entry's value and column are read once per group (the lanes load
+// the same address), and the x values of a column for the group are one coalesced
+// 256-byte load (xw is [n][nrhs]).  Four FP32 partial sums per lane (one per entry of a
+// group of four), added in FP64.  The far part adds the reception values R of the row's
+// V columns (k_receive_leaf) times -i eta k.
 __global__ void __launch_bounds__(256) k_near_wide(cplx *__restrict__ y, const cplxf *__restrict__ xw, int64_t n,
                                                    int nrhs, const int32_t *__restrict__ perm,
                                                    const int64_t *__restrict__ nz_ptr,
                                                    const int32_t *__restrict__ nz_col,
-                                                   const cplxf *__restrict__ nz_val) {
+                                                   const cplxf *__restrict__ nz_val,
+                                                   const int32_t *__restrict__ rx_ptr,
+                                                   const int32_t *__restrict__ rx_col, const cplxf *__restrict__ R,
+                                                   double eta_k, int parts) {
   const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   const int ngrp = (nrhs + 31) >> 5;
@@ -443,22 +507,36 @@ __global__ void __launch_bounds__(256) k_near_wide(cplx *__restrict__ y, const c
   if (r >= n) return;
   const int rr = (int)(wid % ngrp) * 32 + lane;
   const bool on = rr < nrhs;
-  const cplxf *xc = xw + (on ? rr : 0);
-  const int64_t z0 = nz_ptr[r], z1 = nz_ptr[r + 1];
+  const int rc = on ? rr : 0;
   cplxf a0 = {0.0f, 0.0f}, a1 = a0, a2 = a0, a3 = a0;
+  if (parts & NESA_PART_NEAR) {
+    const cplxf *xc = xw + rc;
+    const int64_t z0 = nz_ptr[r], z1 = nz_ptr[r + 1];
 #pragma unroll 2
-  for (int64_t e = z0; e < z1; e += 4) {  // rows are padded to multiples of four
-    const int4 k = *(const int4 *)(nz_col + e);
-    const float4 va = *(const float4 *)(nz_val + e);
-    const float4 vb = *(const float4 *)(nz_val + e + 2);
-    cfma(a0, make_float2(va.x, va.y), xc[(int64_t)k.x * nrhs]);
-    cfma(a1, make_float2(va.z, va.w), xc[(int64_t)k.y * nrhs]);
-    cfma(a2, make_float2(vb.x, vb.y), xc[(int64_t)k.z * nrhs]);
-    cfma(a3, make_float2(vb.z, vb.w), xc[(int64_t)k.w * nrhs]);
+    for (int64_t e = z0; e < z1; e += 4) {  // rows are padded to multiples of four
+      const int4 k = *(const int4 *)(nz_col + e);
+      const float4 va = *(const float4 *)(nz_val + e);
+      const float4 vb = *(const float4 *)(nz_val + e + 2);
+      cfma(a0, make_float2(va.x, va.y), xc[(int64_t)k.x * nrhs]);
+      cfma(a1, make_float2(va.z, va.w), xc[(int64_t)k.y * nrhs]);
+      cfma(a2, make_float2(vb.x, vb.y), xc[(int64_t)k.z * nrhs]);
+      cfma(a3, make_float2(vb.z, vb.w), xc[(int64_t)k.w * nrhs]);
+    }
   }
-  if (on)
-    y[(int64_t)rr * n + perm[r]] = make_double2(((double)a0.x + (double)a1.x) + ((double)a2.x + (double)a3.x),
-                                                ((double)a0.y + (double)a1.y) + ((double)a2.y + (double)a3.y));
+  const int32_t m = perm[r];
+  double2 v = make_double2(((double)a0.x + (double)a1.x) + ((double)a2.x + (double)a3.x),
+                           ((double)a0.y + (double)a1.y) + ((double)a2.y + (double)a3.y));
+  if (parts & NESA_PART_FAR) {
+    double fx = 0.0, fy = 0.0;
+    for (int32_t e = rx_ptr[m]; e < rx_ptr[m + 1]; ++e) {
+      const cplxf f = R[(int64_t)rx_col[e] * nrhs + rc];
+      fx += f.x;
+      fy += f.y;
+    }
+    v.x += eta_k * fy;
+    v.y -= eta_k * fx;
+  }
+  if (on) y[(int64_t)rr * n + m] = v;
 }
 
 // xw[i][r] = complex64(x[r][perm[i]])   (right-hand sides innermost, for k_near_wide)
@@ -609,14 +687,14 @@ static void run_product(nesa_ctx *c, const OpView<CT> &op, const cplx *x, cplx *
   StageScope sc(c, 3, fl, by);
   if constexpr (std::is_same<CT, cplxf>::value) {
     const unsigned pgrid = (unsigned)std::min<int64_t>((c->n * nrhs + 255) / 256, 1 << 16);
-    if (nrhs >= 32 && (parts & NESA_PART_NEAR)) {  // many right-hand sides: lane per right-hand side
-      k_perm_x_wide<<<pgrid, 256, 0, st>>>(c->d_xp, x, c->d_perm, c->n, nrhs);
-      k_near_wide<<<grid_for(c->n * ((nrhs + 31) / 32) * 32, 256), 256, 0, st>>>(
-          y, c->d_xp, c->n, nrhs, c->d_perm, c->d_nz_ptr4, c->d_nz_col4, op.nz_val);
+    if (nrhs >= 32) {  // many right-hand sides: lane per right-hand side
+      if (parts & NESA_PART_NEAR) k_perm_x_wide<<<pgrid, 256, 0, st>>>(c->d_xp, x, c->d_perm, c->n, nrhs);
       if (parts & NESA_PART_FAR)
-        k_near_receive_v<4, true><<<grid_for(c->n * 32, 256), 256, 0, st>>>(
-            y, c->d_xp, c->n, nrhs, c->d_perm, c->d_nz_ptr4, c->d_nz_col4, op.nz_val, c->d_rx_ptr, c->d_rx_col,
-            c->d_vc_leaf, op.V, op.o[L], dL.q, c->eta * c->k, 1.0 / (c->k * c->k), NESA_PART_FAR);
+        k_receive_leaf<<<dim3((unsigned)c->nleaf, (unsigned)((nrhs + 31) / 32)), 256, 0, st>>>(
+            c->d_rcv, op.V, op.o[L], c->d_vc_ptr, nrhs, dL.q, (float)(-1.0 / (c->k * c->k)));
+      k_near_wide<<<grid_for(c->n * ((nrhs + 31) / 32) * 32, 256), 256, 0, st>>>(
+          y, c->d_xp, c->n, nrhs, c->d_perm, c->d_nz_ptr4, c->d_nz_col4, op.nz_val, c->d_rx_ptr, c->d_rx_col,
+          c->d_rcv, c->eta * c->k, parts);
     } else {
       if (parts & NESA_PART_NEAR) k_perm_x<<<pgrid, 256, 0, st>>>(c->d_xp, x, c->d_perm, c->n, nrhs);
       auto near = nrhs == 1 ? k_near_receive_v<1, false> : k_near_receive_v<4, false>;

@@ -82,14 +82,43 @@ def test_refined_solve_with_tensor_product():
 
 def test_many_rhs_near_field_partial_group():
     # 40 right-hand sides: the near field runs one lane per right-hand side in groups of
-    # 32 (the second group partly idle); every column must match its own single product
+    # 32 (the second group partly idle), and so does the per-leaf reception product; every
+    # column must match its own single product
     # (different summation order in FP32: bounded by the mixed tolerance)
     import paper_1801_03589_gb300 as nesa
     c, g = build("C1b")
     X = torch.from_numpy(random_coefficients(g.n, 40, seed=57)).cuda()
-    for parts in (nesa.PART_ALL, nesa.PART_NEAR):
+    for parts in (nesa.PART_ALL, nesa.PART_NEAR, nesa.PART_FAR):
         p = parts | nesa.PART_MIXED
         Y = g.matvec(X, parts=p).cpu().numpy()
         for r in (0, 31, 32, 39):
             y1 = g.matvec(X[r:r + 1].contiguous(), parts=p).cpu().numpy()[0]
             assert rel(Y[r], y1) < TOL_TC, (parts, r, rel(Y[r], y1))
+
+
+def test_many_rhs_reception_large_leaves():
+    # Three levels on the r = 1 sphere: leaves a quarter of the domain wide hold more V
+    # columns than the 64 of one column block of the per-leaf reception product (several
+    # blocks per leaf, the last one ragged).  40 right-hand sides against their single products (the row
+    # kernel's reception) and, for one column, against the oracle.
+    import paper_1801_03589_gb300 as nesa
+    c = get_config("C1b")
+    g = nesa.Nesa(c["vertices"], c["triangles"], c["k"], leaf_size=c["leaf_size"], n_levels=3,
+                  precision=nesa.MIXED, translate=nesa.TRANSLATE_TENSOR)
+    mc = g.info()["max_leaf_columns"]
+    assert mc > 64, mc
+    X = torch.from_numpy(random_coefficients(g.n, 40, seed=58)).cuda()
+    for parts in (nesa.PART_ALL, nesa.PART_FAR):
+        p = parts | nesa.PART_MIXED
+        Y = g.matvec(X, parts=p).cpu().numpy()
+        assert nesa.lib().nesa_device_status(g._h) == nesa.OK
+        for r in (0, 33, 39):
+            y1 = g.matvec(X[r:r + 1].contiguous(), parts=p).cpu().numpy()[0]
+            assert rel(Y[r], y1) < TOL_TC, (parts, r, rel(Y[r], y1))
+    o = NesaOracle(c["vertices"], c["triangles"], c["k"], c["leaf_size"], 3)
+    rows = np.unique(np.linspace(0, g.n - 1, 12).astype(np.int64))
+    Y = g.matvec(X, parts=nesa.PART_ALL | nesa.PART_MIXED).cpu().numpy()
+    xh = X.cpu().numpy()
+    e = rel(Y[39, rows], o.matvec_rows(xh[39], rows))
+    print("C1b at 3 levels (max %d V columns per leaf), 40 RHS: rel err vs oracle (12 rows) %.2e" % (mc, e))
+    assert e < TOL_TC
