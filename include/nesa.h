@@ -373,7 +373,10 @@ int nesa_matvec_noalloc(nesa_ctx *ctx, const nesa_c128 *x_dev, nesa_c128 *y_dev,
  * nesa_batch_create runs every product once eagerly (allocations, tile tuning), then
  * captures the kernels; it is synchronous.  A member context must not be destroyed or
  * rebuilt while the batch exists, and the batch must not run concurrently with other
- * work on its members.  nesa_batch_launch is asynchronous on `stream`.
+ * work on its members.  While the batch exists, every product, solve or training call on
+ * a member must use the member's nrhs (the graph holds the work buffers sized for it):
+ * other counts fail with NESA_ERR_INVALID_ARG, and so does a context listed twice.
+ * nesa_batch_launch is asynchronous on `stream`.
  */
 typedef struct nesa_batch nesa_batch;
 int nesa_batch_create(nesa_ctx *const *ctxs, int n, const nesa_c128 *const *x_dev, nesa_c128 *const *y_dev,

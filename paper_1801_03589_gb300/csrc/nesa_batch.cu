@@ -41,6 +41,17 @@ int nesa_batch_create(nesa_ctx *const *ctxs, int n, const nesa_c128 *const *x, n
     return NESA_ERR_INVALID_ARG;
   for (int i = 0; i < n; ++i)
     if (!ctxs[i] || !x[i] || !y[i] || nrhs[i] < 1 || nrhs[i] > 64) return NESA_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i) {
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) {  // the branches of one context would share its work buffers
+        set_last_error("nesa_batch_create: a context appears twice in the batch");
+        return NESA_ERR_INVALID_ARG;
+      }
+    if (ctxs[i]->batch_refs > 0 && ctxs[i]->batch_nrhs != nrhs[i]) {
+      set_last_error("nesa_batch_create: a member is in another batch with a different number of right-hand sides");
+      return NESA_ERR_INVALID_ARG;
+    }
+  }
   nesa_batch *b = new nesa_batch();
   b->ctx.assign(ctxs, ctxs + n);
   cudaStream_t s0 = nullptr;
@@ -111,6 +122,10 @@ int nesa_batch_create(nesa_ctx *const *ctxs, int n, const nesa_c128 *const *x, n
     batch_free(b);
     return e.status;
   }
+  for (int i = 0; i < n; ++i) {
+    ctxs[i]->batch_refs += 1;
+    ctxs[i]->batch_nrhs = nrhs[i];
+  }
   *out = b;
   return NESA_OK;
 }
@@ -131,7 +146,12 @@ int nesa_batch_kernels(const nesa_batch *b, int64_t *kernel_nodes) {
   return NESA_OK;
 }
 
-void nesa_batch_destroy(nesa_batch *b) { batch_free(b); }
+void nesa_batch_destroy(nesa_batch *b) {
+  if (!b) return;
+  if (b->exec)  // a batch that was created: its members are free to reallocate again
+    for (nesa_ctx *c : b->ctx) c->batch_refs -= 1;
+  batch_free(b);
+}
 
 int nesa_get_tuning(nesa_ctx *c, int32_t *tile_n, float *ms) {
   if (!c || !tile_n || !ms) return NESA_ERR_INVALID_ARG;

@@ -108,6 +108,9 @@ struct nesa_ctx {
   // levels
   nesa::DevLevel lev[NESA_MAX_LEVELS];
   int nrhs_cap = 0;              // capacity of the s/o workspaces
+  // batches holding this context in their graphs, and the right-hand sides they were
+  // captured with: while one exists, no product may reallocate what the graph uses
+  int batch_refs = 0, batch_nrhs = 0;
   int max_leaf_cols = 0;         // largest number of V columns of one leaf
   // host-pointer product buffers
   nesa::cplx *d_hx = nullptr, *d_hy = nullptr;

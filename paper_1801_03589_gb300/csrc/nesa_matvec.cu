@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <string>
 #include <thread>
 #include <type_traits>
 #include <utility>
@@ -34,8 +35,17 @@ void dfree(nesa_ctx *c, void *p) {
   cudaFree(p);
 }
 
+// A context captured in a batch keeps its work buffers: products on it use the batch's
+// number of right-hand sides until the batch is destroyed.
+static void check_batch(const nesa_ctx *c, int nrhs) {
+  if (c->batch_refs > 0 && nrhs != c->batch_nrhs)
+    fail(NESA_ERR_INVALID_ARG, "context is a member of a batch captured with " + std::to_string(c->batch_nrhs) +
+                                   " right-hand sides; destroy the batch before using " + std::to_string(nrhs));
+}
+
 int ensure_workspace(nesa_ctx *c, int nrhs) {
   if (nrhs > c->nrhs_cap) {
+    check_batch(c, nrhs);
     for (int l = c->l0; l <= c->L; ++l) {
       DevLevel &d = c->lev[l];
       dfree(c, d.s);
@@ -712,6 +722,7 @@ static void run_product(nesa_ctx *c, const OpView<CT> &op, const cplx *x, cplx *
 
 // Launch the product on the context's stream.
 void launch_matvec(nesa_ctx *c, const cplx *x, cplx *y, int nrhs, int parts) {
+  check_batch(c, nrhs);
   if (parts & NESA_PART_MIXED) {
     if (!c->mixed) fail(NESA_ERR_INVALID_ARG, "context was not built with NESA_MIXED");
     ensure_workspace32(c, nrhs);

@@ -11,6 +11,14 @@
 //   k_pair_reduce  o_a = P[nil + a] + sum over the pairs of a of P[pair]
 // The reduction runs over each target's own blocks in a fixed order (owner computes),
 // so the product is deterministic.
+//
+// With many right-hand sides (nrhs >= SEG_MIN_RHS) the same GEMMs run target-grouped
+// instead: a work item is (target box, 32 right-hand sides, M tile) and its K loop runs
+// over the target's whole list (interaction list, parent, or children), one segment per
+// entry, into one TMEM accumulator, in list order.  The result goes straight to o_l (or
+// s_P), with no per-pair blocks and no reduction; the A tiles and source blocks read per
+// item are the same as in the offset-grouped form, whose column tiles then hold about
+// two right-hand-side groups of each pair.
 #include <algorithm>
 #include <vector>
 
@@ -33,7 +41,19 @@ struct TcGemm {
   int32_t *wsrc = nullptr, *wdst = nullptr;
   int64_t nwork = 0;
   int work_tn = 0, work_rc = 0;
+  // target-grouped form: per target its entries (slot, source box) in list order
+  std::vector<int32_t> t_ptr, t_slot, t_src;
+  int64_t ntarget = 0, nsource = 0;
+  bool any_empty = false;          // some target has no entry (its output is not written)
+  tc::Work *swork = nullptr;       // work list for swork_rc right-hand sides
+  int32_t *swdst = nullptr;
+  int2 *sseg = nullptr;
+  int64_t snwork = 0;
+  int swork_rc = 0;
 };
+
+constexpr int SEG_MIN_RHS = 32;  // products with at least this many right-hand sides
+constexpr int SEG_TN = 256;      // run target-grouped, 32 right-hand sides per column tile
 
 struct TcLevel {
   TcGemm tr, dn, up;  // translations (Eq. 12); potential transfer (Eq. 13) and source
@@ -43,6 +63,7 @@ struct TcLevel {
   __nv_bfloat16 *o_hi = nullptr, *o_lo = nullptr;  // [parent boxes][rc][dn.nkc][256]
   cplxf *P = nullptr;                              // [nil + nbox][4 rc][q]
   cplxf *P_up = nullptr;                           // [nbox][4 rc][q of the parent level]
+  bool has_P = false;                              // P and P_up exist (offset-grouped form)
   bool s_split = false;  // s_hi/s_lo hold the split of all right-hand sides of the current
                          // product (set by the source transfer, used by the translation)
 };
@@ -168,9 +189,30 @@ static void gemm_setup(nesa_ctx *c, TcGemm &g, const cplx *M, int64_t nslot, int
   }
 }
 
-template <int TN>
+// Target lists of a family for the target-grouped form: entry e (in ascending order)
+// belongs to target tgt[e] and reads A matrix slot[e] and source box src[e].
+static void seg_setup(TcGemm &g, int64_t ntarget, int64_t nsource, const std::vector<int32_t> &tgt,
+                      const std::vector<int32_t> &slot, const std::vector<int32_t> &src) {
+  g.ntarget = ntarget;
+  g.nsource = nsource;
+  g.t_ptr.assign(ntarget + 1, 0);
+  for (int32_t t : tgt) g.t_ptr[t + 1]++;
+  for (int64_t t = 0; t < ntarget; ++t) g.t_ptr[t + 1] += g.t_ptr[t];
+  g.t_slot.resize(tgt.size());
+  g.t_src.resize(tgt.size());
+  std::vector<int32_t> fill(g.t_ptr.begin(), g.t_ptr.end() - 1);
+  for (size_t e = 0; e < tgt.size(); ++e) {
+    const int32_t at = fill[tgt[e]]++;
+    g.t_slot[at] = slot[e];
+    g.t_src[at] = src[e];
+  }
+  g.any_empty = false;
+  for (int64_t t = 0; t < ntarget; ++t) g.any_empty |= g.t_ptr[t + 1] == g.t_ptr[t];
+}
+
+template <int TN, bool SEG>
 static void set_smem() {
-  check_cuda(cudaFuncSetAttribute(tc::k_tc_gemm<TN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  check_cuda(cudaFuncSetAttribute(tc::k_tc_gemm<TN, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   tc::smem_bytes<TN>()),
              "smem attribute");
 }
@@ -178,9 +220,10 @@ static void set_smem() {
 void tc_build(nesa_ctx *c) {
   TcState *S = new TcState();
   c->tc_state = S;
-  set_smem<64>();
-  set_smem<128>();
-  set_smem<256>();
+  set_smem<64, false>();
+  set_smem<128, false>();
+  set_smem<256, false>();
+  set_smem<SEG_TN, true>();
   int dev = 0;
   check_cuda(cudaGetDevice(&dev), "device");
   check_cuda(cudaDeviceGetAttribute(&S->nsm, cudaDevAttrMultiProcessorCount, dev), "SM count");
@@ -194,6 +237,10 @@ void tc_build(nesa_ctx *c) {
     std::vector<int32_t> dst(hl.il_slot.size());
     for (size_t e = 0; e < dst.size(); ++e) dst[e] = (int32_t)e;
     gemm_setup(c, t.tr, d.D, d.noff, d.q, d.q, hl.il_slot, dst, hl.il_src);
+    std::vector<int32_t> il_tgt(hl.il_slot.size());  // pair e belongs to target box a
+    for (int64_t a = 0; a < d.nbox; ++a)
+      for (int32_t e = hl.il_ptr[a]; e < hl.il_ptr[a + 1]; ++e) il_tgt[e] = (int32_t)a;
+    seg_setup(t.tr, d.nbox, d.nbox, il_tgt, hl.il_slot, hl.il_src);
     if (l > c->l0) {  // potential transfer: entry = box a, slot = octant, source = parent
       std::vector<int32_t> bd(d.nbox), id(d.nbox);
       for (int64_t a = 0; a < d.nbox; ++a) {
@@ -201,8 +248,10 @@ void tc_build(nesa_ctx *c) {
         id[a] = (int32_t)a;
       }
       gemm_setup(c, t.dn, d.Ct, 8, d.q, c->lev[l - 1].q, hl.octant, bd, hl.parent);
+      seg_setup(t.dn, d.nbox, c->lev[l - 1].nbox, id, hl.octant, hl.parent);
       // source transfer: entry = child box a, slot = octant, source = a, block a of P_up
       gemm_setup(c, t.up, d.C, 8, c->lev[l - 1].q, d.q, hl.octant, id, id);
+      seg_setup(t.up, c->lev[l - 1].nbox, d.nbox, hl.parent, hl.octant, id);
     }
   }
   if (c->fixed_tn)
@@ -278,6 +327,68 @@ static void launch_gemm(nesa_ctx *c, const TcGemm &g, const __nv_bfloat16 *B_hi,
   }
 }
 
+// Target-grouped work list for rc right-hand sides: per target with entries, per group
+// of SEG_TN/8 right-hand sides r0.., its segments (slot, source block src * rc + r0) and
+// one item per M tile; the output column of group j is target * 4 rc + 4 (r0 + j).
+static void make_seg_work(nesa_ctx *c, TcGemm &g, int rc) {
+  if (g.swork && g.swork_rc == rc) return;
+  dfree(c, g.swork);
+  dfree(c, g.swdst);
+  dfree(c, g.sseg);
+  g.swork = nullptr;
+  g.swdst = nullptr;
+  g.sseg = nullptr;
+  std::vector<tc::Work> w;
+  std::vector<int32_t> wd;
+  std::vector<int2> sg;
+  const int gt = SEG_TN / 8;
+  for (int64_t t = 0; t < g.ntarget; ++t) {
+    const int32_t e0 = g.t_ptr[t], e1 = g.t_ptr[t + 1];
+    if (e0 == e1) continue;
+    for (int r0 = 0; r0 < rc; r0 += gt) {
+      const int nvalid = std::min(gt, rc - r0);
+      const int32_t sb = (int32_t)sg.size();
+      for (int32_t e = e0; e < e1; ++e) {
+        if (g.t_slot[e] < 0 || g.t_slot[e] >= g.nslot || g.t_src[e] < 0 || g.t_src[e] >= g.nsource)
+          fail(NESA_ERR_INVALID_ARG, "target-grouped work list: entry out of range");
+        sg.push_back(make_int2(g.t_slot[e], g.t_src[e] * rc + r0));
+      }
+      const int32_t se = (int32_t)sg.size();
+      for (int mt = 0; mt < g.nmt; ++mt) {
+        w.push_back({sb, mt, nvalid, se});
+        for (int j = 0; j < gt; ++j) wd.push_back(j < nvalid ? (int32_t)(t * 4 * rc + 4 * (r0 + j)) : -1);
+      }
+    }
+  }
+  if ((int64_t)sg.size() >= INT32_MAX || g.ntarget * 4 * (int64_t)rc >= INT32_MAX ||
+      g.nsource * (int64_t)rc >= INT32_MAX)
+    fail(NESA_ERR_INVALID_ARG, "target-grouped work list: index range");
+  g.snwork = (int64_t)w.size();
+  g.swork = (tc::Work *)dalloc(c, sizeof(tc::Work) * std::max<size_t>(1, w.size()));
+  g.swdst = (int32_t *)dalloc(c, sizeof(int32_t) * std::max<size_t>(1, wd.size()));
+  g.sseg = (int2 *)dalloc(c, sizeof(int2) * std::max<size_t>(1, sg.size()));
+  if (!w.empty()) {
+    check_cuda(cudaMemcpy(g.swork, w.data(), sizeof(tc::Work) * w.size(), cudaMemcpyHostToDevice), "work");
+    check_cuda(cudaMemcpy(g.swdst, wd.data(), sizeof(int32_t) * wd.size(), cudaMemcpyHostToDevice), "work");
+    check_cuda(cudaMemcpy(g.sseg, sg.data(), sizeof(int2) * sg.size(), cudaMemcpyHostToDevice), "work");
+  }
+  g.swork_rc = rc;
+}
+
+// out[target][4 rc][q] (+)= sum over the target's entries of A(slot) B(source).
+static void launch_gemm_seg(nesa_ctx *c, const TcGemm &g, const __nv_bfloat16 *B_hi, const __nv_bfloat16 *B_lo,
+                            cplxf *out, bool accum) {
+  TcState *S = state(c);
+  if (g.snwork == 0) return;
+  // about 32 K steps of 16 per TMEM accumulation, as many as the largest translation
+  // matrix of the offset-grouped form; the chunks are added in FP32 by the epilogue
+  const int chunk = std::max(1, 32 / g.nk16);
+  tc::GemmArgs a{g.swork, nullptr, g.swdst, g.snwork, g.A, B_hi, B_lo, out, g.q, g.nk16, g.nmt, S->err,
+                 g.sseg, accum ? 1 : 0, chunk};
+  const unsigned grid = (unsigned)std::min<int64_t>(g.snwork, S->nsm);
+  tc::k_tc_gemm<SEG_TN, true><<<grid, tc::THREADS, tc::smem_bytes<SEG_TN>(), c->stream>>>(a);
+}
+
 // Autotuner of the column-tile width: every candidate runs three times on the current
 // operands (timed with CUDA events on the context's stream), the fastest is kept for
 // this GEMM family and chunk size.  Synchronous: it runs at the first mixed product
@@ -312,8 +423,8 @@ static void autotune(nesa_ctx *c, TcGemm &g, const __nv_bfloat16 *B_hi, const __
   g.tuned_rc = rc;
 }
 
-static void prepare_rc(nesa_ctx *c, TcLevel &t, int l, int rc) {
-  if (t.rc == rc) return;
+static void prepare_rc(nesa_ctx *c, TcLevel &t, int l, int rc, bool with_P = true) {
+  if (t.rc == rc && t.has_P == with_P) return;
   const DevLevel &d = c->lev[l];
   dfree(c, t.s_hi);
   dfree(c, t.s_lo);
@@ -331,10 +442,11 @@ static void prepare_rc(nesa_ctx *c, TcLevel &t, int l, int rc) {
     t.o_hi = (__nv_bfloat16 *)dalloc(c, sizeof(__nv_bfloat16) * (size_t)np * rc * t.dn.nkc * tc::GROUP_ELEMS);
     t.o_lo = (__nv_bfloat16 *)dalloc(c, sizeof(__nv_bfloat16) * (size_t)np * rc * t.dn.nkc * tc::GROUP_ELEMS);
     nblk += d.nbox;
-    t.P_up = (cplxf *)dalloc(c, sizeof(cplxf) * (size_t)d.nbox * 4 * rc * c->lev[l - 1].q);
+    if (with_P) t.P_up = (cplxf *)dalloc(c, sizeof(cplxf) * (size_t)d.nbox * 4 * rc * c->lev[l - 1].q);
   }
-  t.P = (cplxf *)dalloc(c, sizeof(cplxf) * (size_t)std::max<int64_t>(1, nblk) * 4 * rc * d.q);
+  t.P = with_P ? (cplxf *)dalloc(c, sizeof(cplxf) * (size_t)std::max<int64_t>(1, nblk) * 4 * rc * d.q) : nullptr;
   t.rc = rc;
+  t.has_P = with_P;
 }
 
 // Right-hand sides per chunk at level l: the largest divisor of nrhs for which the
@@ -358,6 +470,45 @@ void tc_translate_level(nesa_ctx *c, int l, const cplxf *s, cplxf *o, const cplx
   const DevLevel &d = c->lev[l];
   cudaStream_t st = c->stream;
   const bool down = op != nullptr && l > c->l0;
+  if (nrhs >= SEG_MIN_RHS) {  // target-grouped: o_l written by the GEMMs themselves
+    prepare_rc(c, t, l, nrhs, false);
+    if (!t.s_split)
+      k_split<<<grid_of(d.nbox * nrhs * t.tr.nkc * (int64_t)32), 256, 0, st>>>(t.s_hi, t.s_lo, s, d.nbox, nrhs, 0,
+                                                                                nrhs, d.q, t.tr.nkc);
+    if (down) {
+      const DevLevel &p = c->lev[l - 1];
+      k_split<<<grid_of(p.nbox * nrhs * t.dn.nkc * (int64_t)32), 256, 0, st>>>(t.o_hi, t.o_lo, op, p.nbox, nrhs, 0,
+                                                                                nrhs, p.q, t.dn.nkc);
+      make_seg_work(c, t.dn, nrhs);
+    }
+    make_seg_work(c, t.tr, nrhs);
+    const bool zero_first = !down && t.tr.any_empty;  // boxes without pairs still get o = 0
+    if (zero_first)
+      check_cuda(cudaMemsetAsync(o, 0, sizeof(cplxf) * (size_t)d.nbox * 4 * nrhs * d.q, st), "clear o");
+    cudaEvent_t ev0 = nullptr;
+    if (c->profiling) {
+      ev0 = take_event(c);
+      cudaEventRecord(ev0, st);
+    }
+    if (down) launch_gemm_seg(c, t.dn, t.o_hi, t.o_lo, o, false);  // o_a = C^T o_P(a)
+    launch_gemm_seg(c, t.tr, t.s_hi, t.s_lo, o, down || zero_first);  // o_a += sum_b D s_b
+    if (c->profiling) {
+      cudaEvent_t ev1 = take_event(c);
+      cudaEventRecord(ev1, st);
+      double fl = 32.0 * nrhs * (double)d.nil * d.q * d.q;
+      double by = 4.0 * (double)d.noff * t.tr.nmt * t.tr.nkc * tc::TILE_ELEMS +
+                  4.0 * (double)d.nil * nrhs * t.tr.nkc * tc::GROUP_ELEMS + 8.0 * (double)d.nbox * 4 * nrhs * d.q;
+      if (down) {
+        const int qp = c->lev[l - 1].q;
+        fl += 32.0 * nrhs * (double)d.nbox * d.q * qp;
+        by += 4.0 * 8 * t.dn.nmt * t.dn.nkc * tc::TILE_ELEMS + 4.0 * (double)d.nbox * nrhs * t.dn.nkc * tc::GROUP_ELEMS +
+              16.0 * (double)d.nbox * 4 * nrhs * d.q;
+      }
+      c->pending.push_back({4, ev0, ev1, fl, by});
+    }
+    t.s_split = false;
+    return;
+  }
   const int rc = level_rc(c, l, nrhs);  // right-hand sides go through in equal chunks
   prepare_rc(c, t, l, rc);
   for (int r0 = 0; r0 < nrhs; r0 += rc) {
@@ -409,6 +560,17 @@ void tc_upward_level(nesa_ctx *c, int l, const cplxf *s, cplxf *sp, int nrhs) {
   TcLevel &t = S->lev[l];
   const DevLevel &d = c->lev[l], &p = c->lev[l - 1];
   cudaStream_t st = c->stream;
+  if (nrhs >= SEG_MIN_RHS) {  // target-grouped: s_P written by the GEMM itself
+    prepare_rc(c, t, l, nrhs, false);
+    k_split<<<grid_of(d.nbox * nrhs * t.tr.nkc * (int64_t)32), 256, 0, st>>>(t.s_hi, t.s_lo, s, d.nbox, nrhs, 0,
+                                                                              nrhs, d.q, t.tr.nkc);
+    make_seg_work(c, t.up, nrhs);
+    if (t.up.any_empty)
+      check_cuda(cudaMemsetAsync(sp, 0, sizeof(cplxf) * (size_t)p.nbox * 4 * nrhs * p.q, st), "clear s");
+    launch_gemm_seg(c, t.up, t.s_hi, t.s_lo, sp, t.up.any_empty);
+    t.s_split = true;  // the translation of this level reuses the split
+    return;
+  }
   const int rc = level_rc(c, l, nrhs);
   prepare_rc(c, t, l, rc);
   for (int r0 = 0; r0 < nrhs; r0 += rc) {

@@ -51,3 +51,30 @@ def test_autotuner_picks_measured_minimum():
         ms = dict(zip((64, 128, 256), t["ms"]))
         assert t["tile_n"] in ms and ms[t["tile_n"]] == min(v for v in ms.values() if v > 0)
     print("chosen tile widths:", {l: t["tile_n"] for l, t in tun.items()})
+
+
+def test_batch_members_keep_their_right_hand_sides():
+    # the graph holds the members' work buffers: a product with another number of
+    # right-hand sides (which would reallocate them) is refused while the batch exists,
+    # and so is a context listed twice; after close() the member is free again
+    import paper_1801_03589_gb300 as nesa
+    parts = nesa.PART_ALL | nesa.PART_MIXED
+    g = _build("tiny", precision=nesa.MIXED, translate=nesa.TRANSLATE_TENSOR)
+    x = torch.from_numpy(random_coefficients(g.n, 2, seed=97)).cuda()
+    y = torch.zeros_like(x)
+    with pytest.raises(nesa.NesaError):
+        nesa.Batch([g, g], [x, x], [y, y], parts=parts)
+    b = nesa.Batch([g], [x], [y], parts=parts)
+    b.launch()
+    torch.cuda.synchronize()
+    same = g.matvec(x, parts=parts)  # the batch's count is fine
+    with pytest.raises(nesa.NesaError):
+        g.matvec(x[:1].contiguous(), parts=parts)
+    with pytest.raises(nesa.NesaError):
+        g.matvec(x[:1].contiguous())
+    b.launch()  # the graph still runs on intact buffers
+    torch.cuda.synchronize()
+    assert float((y - same).abs().max() / same.abs().max()) <= 1e-13
+    b.close()
+    y1 = g.matvec(x[:1].contiguous(), parts=parts)
+    assert float((y1[0] - same[0]).abs().max() / same[0].abs().max()) < 1e-5

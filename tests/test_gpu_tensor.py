@@ -122,3 +122,24 @@ def test_many_rhs_reception_large_leaves():
     e = rel(Y[39, rows], o.matvec_rows(xh[39], rows))
     print("C1b at 3 levels (max %d V columns per leaf), 40 RHS: rel err vs oracle (12 rows) %.2e" % (mc, e))
     assert e < TOL_TC
+
+
+@pytest.mark.parametrize("name", ["C1b", "C3a"])
+def test_target_grouped_gemm_vs_fp64(name):
+    # 64 right-hand sides run the transfers and translations target-grouped (a work item
+    # per target box and 32 right-hand sides, its list summed in TMEM in chunks of about
+    # 32 K steps that the epilogue adds in FP32): every column against the FP64 product.
+    # The far part alone stays within 2^-16, the error of one BF16 hi/lo product; one
+    # accumulation over a whole interaction list (thousands of MMAs) measured 2.7e-5
+    # there, the chunked form 5e-6, the offset-grouped form 4e-6.
+    import paper_1801_03589_gb300 as nesa
+    c, g = build(name)
+    X = torch.from_numpy(random_coefficients(g.n, 64, seed=59)).cuda()
+    for parts in (nesa.PART_ALL, nesa.PART_FAR):
+        Y = g.matvec(X, parts=parts | nesa.PART_MIXED).cpu().numpy()
+        Y64 = g.matvec(X, parts=parts).cpu().numpy()
+        assert nesa.lib().nesa_device_status(g._h) == nesa.OK
+        errs = [rel(Y[r], Y64[r]) for r in range(64)]
+        print("%s target-grouped tensor product, 64 RHS, parts %d: max rel err vs FP64 %.2e"
+              % (name, parts, max(errs)))
+        assert max(errs) < (TOL_TC if parts == nesa.PART_ALL else 2.0 ** -16)
