@@ -445,15 +445,17 @@ __global__ void __launch_bounds__(256) k_near_receive_v(cplx *__restrict__ y, co
 // for the leaf's V columns g (an RWG function has one column per leaf that holds one of
 // its triangles; k_near_wide adds its columns up).  V and o go through shared memory in
 // chunks of RC_KC of the 4Q values: V as [column][k] (every lane of a warp reads the
-// same value), o transposed to [k][right-hand side] (consecutive lanes, consecutive
-// values).  Thread (warp w, lane) owns right-hand side r0 + lane and the columns
-// w, w + 8, ... of a block of RC_COLS; FP32 sums in the order k = 0 .. 4Q-1.
-constexpr int RC_KC = 32, RC_COLS = 64;
+// same two values with one 16-byte load), o as [right-hand side][k] with rows padded to
+// RC_KC + 2 values (lane r reads its two values with one 16-byte load, eight lanes per
+// bank cycle).  Thread (warp w, lane) owns right-hand side r0 + lane and the columns
+// w, w + 8, ... of a block of RC_COLS (only those the leaf has); FP32 sums in the order
+// k = 0 .. 4Q-1.
+constexpr int RC_KC = 32, RC_COLS = 64, RC_OPAD = RC_KC + 2;
 __global__ void __launch_bounds__(256) k_receive_leaf(cplxf *__restrict__ R, const cplxf *__restrict__ V,
                                                       const cplxf *__restrict__ oL, const int32_t *__restrict__ vc_ptr,
                                                       int nrhs, int q, float mk2) {
   __shared__ __align__(16) cplxf Vs[RC_COLS][RC_KC];
-  __shared__ __align__(16) cplxf Os[RC_KC][33];
+  __shared__ __align__(16) cplxf Os[32][RC_OPAD];
   const int64_t b = blockIdx.x;
   const int r0 = blockIdx.y * 32;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -462,6 +464,7 @@ __global__ void __launch_bounds__(256) k_receive_leaf(cplxf *__restrict__ R, con
   const cplxf *ob = oL + b * nrhs * (int64_t)q4;  // o_b[r][ch][i] at ob + r * 4Q + ch * Q + i
   for (int c0 = 0; c0 < ns; c0 += RC_COLS) {
     const int nc = min(RC_COLS, ns - c0);
+    const int jn = nc > warp ? (nc - warp + 7) / 8 : 0;  // this warp's columns in the block
     cplxf acc[RC_COLS / 8] = {};
     for (int k0 = 0; k0 < q4; k0 += RC_KC) {
       const int kn = min(RC_KC, q4 - k0);
@@ -478,20 +481,26 @@ __global__ void __launch_bounds__(256) k_receive_leaf(cplxf *__restrict__ R, con
       }
       for (int t = threadIdx.x; t < 32 * RC_KC; t += blockDim.x) {
         const int rr = t / RC_KC, kk = t % RC_KC;
-        Os[kk][rr] = r0 + rr < nrhs && kk < kn ? ob[(int64_t)(r0 + rr) * q4 + k0 + kk] : make_float2(0.0f, 0.0f);
+        Os[rr][kk] = r0 + rr < nrhs && kk < kn ? ob[(int64_t)(r0 + rr) * q4 + k0 + kk] : make_float2(0.0f, 0.0f);
       }
       __syncthreads();
-#pragma unroll 4
-      for (int kk = 0; kk < RC_KC; ++kk) {  // zeros past kn
-        const cplxf o = Os[kk][lane];
+#pragma unroll 2
+      for (int kk = 0; kk < RC_KC; kk += 2) {  // zeros past kn
+        const float4 o2 = *(const float4 *)&Os[lane][kk];
+        const cplxf oa = make_float2(o2.x, o2.y), obv = make_float2(o2.z, o2.w);
 #pragma unroll
-        for (int j = 0; j < RC_COLS / 8; ++j) cfma(acc[j], Vs[warp + 8 * j][kk], o);
+        for (int j = 0; j < RC_COLS / 8; ++j)
+          if (j < jn) {
+            const float4 v2 = *(const float4 *)&Vs[warp + 8 * j][kk];
+            cfma(acc[j], make_float2(v2.x, v2.y), oa);
+            cfma(acc[j], make_float2(v2.z, v2.w), obv);
+          }
       }
     }
     if (r0 + lane < nrhs)
 #pragma unroll
       for (int j = 0; j < RC_COLS / 8; ++j)
-        if (warp + 8 * j < nc) R[(int64_t)(g0 + c0 + warp + 8 * j) * nrhs + r0 + lane] = acc[j];
+        if (j < jn) R[(int64_t)(g0 + c0 + warp + 8 * j) * nrhs + r0 + lane] = acc[j];
   }
 }
 
