@@ -7,6 +7,9 @@
 //                                                              (Eq. 13 and Eq. 12, l = l0..L)
 //   k_near_receive y_m    = sum_n Z^near_mn x_n                (Eq. 9)
 //                         + (-i eta k) sum_ch gamma_ch V^T o   (Eq. 14; U = V^T)
+// The mixed product with 32 or more right-hand sides splits the last stage in two:
+// k_receive_leaf (Eq. 14 per leaf and V column, for 32 right-hand sides at a time) and
+// k_near_wide (Eq. 9, one lane per right-hand side, plus the row's reception values).
 // Every output element is owned by one thread or one warp (no atomics), so the
 // product is deterministic.  The kernels are templated on the complex type of the
 // operator: complex128 (the FP64 product, bound by the FP64 pipe: a complex
@@ -360,7 +363,7 @@ __global__ void __launch_bounds__(256) k_near_receive(cplx *__restrict__ y, cons
 // entries per lane and step (16- and 32-byte streaming loads) and gathers x from its
 // internal-order complex64 copy xp; reception reads each V column and the leaf's
 // outgoing field as contiguous 4Q-value blocks, two values per lane and load.
-template <int RB, bool ACC>
+template <int RB>
 __global__ void __launch_bounds__(256) k_near_receive_v(cplx *__restrict__ y, const cplxf *__restrict__ xp, int64_t n,
                                                         int nrhs, const int32_t *__restrict__ perm,
                                                         const int64_t *__restrict__ nz_ptr,
@@ -426,15 +429,7 @@ __global__ void __launch_bounds__(256) k_near_receive_v(cplx *__restrict__ y, co
         v.x += __shfl_down_sync(0xffffffffu, v.x, off);
         v.y += __shfl_down_sync(0xffffffffu, v.y, off);
       }
-      if (lane == 0 && rr < rb) {
-        cplx &out = y[(int64_t)(r0 + rr) * n + m];
-        if (ACC) {  // add to the near field written by k_near_wide
-          out.x += v.x;
-          out.y += v.y;
-        } else {
-          out = v;
-        }
-      }
+      if (lane == 0 && rr < rb) y[(int64_t)(r0 + rr) * n + m] = v;
     }
   }
 }
@@ -716,7 +711,7 @@ static void run_product(nesa_ctx *c, const OpView<CT> &op, const cplx *x, cplx *
           c->d_rcv, c->eta * c->k, parts);
     } else {
       if (parts & NESA_PART_NEAR) k_perm_x<<<pgrid, 256, 0, st>>>(c->d_xp, x, c->d_perm, c->n, nrhs);
-      auto near = nrhs == 1 ? k_near_receive_v<1, false> : k_near_receive_v<4, false>;
+      auto near = nrhs == 1 ? k_near_receive_v<1> : k_near_receive_v<4>;
       near<<<grid_for(c->n * 32, 256), 256, 0, st>>>(y, c->d_xp, c->n, nrhs, c->d_perm, c->d_nz_ptr4, c->d_nz_col4,
                                                     op.nz_val, c->d_rx_ptr, c->d_rx_col, c->d_vc_leaf, op.V, op.o[L],
                                                     dL.q, c->eta * c->k, 1.0 / (c->k * c->k), parts);
