@@ -452,9 +452,9 @@ def run_ours(args, world, rank, local):
     gemm = prof_mx["translation_tensor_gemm"]
     rest = {"ms": max(0.0, prof_mx["translation"]["ms"] - gemm["ms"]), "flops": 0.0,
             "bytes": max(0.0, prof_mx["translation"]["bytes"] - gemm["bytes"])}
-    kernels = {"k_tc_gemm": (gemm, "tensor"), "k_near_receive<float2>": (prof_mx["near_reception"], "hbm"),
-               "k_upward<float2>": (prof_mx["source_transfer"], "alu"),
-               "k_radiate<float2>": (prof_mx["radiation"], "hbm"),
+    kernels = {"k_tc_gemm": (gemm, "tensor"), "k_perm_x + k_near_receive_v": (prof_mx["near_reception"], "hbm"),
+               "k_split + k_tc_gemm + k_pair_reduce (source transfer)": (prof_mx["source_transfer"], "tensor"),
+               "k_radiate2": (prof_mx["radiation"], "hbm"),
                "k_split + k_pair_reduce": (rest, "hbm")}
     kernel = max(kernels, key=lambda k: kernels[k][0]["ms"])
     d, bound = kernels[kernel]
