@@ -47,7 +47,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # DRAM traffic of the translation / potential-transfer GEMM launches of one product of
 # the r = 3 sphere (ncu, dram__bytes_read.sum + dram__bytes_write.sum); null elsewhere
-GEMM_DRAM_BYTES_C2 = 1.5082e9
+GEMM_DRAM_BYTES_C2 = 1.5083e9
 SPEC = ("PEC sphere r=3 wavelengths, icosphere subdiv 6 (81,920 triangles, 122,880 RWG), "
         "6-level octree, leaf 0.25 wavelength, 1 RHS")
 
