@@ -316,6 +316,22 @@ int nesa_precond_loss_grad(nesa_ctx *ctx, const nesa_c128 *u_dev, const nesa_c12
 int nesa_export(const nesa_ctx *ctx, int which, void *host_buf, size_t bytes);
 
 /*
+ * Export one operator block (host copy of the FP64 operator, complex128 column-major):
+ *   NESA_OP_D       D_l(o) of Eq. 12 for level l (l0 <= l <= L) and offset slot index
+ *                   (0 .. n_offsets[l]-1): Q_l x Q_l, entry (i, j) = G(|E_i + o w_l - E_j|)
+ *   NESA_OP_C       C_l(octant) of Eq. 11 for level l (l0 < l <= L), index = octant bits
+ *                   x | y << 1 | z << 2 of the child: Q_{l-1} x Q_l
+ *   NESA_OP_OFFSET  the offset o of slot index at level l: int32[3] (target - source, in
+ *                   boxes of level l)
+ * bytes must equal the block size (NESA_ERR_INVALID_ARG otherwise, and for an index
+ * out of range).  Synchronous.
+ */
+#define NESA_OP_D 1
+#define NESA_OP_C 2
+#define NESA_OP_OFFSET 3
+int nesa_export_op(const nesa_ctx *ctx, int which, int level, int index, void *host_buf, size_t bytes);
+
+/*
  * Per-stage device timing of the product (for benchmarks).  When enabled, every kernel
  * launch of nesa_matvec* is bracketed by CUDA events on the context's stream.
  * nesa_profile_read synchronises the stream, adds the elapsed times of all launches

@@ -21,6 +21,7 @@ Q_FIXED, Q_AUTO = 0, 1
 PART_NEAR, PART_FAR, PART_ALL, PART_MIXED = 1, 2, 3, 4
 TRANSLATE_FP32, TRANSLATE_TENSOR = 0, 1
 EXPORT_POINT_LEAF, EXPORT_RWG = 1, 2
+OP_D, OP_C, OP_OFFSET = 1, 2, 3
 MAX_LEVELS = 20
 
 
@@ -116,6 +117,7 @@ def lib():
             "nesa_matvec_host": (I, [P, P, P, I, I]),
             "nesa_rhs_planewave": (I, [P, P, P, I, P]),
             "nesa_export": (I, [P, I, P, ctypes.c_size_t]),
+            "nesa_export_op": (I, [P, I, I, I, P, ctypes.c_size_t]),
             "nesa_destroy": (None, [P]),
             "nesa_status_str": (ctypes.c_char_p, [I]),
             "nesa_last_error": (ctypes.c_char_p, []),
@@ -382,4 +384,24 @@ class Nesa:
     def export_rwg(self):
         a = np.empty((self.n, 4), np.int32)
         _check(lib().nesa_export(self._h, EXPORT_RWG, a.ctypes.data, a.nbytes))
+        return a
+
+    def export_offset(self, level, slot):
+        """Offset (target - source, in boxes) of translation slot `slot` at `level`."""
+        a = np.empty(3, np.int32)
+        _check(lib().nesa_export_op(self._h, OP_OFFSET, level, slot, a.ctypes.data, a.nbytes))
+        return a
+
+    def export_D(self, level, slot):
+        """D_l of translation slot `slot` (complex128, Q_l x Q_l)."""
+        q = self.info()["q"][level]
+        a = np.empty((q, q), np.complex128, order="F")
+        _check(lib().nesa_export_op(self._h, OP_D, level, slot, a.ctypes.data, a.nbytes))
+        return a
+
+    def export_C(self, level, octant):
+        """C_l of the child octant (bits x | y << 1 | z << 2; complex128, Q_{l-1} x Q_l)."""
+        q = self.info()["q"]
+        a = np.empty((q[level - 1], q[level]), np.complex128, order="F")
+        _check(lib().nesa_export_op(self._h, OP_C, level, octant, a.ctypes.data, a.nbytes))
         return a

@@ -827,4 +827,33 @@ int nesa_export(const nesa_ctx *c, int which, void *buf, size_t bytes) {
   return NESA_ERR_INVALID_ARG;
 }
 
+int nesa_export_op(const nesa_ctx *c, int which, int level, int index, void *buf, size_t bytes) {
+  if (!c || !buf || index < 0) return NESA_ERR_INVALID_ARG;
+  if (level < c->l0 || level > c->L) return NESA_ERR_INVALID_ARG;
+  const DevLevel &d = c->lev[level];
+  const cplx *src = nullptr;
+  size_t need = 0;
+  if (which == NESA_OP_D || which == NESA_OP_OFFSET) {
+    if (index >= d.noff) return NESA_ERR_INVALID_ARG;
+    if (which == NESA_OP_OFFSET) {
+      if (bytes != 3 * sizeof(int32_t)) return NESA_ERR_INVALID_ARG;
+      std::memcpy(buf, c->h.lev[level].offsets.data() + 3 * (size_t)index, bytes);
+      return NESA_OK;
+    }
+    src = d.D + (int64_t)index * d.q * d.q;
+    need = sizeof(cplx) * (size_t)d.q * d.q;
+  } else if (which == NESA_OP_C) {
+    if (level == c->l0 || index >= 8) return NESA_ERR_INVALID_ARG;
+    const int qp = c->lev[level - 1].q;
+    src = d.C + (int64_t)index * qp * d.q;
+    need = sizeof(cplx) * (size_t)qp * d.q;
+  } else {
+    return NESA_ERR_INVALID_ARG;
+  }
+  if (bytes != need) return NESA_ERR_INVALID_ARG;
+  if (need == 0) return NESA_OK;
+  if (cudaMemcpy(buf, src, need, cudaMemcpyDeviceToHost) != cudaSuccess) return NESA_ERR_CUDA;
+  return NESA_OK;
+}
+
 }  // extern "C"
