@@ -373,7 +373,7 @@ def run_ours(args, world, rank, local):
             solve["fp64_none"] = one()
 
     # learned preconditioner on the aircraft-like body: trained on the GMRES vectors of
-    # two plane waves, judged by iterations and true residual on six held-out ones
+    # two plane waves, measured by iterations and true residual on six held-out ones
     learned = None
     if not args.no_learned:
         cf = get_config("C4")
