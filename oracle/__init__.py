@@ -14,6 +14,8 @@ Modules (each function cites the part of the paper it follows):
 * :mod:`oracle.rhs`         plane-wave excitation vector (Eq. 2, Eq. 3)
 * :mod:`oracle.gmres`       restarted GMRES (Sec. 2, solver named there)
 * :mod:`oracle.mie`         Mie series and far-field RCS of a PEC sphere (not in the paper)
+* :mod:`oracle.nesa2d`      the 2D model problem of Sec. 3: log-kernel potential, quadtree
+                            and its NESA product (Eqs. 8-14)
 
 Pins (what each function is checked against) are the ``-m "not gpu"`` tests in
 ``tests/test_oracle_*.py``.  Parity unpinned: the absolute NESA accuracy at a given
