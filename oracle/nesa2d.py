@@ -149,7 +149,7 @@ def circle(n, radius, shift):
 class Nesa2D:
     """The NESA product of the 2D model problem, one group pair at a time."""
 
-    def __init__(self, x, P, Q, rho_eq=1.0, rho_test=RHO_TEST_2D, pinv_eps=1e-12):
+    def __init__(self, x, P, Q, rho_eq=1.0, rho_test=RHO_TEST_2D, pinv_eps=1e-9):
         self.x = np.asarray(x, np.float64)
         self.n = len(self.x)
         self.Q = int(Q)

@@ -138,6 +138,11 @@ def lib():
             "nesa_batch_kernels": (I, [P, P]),
             "nesa_batch_destroy": (None, [P]),
             "nesa_get_tuning": (I, [P, P, P]),
+            "nesa2d_build": (I, [P, I64, I, I, D, P]),
+            "nesa2d_set_stream": (I, [P, P]),
+            "nesa2d_get_info": (I, [P, P]),
+            "nesa2d_matvec": (I, [P, P, P, I, I]),
+            "nesa2d_destroy": (None, [P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -179,6 +184,68 @@ def _dev_ptr(t, n, what):
     if t.shape[-1] != n:
         raise ValueError("%s has %d columns, expected %d" % (what, t.shape[-1], n))
     return t, t.data_ptr(), t.shape[0]
+
+
+MAX_LEVELS_2D = 32
+PART2D_NEAR, PART2D_FAR, PART2D_ALL = 1, 2, 3
+
+
+class Info2D(ctypes.Structure):
+    _fields_ = [("n_points", ctypes.c_int64), ("l0", ctypes.c_int32), ("L", ctypes.c_int32),
+                ("q", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("n_boxes", ctypes.c_int64 * MAX_LEVELS_2D), ("n_interactions", ctypes.c_int64 * MAX_LEVELS_2D),
+                ("n_offsets", ctypes.c_int64 * MAX_LEVELS_2D), ("near_entries", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64)]
+
+
+class Model2D:
+    """The 2D model problem of Sec. 3 (log-kernel potential of charges on a curve):
+    one built operator on the current CUDA device (owns its device memory)."""
+
+    def __init__(self, points, P, Q, pinv_eps=0.0):
+        x = np.ascontiguousarray(points, dtype=np.float64)
+        if x.ndim != 2 or x.shape[1] != 2:
+            raise ValueError("points must be [n][2]")
+        self.n = x.shape[0]
+        h = ctypes.c_void_p()
+        _check(lib().nesa2d_build(x.ctypes.data, self.n, int(P), int(Q), float(pinv_eps), ctypes.byref(h)))
+        self._h = h
+
+    def info(self):
+        i = Info2D()
+        _check(lib().nesa2d_get_info(self._h, ctypes.byref(i)))
+        levels = range(i.l0, i.L + 1)
+        return dict(n_points=i.n_points, l0=i.l0, L=i.L, q=i.q, n_boxes={l: i.n_boxes[l] for l in levels},
+                    n_interactions={l: i.n_interactions[l] for l in levels},
+                    n_offsets={l: i.n_offsets[l] for l in levels}, near_entries=i.near_entries,
+                    device_bytes=i.device_bytes)
+
+    def set_stream(self, stream):
+        _check(lib().nesa2d_set_stream(self._h, ctypes.c_void_p(getattr(stream, "cuda_stream", stream))))
+
+    def matvec(self, q, phi=None, parts=PART2D_ALL):
+        """phi = K~ q for q a float64 CUDA tensor [n] or [nrhs][n] (rows are vectors)."""
+        import torch
+        if not isinstance(q, torch.Tensor) or not q.is_cuda or q.dtype != torch.float64 or not q.is_contiguous():
+            raise TypeError("q must be a contiguous float64 CUDA tensor")
+        if q.shape[-1] != self.n:
+            raise ValueError("q has %d columns, expected %d" % (q.shape[-1], self.n))
+        nrhs = 1 if q.dim() == 1 else q.shape[0]
+        if phi is None:
+            phi = torch.empty_like(q)
+        _check(lib().nesa2d_matvec(self._h, q.data_ptr(), phi.data_ptr(), nrhs, int(parts)))
+        return phi
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().nesa2d_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
 
 
 class Batch:

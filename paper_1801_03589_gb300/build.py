@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnesa.so")
-SOURCES = ["nesa_host.cpp", "nesa_build.cu", "nesa_matvec.cu", "nesa_solve.cu", "nesa_noalloc.cu", "nesa_tc.cu", "nesa_precond.cu", "nesa_batch.cu"]
+SOURCES = ["nesa_host.cpp", "nesa_build.cu", "nesa_matvec.cu", "nesa_solve.cu", "nesa_noalloc.cu", "nesa_tc.cu", "nesa_precond.cu", "nesa_batch.cu", "nesa2d.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 
@@ -26,7 +26,7 @@ def _compile(src):
     obj = os.path.join(OUT, src + ".o")
     path = os.path.join(CSRC, src)
     deps = [path] + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
-    deps.append(os.path.join(HERE, "..", "include", "nesa.h"))
+    deps += [os.path.join(HERE, "..", "include", h) for h in ("nesa.h", "nesa2d.h")]
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(d) for d in deps):
         return obj
     cmd = [NVCC] + _flags() + ["-c", path, "-o", obj]
