@@ -294,6 +294,49 @@ def _time_products(g, x, y, parts, steps, warmup, stream, barrier):
     return ev0.elapsed_time(ev1) / steps, prof
 
 
+# the paper's CPU timings of the complete 2D product at N = 100,000 (Sec. 5, Tables 3
+# and 7): context for the 2D block, other hardware
+MODEL2D_PAPER_MS = {(300, 100): {"1 core (Table 3)": 1192.0, "64 cores (Table 7)": 127.0},
+                    (50, 10): {"1 core (Table 3)": 244.0, "16 cores (Table 3)": 156.0}}
+
+
+def run_model2d(args, stream, world, barrier, max_over_ranks):
+    """FP64 NESA products of the 2D model problem (Sec. 3) at the paper's size."""
+    import torch
+
+    import paper_1801_03589_gb300 as nesa
+    from workloads.curve2d import charges, curve_points
+    n = 100_000
+    x = curve_points(n, seed=1)
+    qd = torch.from_numpy(charges(n, seed=1)).cuda()
+    y = torch.empty_like(qd)
+    out = {"workload": "N = 100,000 charges on a seeded closed curve (the paper's curve is not available); "
+                       "phi = K q, K = -log|x_i - x_j|; FP64", "cases": []}
+    for P, Q in ((300, 100), (50, 10)):
+        t0 = time.perf_counter()
+        g = nesa.Model2D(x, P, Q)
+        build_s = time.perf_counter() - t0
+        g.set_stream(stream)
+        info = g.info()
+        for _ in range(max(3, args.warmup)):
+            g.matvec(qd, y)
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            g.matvec(qd, y)
+        e1.record(stream)
+        stream.synchronize()
+        ms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+        out["cases"].append({"P": P, "Q": Q, "levels": [info["l0"], info["L"]], "leaves": info["n_boxes"][info["L"]],
+                             "near_entries": info["near_entries"], "near_gb": 8e-9 * info["near_entries"],
+                             "ms_per_matvec": ms, "matvec_per_s": job_throughput(world, 1, ms),
+                             "build_s": build_s, "paper_cpu_ms": MODEL2D_PAPER_MS[(P, Q)]})
+        g.close()
+    return out
+
+
 def _stages(prof, steps):
     return {k: {"launches": v["launches"], "ms_per_step": v["ms"] / steps,
                 "tflops": (v["flops"] / (v["ms"] * 1e-3) / 1e12) if v["ms"] > 0 else None,
@@ -441,6 +484,15 @@ def run_ours(args, world, rank, local):
                  "tile_n": [{l: t["tile_n"] for l, t in m.tuning().items()} for m in members]}
         bt.close()
 
+    # the paper's 2D model problem at its size (a separate library path; a failure here
+    # is reported in the block and leaves the rest of the line intact)
+    model2d = None
+    if not args.no_model2d:
+        try:
+            model2d = run_model2d(args, stream, world, barrier, max_over_ranks)
+        except Exception as e:  # noqa: BLE001
+            model2d = {"error": "%s: %s" % (type(e).__name__, e)}
+
     if rank != 0:
         ranks.close()
         return 0
@@ -525,6 +577,7 @@ def run_ours(args, world, rank, local):
         "solve": solve,
         "learned": learned,
         "batch": batch,
+        "model2d": model2d,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line))
@@ -541,6 +594,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-model2d", action="store_true", help="skip the 2D model problem block")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner block (aircraft body)")
     ap.add_argument("--fp64-solve", action="store_true", help="also time the plain FP64 solve (about 2 minutes)")
     ap.add_argument("--workload", default=CONFIG, help="workload name (smaller ones are for profiling runs)")

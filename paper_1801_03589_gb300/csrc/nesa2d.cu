@@ -162,14 +162,18 @@ static std::vector<double> tikhonov_pinv(const std::vector<double> &A, int m, in
   return K;
 }
 
-// out (nq x cols, column-major) = K (nq x m) * G (m x cols)
+// out (nq x cols, column-major) = K (nq x m) * G (m x cols); each entry summed over t
+// in ascending order
 static void matmul(const std::vector<double> &K, int nq, int m, const double *G, int cols, double *out) {
-  for (int j = 0; j < cols; ++j)
-    for (int i = 0; i < nq; ++i) {
-      double acc = 0.0;
-      for (int t = 0; t < m; ++t) acc += K[(size_t)t * nq + i] * G[(size_t)j * m + t];
-      out[(size_t)j * nq + i] = acc;
+  for (int j = 0; j < cols; ++j) {
+    double *o = out + (size_t)j * nq;
+    for (int i = 0; i < nq; ++i) o[i] = 0.0;
+    for (int t = 0; t < m; ++t) {
+      const double gt = G[(size_t)j * m + t];
+      const double *kt = &K[(size_t)t * nq];
+      for (int i = 0; i < nq; ++i) o[i] += kt[i] * gt;
     }
+  }
 }
 
 static void parallel_for(int64_t n, const std::function<void(int64_t, int64_t)> &f) {
