@@ -579,7 +579,7 @@ static void matvec(nesa2d_ctx *c, const double *q, double *phi, int nrhs, int pa
   const int Q = c->Q, L = c->L, l0 = c->l0;
   const int tq = std::min(256, ((Q + 31) / 32) * 32);
   k2_perm_in<<<grid_of(c->n * nrhs), 256, 0, st>>>(c->d_qp, q, c->d_perm, c->n, nrhs);
-  k2_near<<<(unsigned)c->nleaf, 128, 0, st>>>(c->d_yp, c->d_qp, c->n, nrhs, c->d_leaf_ptr, c->d_nptr, c->d_nleaf,
+  k2_near<<<(unsigned)c->nleaf, 256, 0, st>>>(c->d_yp, c->d_qp, c->n, nrhs, c->d_leaf_ptr, c->d_nptr, c->d_nleaf,
                                               c->d_noff, c->d_Z, (parts & NESA2D_PART_NEAR) ? 1 : 0);
   if (parts & NESA2D_PART_FAR) {
     k2_radiate<<<(unsigned)c->nleaf, tq, 0, st>>>(c->lev[L].s, c->d_V, c->d_qp, c->n, nrhs, c->d_leaf_ptr, Q);
@@ -592,7 +592,7 @@ static void matvec(nesa2d_ctx *c, const double *q, double *phi, int nrhs, int pa
                                                      l > l0 ? c->lev[l - 1].o : nullptr, lv.C, lv.d_parent,
                                                      lv.d_quad, nrhs, Q);
     }
-    k2_receive<<<(unsigned)c->nleaf, 128, 0, st>>>(c->d_yp, c->lev[L].o, c->d_V, c->n, nrhs, c->d_leaf_ptr, Q);
+    k2_receive<<<(unsigned)c->nleaf, 256, 0, st>>>(c->d_yp, c->lev[L].o, c->d_V, c->n, nrhs, c->d_leaf_ptr, Q);
   }
   k2_perm_out<<<grid_of(c->n * nrhs), 256, 0, st>>>(phi, c->d_yp, c->d_perm, c->n, nrhs);
   check(cudaGetLastError(), "product launch");
