@@ -22,6 +22,7 @@
 #include <cstring>
 #include <functional>
 #include <map>
+#include <new>
 #include <string>
 #include <thread>
 #include <vector>
@@ -620,6 +621,10 @@ int nesa2d_build(const double *points, int64_t n, int P, int Q, double pinv_eps,
     nesa::set_last_error(e.what);
     free_ctx(c);
     return e.status;
+  } catch (const std::bad_alloc &) {
+    nesa::set_last_error("nesa2d_build: host allocation failed");
+    free_ctx(c);
+    return NESA_ERR_OOM;
   }
   *out = c;
   return NESA_OK;
@@ -657,6 +662,9 @@ int nesa2d_matvec(nesa2d_ctx *c, const double *q, double *phi, int nrhs, int par
   } catch (const Error &e) {
     nesa::set_last_error(e.what);
     return e.status;
+  } catch (const std::bad_alloc &) {
+    nesa::set_last_error("nesa2d_matvec: host allocation failed");
+    return NESA_ERR_OOM;
   }
   return NESA_OK;
 }
