@@ -21,6 +21,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <new>
 #include <string>
 #include <thread>
 #include <type_traits>
@@ -932,6 +933,9 @@ int nesa_matvec_parts(nesa_ctx *c, const nesa_c128 *x, nesa_c128 *y, int nrhs, i
   } catch (const Error &e) {
     set_last_error(e.what);
     return e.status;
+  } catch (const std::bad_alloc &) {
+    set_last_error("host allocation failed");
+    return NESA_ERR_OOM;
   }
   return NESA_OK;
 }
@@ -944,6 +948,9 @@ int nesa_device_status(nesa_ctx *c) {
   } catch (const Error &e) {
     set_last_error(e.what);
     return e.status;
+  } catch (const std::bad_alloc &) {
+    set_last_error("host allocation failed");
+    return NESA_ERR_OOM;
   }
   return NESA_OK;
 }
@@ -974,6 +981,9 @@ int nesa_matvec_host(nesa_ctx *c, const nesa_c128 *xh, nesa_c128 *yh, int nrhs, 
   } catch (const Error &e) {
     set_last_error(e.what);
     return e.status;
+  } catch (const std::bad_alloc &) {
+    set_last_error("host allocation failed");
+    return NESA_ERR_OOM;
   }
   return NESA_OK;
 }
@@ -1001,6 +1011,9 @@ int nesa_rhs_planewave(nesa_ctx *c, const double *khat, const nesa_c128 *pol, in
   } catch (const Error &e) {
     set_last_error(e.what);
     return e.status;
+  } catch (const std::bad_alloc &) {
+    set_last_error("host allocation failed");
+    return NESA_ERR_OOM;
   }
   return NESA_OK;
 }

@@ -20,6 +20,7 @@
 // in the array needs to start at zero: every kernel writes each work-vector element
 // it owns before any kernel reads it.
 #include <mutex>
+#include <new>
 #include <string>
 
 #include "nesa_device.cuh"
@@ -89,6 +90,8 @@ extern "C" int nesa_matvec_noalloc(nesa_ctx *c, const nesa_c128 *x, nesa_c128 *y
     check_cuda(cudaGetLastError(), "matvec launch");
   } catch (const Error &e) {
     status = e.status;
+  } catch (const std::bad_alloc &) {
+    status = NESA_ERR_OOM;
   }
   for (int l = c->l0; l <= c->L; ++l) {
     c->lev[l].s = saved_s[l];

@@ -21,6 +21,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <new>
 #include <vector>
 
 #include <cuda_fp16.h>
@@ -820,6 +821,9 @@ int nesa_precond_setup(nesa_ctx *c) {
   } catch (const Error &e) {
     set_last_error(e.what);
     return e.status;
+  } catch (const std::bad_alloc &) {
+    set_last_error("host allocation failed");
+    return NESA_ERR_OOM;
   }
   return NESA_OK;
 }
@@ -835,6 +839,9 @@ int nesa_precond_apply(nesa_ctx *c, int kind, const nesa_c128 *r, nesa_c128 *z, 
   } catch (const Error &e) {
     set_last_error(e.what);
     return e.status;
+  } catch (const std::bad_alloc &) {
+    set_last_error("host allocation failed");
+    return NESA_ERR_OOM;
   }
   return NESA_OK;
 }
@@ -855,6 +862,9 @@ int nesa_precond_params(nesa_ctx *c, int set, float *host) {
   } catch (const Error &e) {
     set_last_error(e.what);
     return e.status;
+  } catch (const std::bad_alloc &) {
+    set_last_error("host allocation failed");
+    return NESA_ERR_OOM;
   }
   return NESA_OK;
 }
@@ -867,6 +877,9 @@ int nesa_precond_features(nesa_ctx *c, float *host) {
   } catch (const Error &e) {
     set_last_error(e.what);
     return e.status;
+  } catch (const std::bad_alloc &) {
+    set_last_error("host allocation failed");
+    return NESA_ERR_OOM;
   }
   return NESA_OK;
 }
@@ -880,6 +893,9 @@ int nesa_precond_loss_grad(nesa_ctx *c, const nesa_c128 *u, const nesa_c128 *v, 
   } catch (const Error &e) {
     set_last_error(e.what);
     return e.status;
+  } catch (const std::bad_alloc &) {
+    set_last_error("host allocation failed");
+    return NESA_ERR_OOM;
   }
   return NESA_OK;
 }
@@ -968,6 +984,9 @@ int nesa_precond_train(nesa_ctx *c, const nesa_c128 *b, int nrhs, const nesa_lea
   } catch (const Error &e) {
     set_last_error(e.what);
     return e.status;
+  } catch (const std::bad_alloc &) {
+    set_last_error("host allocation failed");
+    return NESA_ERR_OOM;
   }
   I.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (info) *info = I;

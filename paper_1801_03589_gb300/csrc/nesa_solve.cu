@@ -15,6 +15,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <new>
 
 #include "nesa_device.cuh"
 
@@ -633,6 +634,9 @@ int nesa_solve(nesa_ctx *c, const nesa_c128 *b_dev, nesa_c128 *x_dev, int nrhs, 
   } catch (const Error &e) {
     status = e.status;
     set_last_error(e.what);
+  } catch (const std::bad_alloc &) {
+    status = NESA_ERR_OOM;
+    set_last_error("host allocation failed");
   }
   I.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (info) *info = I;
