@@ -310,6 +310,7 @@ def run_model2d(args, stream, world, barrier, max_over_ranks):
     x = curve_points(n, seed=1)
     qd = torch.from_numpy(charges(n, seed=1)).cuda()
     y = torch.empty_like(qd)
+    torch.cuda.synchronize()  # the copy above ran on torch's stream, the products run on `stream`
     out = {"workload": "N = 100,000 charges on a seeded closed curve (the paper's curve is not available); "
                        "phi = K q, K = -log|x_i - x_j|; FP64", "cases": []}
     for P, Q in ((300, 100), (50, 10)):
