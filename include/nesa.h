@@ -153,6 +153,14 @@ void nesa_default_params(nesa_params *p);
  */
 int nesa_build(const nesa_mesh *mesh, double k, const nesa_params *params, nesa_ctx **out);
 
+/*
+ * The host part of nesa_build alone (no device, no CUDA call): RWG functions, octree,
+ * lists and Q per level for the same arguments, reported in *info (host struct) as
+ * nesa_get_info would report them; device_bytes is 0 and build_seconds the host time.
+ * Synchronous.  Errors: INVALID_ARG, MESH, OOM.
+ */
+int nesa_plan(const nesa_mesh *mesh, double k, const nesa_params *params, nesa_info *info);
+
 /* Use cuda_stream (a cudaStream_t, may be NULL for the legacy stream) for all later
    device work of the context. */
 int nesa_set_stream(nesa_ctx *ctx, void *cuda_stream);

@@ -109,6 +109,7 @@ def lib():
         sig = {
             "nesa_default_params": (None, [P]),
             "nesa_build": (I, [P, D, P, P]),
+            "nesa_plan": (I, [P, D, P, P]),
             "nesa_set_stream": (I, [P, P]),
             "nesa_num_unknowns": (I, [P, P]),
             "nesa_get_info": (I, [P, P]),
@@ -285,6 +286,17 @@ class Batch:
             self.close()
         except Exception:  # noqa: BLE001 - interpreter shutdown
             pass
+
+
+def plan(vertices, triangles, k, **params):
+    """The host part of a build (no device): sizes of the operator nesa_build would make."""
+    v = np.ascontiguousarray(vertices, dtype=np.float64)
+    t = np.ascontiguousarray(triangles, dtype=np.int32)
+    mesh = Mesh(len(v), len(t), v.ctypes.data, t.ctypes.data)
+    p = default_params(**params)
+    i = Info()
+    _check(lib().nesa_plan(ctypes.byref(mesh), float(k), ctypes.byref(p), ctypes.byref(i)))
+    return i.as_dict()
 
 
 class Nesa:

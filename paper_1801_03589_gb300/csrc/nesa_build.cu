@@ -700,25 +700,69 @@ static void free_ctx(nesa_ctx *c) {
   delete c;
 }
 
+static bool build_args_ok(const nesa_mesh *mesh, double k, const nesa_params *params) {
+  if (!mesh || !params || !mesh->vertices || !mesh->triangles || mesh->n_vertices < 3 || mesh->n_triangles < 1)
+    return false;
+  return (k > 0.0) && (params->leaf_size > 0.0) && params->n_levels >= 1 && params->n_levels <= NESA_MAX_LEVELS &&
+         (params->q_mode == NESA_Q_FIXED || params->q_mode == NESA_Q_AUTO) && params->q_fixed >= 1 &&
+         (params->precision == NESA_FP64 || params->precision == NESA_MIXED) && params->translate >= 0 &&
+         params->translate <= 1 &&
+         (params->tile_n == 0 || params->tile_n == 64 || params->tile_n == 128 || params->tile_n == 256) &&
+         (params->rho_eq > 0.0) && (params->rho_test > params->rho_eq) && (params->pinv_eps >= 0.0) &&
+         mesh->n_triangles <= (1LL << 28);
+}
+
+// the sizes nesa_info reports that the host model alone determines
+static void host_info(const HostModel &h, nesa_info &I) {
+  I.n_unknowns = h.n;
+  I.n_triangles = h.nt;
+  I.n_points = h.np;
+  I.n_levels = h.L + 1;
+  I.l0 = h.l0;
+  for (int l = 0; l <= h.L; ++l) {
+    I.q[l] = h.lev[l].q;
+    I.n_boxes[l] = (int64_t)h.lev[l].key.size();
+    I.n_interactions[l] = (int64_t)h.lev[l].il_src.size();
+    I.n_offsets[l] = (int64_t)h.lev[l].offsets.size() / 3;
+  }
+  I.near_nnz = h.nz_ptr.empty() ? 0 : h.nz_ptr.back();
+  I.near_tri_pairs = h.tp_ptr.empty() ? 0 : h.tp_ptr.back();
+  I.v_columns = (int64_t)h.vc_rwg.size();
+  I.max_leaf_columns = 0;
+  for (size_t b = 0; b + 1 < h.vc_ptr.size(); ++b)
+    I.max_leaf_columns = std::max<int64_t>(I.max_leaf_columns, h.vc_ptr[b + 1] - h.vc_ptr[b]);
+}
+
+int nesa_plan(const nesa_mesh *mesh, double k, const nesa_params *params, nesa_info *info) {
+  if (!info || !build_args_ok(mesh, k, params)) return NESA_ERR_INVALID_ARG;
+  auto t0 = std::chrono::steady_clock::now();
+  try {
+    HostModel h;
+    build_host_model(*mesh, k, *params, h);
+    std::memset(info, 0, sizeof(*info));
+    host_info(h, *info);
+  } catch (const Error &e) {
+    g_last_error = e.what;
+    return e.status;
+  } catch (const std::bad_alloc &) {
+    g_last_error = "host allocation failed";
+    return NESA_ERR_OOM;
+  }
+  info->build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return NESA_OK;
+}
+
 int nesa_build(const nesa_mesh *mesh, double k, const nesa_params *params, nesa_ctx **out) {
   if (!out) return NESA_ERR_INVALID_ARG;
   *out = nullptr;
-  if (!mesh || !params || !mesh->vertices || !mesh->triangles || mesh->n_vertices < 3 || mesh->n_triangles < 1)
-    return NESA_ERR_INVALID_ARG;
-  if (!(k > 0.0) || !(params->leaf_size > 0.0) || params->n_levels < 1 || params->n_levels > NESA_MAX_LEVELS ||
-      (params->q_mode != NESA_Q_FIXED && params->q_mode != NESA_Q_AUTO) || params->q_fixed < 1 ||
-      (params->precision != NESA_FP64 && params->precision != NESA_MIXED) || params->translate < 0 ||
-      params->translate > 1 ||
-      (params->tile_n != 0 && params->tile_n != 64 && params->tile_n != 128 && params->tile_n != 256) ||
-      !(params->rho_eq > 0.0) || !(params->rho_test > params->rho_eq) ||
-      !(params->pinv_eps >= 0.0) || mesh->n_triangles > (1LL << 28))
-    return NESA_ERR_INVALID_ARG;
+  if (!build_args_ok(mesh, k, params)) return NESA_ERR_INVALID_ARG;
   auto t0 = std::chrono::steady_clock::now();
   nesa_ctx *c = new nesa_ctx();
   c->k = k;
   c->eta = 4e-7 * 3.14159265358979323846 * 299792458.0;
   try {
     build_host_model(*mesh, k, *params, c->h);
+    c->info.near_tri_pairs = c->h.tp_ptr.empty() ? 0 : c->h.tp_ptr.back();
     build_device(c, *params);
     // drop the host arrays that the device copies replace
     c->h.tp_ptr.clear();
