@@ -56,6 +56,37 @@ def groups(nesa_oracle):
     return [np.array(v) for _, v in sorted(out.items())]
 
 
+def touching(a, b):
+    """Leaves with integer coordinates a and b touch (or coincide): every coordinate
+    differs by at most one."""
+    return max(abs(x - y) for x, y in zip(a, b)) <= 1
+
+
+def ras_blocks(N, home):
+    """Blocks of the overlapping block-Jacobi preconditioner for the functions whose
+    home leaves (integer coordinates) are the rows of ``home``: per home leaf c, its
+    group g (functions homed in c), the extended set E (functions whose home leaf
+    touches c, ascending) and the rows of g in (N restricted to E x E)^-1."""
+    by_leaf = {}
+    for m, key in enumerate(map(tuple, np.asarray(home).tolist())):
+        by_leaf.setdefault(key, []).append(m)
+    out = []
+    for key, members in by_leaf.items():
+        E = np.array(sorted(m for k2, ms in by_leaf.items() if touching(key, k2) for m in ms))
+        g = np.array(members)
+        rows = np.linalg.inv(N[np.ix_(E, E)])[np.searchsorted(E, g), :]
+        out.append((g, E, rows))
+    return out
+
+
+def ras_apply(blocks, u):
+    """z = S u: each group's rows of its extended inverse applied to u on E."""
+    z = np.zeros_like(u)
+    for g, E, rows in blocks:
+        z[g] = rows @ u[E]
+    return z
+
+
 class Preconditioner:
     def __init__(self, nesa_oracle):
         self.o = nesa_oracle
@@ -73,29 +104,15 @@ class Preconditioner:
         return z
 
     def _ras_setup(self):
-        """Overlapping block-Jacobi (restricted additive Schwarz): for the group of leaf
-        c, E = functions whose home leaf touches c; keep the group's rows of
-        (N restricted to E x E)^-1."""
+        """Overlapping block-Jacobi (restricted additive Schwarz) over the home leaves."""
         o = self.o
         home = o.tree.point_leaf_ijk.reshape(-1, 7, 3)[o.rwg["tri"][:, 0], 0]
-        by_leaf = {}
-        for m, key in enumerate(map(tuple, home.tolist())):
-            by_leaf.setdefault(key, []).append(m)
-        self._ras = []
-        for key, members in by_leaf.items():
-            E = np.array(sorted(m for k2, ms in by_leaf.items()
-                                if max(abs(a - b) for a, b in zip(key, k2)) <= 1 for m in ms))
-            g = np.array(members)
-            rows = np.linalg.inv(self.N[np.ix_(E, E)])[np.searchsorted(E, g), :]
-            self._ras.append((g, E, rows))
+        self._ras = ras_blocks(self.N, home)
 
     def ras(self, u):
         if self._ras is None:
             self._ras_setup()
-        z = np.zeros_like(u)
-        for g, E, rows in self._ras:
-            z[g] = rows @ u[E]
-        return z
+        return ras_apply(self._ras, u)
 
     def near_row_lengths(self):
         """Structural length of every near-field row: the number of functions n with at

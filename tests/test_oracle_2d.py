@@ -72,10 +72,23 @@ def test_nesa_converges_to_dense():
     x = curve_points(3000, seed=1)
     q = charges(3000, seed=1)
     ref = dense_matvec(x, q)
-    errs = [rel(Nesa2D(x, 30, Q).matvec(q), ref) for Q in (6, 10, 16, 24)]
+    errs = [rel(Nesa2D(x, 30, Q, pinv_eps=1e-9).matvec(q), ref) for Q in (6, 10, 16, 24)]
     print("2D NESA vs dense, Q = 6, 10, 16, 24:", ["%.2e" % e for e in errs])
     assert all(e2 < e1 / 5 for e1, e2 in zip(errs, errs[1:]))
     assert errs[1] < 1e-3 and errs[-1] < 1e-6
+
+
+def test_regulariser_reading_does_not_change_the_accuracy():
+    """The equivalent-charge fit is Tikhonov-regularised at eps = 1e-9 ||G(T, E)||_F (the
+    same rule as the 3D fit).  The error against the dense product at 1e-9 is that of
+    the nearly unregularised fit (1e-12) to within 10 %, at every Q of the table."""
+    x = curve_points(3000, seed=1)
+    q = charges(3000, seed=1)
+    ref = dense_matvec(x, q)
+    for Q in (10, 16, 24):
+        e9 = rel(Nesa2D(x, 30, Q, pinv_eps=1e-9).matvec(q), ref)
+        e12 = rel(Nesa2D(x, 30, Q, pinv_eps=1e-12).matvec(q), ref)
+        assert abs(e9 - e12) <= 0.1 * e12, (Q, e9, e12)
 
 
 def test_nesa_matrix_is_symmetric():
