@@ -6,18 +6,20 @@ one right-hand side.  One step = one full operator application (near field +
 radiation, source transfer, translation, potential transfer, reception) through the
 library's C ABI.
 
-``value`` is the rate of the mixed-precision product (the low-precision operator
-copy; its error against the FP64 product is measured and reported); the plain FP64
-product is timed beside it (``fp64``), and one GMRES solve to 1e-5 with FP64
-iterative refinement around the mixed product is timed (``solve``).
+``value`` is the rate of the FP64 product (the paper's arithmetic: complex128 operator,
+FP64 kernels).  The mixed-precision product (tensor-core BF16 hi/lo translations,
+complex64 elsewhere; its error against the FP64 product is measured and reported) is
+timed beside it (``mixed``), and GMRES solves to 1e-5 are timed for both: the plain
+FP64 solve and FP64 iterative refinement around the mixed product (``solve``).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Prints one JSON line on rank 0.  ``--impl reference`` times the CPU oracle instead:
-each step is a stage-wise sample of one product (see ``oracle_sampled_product``).
-Under torchrun (N > 1) every rank runs an independent replica of the workload
-(the product of one operator does not shard without a halo exchange, which is not
-built); ``value`` counts the products of all ranks.
+Prints one JSON line on rank 0.  ``--impl reference`` times the CPU oracle instead, on
+all host cores: each step is a stage-wise sample of one product (see
+``oracle_sampled_product``) spread over a process pool.  Under torchrun (N > 1) every
+rank runs an independent replica of the workload (the product of one operator does not
+shard without a halo exchange, which is not built); ``value`` counts the products of
+all ranks.
 """
 import os
 
@@ -48,6 +50,9 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # DRAM traffic of the translation / potential-transfer GEMM launches of one product of
 # the r = 3 sphere (ncu, dram__bytes_read.sum + dram__bytes_write.sum); null elsewhere
 GEMM_DRAM_BYTES_C2 = 1.5083e9
+# DRAM traffic of the FP64 translation launches (k_translate<double2>) of one product of
+# the r = 3 sphere; None until measured on the current kernel
+K_TRANSLATE64_DRAM_BYTES_C2 = None
 SPEC = ("PEC sphere r=3 wavelengths, icosphere subdiv 6 (81,920 triangles, 122,880 RWG), "
         "6-level octree, leaf 0.25 wavelength, 1 RHS")
 
@@ -234,32 +239,145 @@ def oracle_sampled_product(o, x, n_leaves=12, n_boxes=12, n_rows=48, seed=0):
     return total, parts, desc
 
 
+# ------------------------------------------------------------------ all-core oracle timing
+# Worker processes (spawned, so that no CUDA state is inherited) each build the oracle
+# once; a sampled stage then runs as one task per worker, every task the size of the
+# single-core sample (like the paper's OpenMP/SuperGlue tasks, Sec. 5.3, one unit group
+# per task), and the stage's wall time is scaled by its unit count.
+_W = {}
+
+
+def _pool_init(cfg_name, seed):
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    o = build_oracle(get_config(cfg_name))
+    x = random_coefficients(o.n, 1, seed=seed)[0]
+    _W.update(o=o, x=x, J=o.sources(x))
+
+
+def _pool_task(task):
+    o, kind = _W["o"], task[0]
+    rng = np.random.default_rng(task[-1])
+    if kind == "near":
+        _ = o.near_rows(task[1]) @ _W["x"]
+    elif kind == "radiation":
+        for b in task[1]:
+            o.radiate(_W["J"], b)
+    elif kind == "source_transfer":
+        s = rng.standard_normal((o.Q[task[1]], 4)) + 0j
+        for b in task[2]:
+            o.source_transfer(task[1], b, s)
+    elif kind == "translation":
+        l, boxes = task[1], task[2]
+        srcs = {b for a in boxes for b in o.tree.interaction_list(l, a)}
+        s = {b: rng.standard_normal((o.Q[l], 4)) + 0j for b in srcs}
+        op = rng.standard_normal((o.Q[l - 1], 4)) + 0j if l > o.l0 else None
+        o._D = {}
+        for a in boxes:
+            o.translate(l, a, s, op)
+        o._D = {}
+    elif kind == "reception":
+        oL = rng.standard_normal((o.Q[o.L], 4)) + 0j
+        for b in task[1]:
+            o.receive(b, oL)
+    elif kind == "testing":
+        F = np.zeros((len(o.tree.points), 4), np.complex128)
+        o.test(F, task[1])
+    return 0
+
+
+class OraclePool:
+    """A spawned process pool of `procs` workers, each holding the oracle of one workload."""
+
+    def __init__(self, cfg_name, procs, seed=2024):
+        import multiprocessing as mp
+        self.procs = procs
+        self.pool = mp.get_context("spawn").Pool(procs, initializer=_pool_init, initargs=(cfg_name, seed))
+        self.pool.map(_pool_task, [("near", [0], i) for i in range(procs)])  # every worker is up
+
+    def close(self):
+        self.pool.terminate()
+        self.pool.join()
+
+    def sampled_product(self, o, n_leaves=12, n_boxes=12, n_rows=48, seed=0):
+        """As oracle_sampled_product, with every stage's sample multiplied by the number of
+        workers and run as one task per worker.  The channel sources (one pass over the
+        triangles, under 1 % of the product) are timed on one core."""
+        P = self.procs
+        rng = np.random.default_rng(seed)
+        t = o.tree
+        L, l0 = o.L, o.l0
+        parts = {}
+
+        def run(tasks):
+            t0 = time.perf_counter()
+            self.pool.map(_pool_task, tasks, chunksize=1)
+            return time.perf_counter() - t0
+
+        def groups(seq, k):
+            seq = list(seq)
+            idx = rng.choice(len(seq), size=min(k * P, len(seq)), replace=False)
+            picked = [seq[i] for i in idx]
+            return [picked[i::P] for i in range(P) if picked[i::P]], len(picked)
+
+        t0 = time.perf_counter()
+        o.sources(random_coefficients(o.n, 1, seed=seed)[0])
+        parts["sources"] = time.perf_counter() - t0
+        rows = np.sort(rng.choice(o.n, size=min(n_rows * P, o.n), replace=False))
+        chunks = [rows[i::P] for i in range(P)]
+        parts["near"] = run([("near", c, i) for i, c in enumerate(chunks)]) * o.n / len(rows)
+        g, m = groups(t.boxes[L], n_leaves)
+        parts["radiation"] = run([("radiation", c, i) for i, c in enumerate(g)]) * len(t.boxes[L]) / m
+        up = 0.0
+        for l in range(L, l0, -1):
+            g, m = groups(t.boxes[l], n_boxes)
+            up += run([("source_transfer", l, c, i) for i, c in enumerate(g)]) * len(t.boxes[l]) / m
+        parts["source_transfer"] = up
+        tr = 0.0
+        for l in range(l0, L + 1):
+            g, m = groups(t.boxes[l], n_boxes)
+            tr += run([("translation", l, c, i) for i, c in enumerate(g)]) * len(t.boxes[l]) / m
+        parts["translation"] = tr
+        g, m = groups(t.boxes[L], n_leaves)
+        parts["reception"] = run([("reception", c, i) for i, c in enumerate(g)]) * len(t.boxes[L]) / m
+        parts["testing"] = run([("testing", c, i) for i, c in enumerate(chunks)]) * o.n / len(rows)
+        desc = ("stage-wise sample of one product on %d worker processes (one task per worker, each the size of "
+                "the single-core sample: %d leaves, %d boxes per level, %d rows); each stage's wall time scaled by "
+                "its unit count; channel sources on one core" % (P, n_leaves, n_boxes, n_rows))
+        return sum(parts.values()), parts, desc
+
+
 def build_oracle(cfg):
     from oracle.nesa import NesaOracle
     return NesaOracle(cfg["vertices"], cfg["triangles"], cfg["k"], cfg["leaf_size"], cfg["n_levels"])
 
 
 def run_reference(args, world, rank):
+    """The oracle, as it stands, on all host cores (rank 0 only)."""
     if rank != 0:
         return 0
     cfg = get_config(CONFIG)
     o = build_oracle(cfg)
-    x = random_coefficients(o.n, 1, seed=2024)[0]
-    for _ in range(args.warmup):
-        oracle_sampled_product(o, x, seed=1)
-    est, walls = [], []
-    for s in range(args.steps):
-        t0 = time.perf_counter()
-        sec, parts, desc = oracle_sampled_product(o, x, seed=100 + s)
-        walls.append(time.perf_counter() - t0)
-        est.append(sec)
+    procs = os.cpu_count() or 1
+    pool = OraclePool(CONFIG, procs)
+    try:
+        for _ in range(args.warmup):
+            pool.sampled_product(o, seed=1)
+        est, walls = [], []
+        for s in range(args.steps):
+            t0 = time.perf_counter()
+            sec, parts, desc = pool.sampled_product(o, seed=100 + s)
+            walls.append(time.perf_counter() - t0)
+            est.append(sec)
+    finally:
+        pool.close()
     value = 1.0 / float(np.mean(est))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * float(np.mean(walls)), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": {"workload": "%s: %s" % (CONFIG, SPEC), "parallelism": "single process, host cores"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "config": {"workload": "%s: %s" % (CONFIG, SPEC), "parallelism": "%d host processes" % procs},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle", "sample": desc,
+                         "host_cpu_count": os.cpu_count()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -371,26 +489,33 @@ def run_ours(args, world, rank, local):
         ms64, prof64 = _time_products(g, x, y, nesa.PART_ALL, args.steps, args.warmup, stream, barrier)
         ms_mx, prof_mx = _time_products(g, x, y, mixed, args.steps, args.warmup, stream, barrier)
     ms64, ms_mx = max_over_ranks(ms64), max_over_ranks(ms_mx)
-    value = job_throughput(world, nrhs, ms_mx)
+    value = job_throughput(world, nrhs, ms64)  # the FP64 product: the paper's arithmetic
     # accuracy of the mixed product against the FP64 product on this input
     y64 = g.matvec(x)
     ymx = g.matvec(x, parts=mixed)
     mixed_err = float((ymx - y64).abs().pow(2).sum().sqrt() / y64.abs().pow(2).sum().sqrt())
 
     # end to end through the host-pointer entry point: H2D of x, product, D2H of y
+    # (FP64 product for the headline, the mixed product beside it)
     xh = torch.from_numpy(random_coefficients(n, nrhs, seed=7 + rank)).pin_memory()
     yh = torch.empty_like(xh).pin_memory()
-    for _ in range(3):
-        g.matvec_host_ptr(xh.data_ptr(), yh.data_ptr(), nrhs, mixed)
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        g.matvec_host_ptr(xh.data_ptr(), yh.data_ptr(), nrhs, mixed)
-    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps)
 
-    # solves to 1e-5 (x-polarised plane wave along +z): FP64 refinement around GMRES(100)
-    # on the mixed product (inner tolerance 1e-2), without and with the overlapping
-    # block-Jacobi preconditioner; optionally the plain FP64 solve for comparison
+    def e2e(parts):
+        for _ in range(3):
+            g.matvec_host_ptr(xh.data_ptr(), yh.data_ptr(), nrhs, parts)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            g.matvec_host_ptr(xh.data_ptr(), yh.data_ptr(), nrhs, parts)
+        return max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps)
+
+    e2e_ms = e2e(nesa.PART_ALL)
+    e2e_mx_ms = e2e(mixed)
+
+    # solves to 1e-5 (x-polarised plane wave along +z): the plain FP64 GMRES(100) with the
+    # overlapping block-Jacobi preconditioner (the comparator of the metric), and FP64
+    # refinement around GMRES(100) on the mixed product (inner tolerance 3e-3), without
+    # and with that preconditioner; optionally the unpreconditioned FP64 solve
     solve = None
     if not args.no_solve:
         b = g.rhs_planewave([[0.0, 0.0, 1.0]], [[1.0, 0.0, 0.0]])
@@ -408,11 +533,13 @@ def run_ours(args, world, rank, local):
         torch.cuda.synchronize()
         setup_s = time.perf_counter() - t0
         solve = {"tol": 1e-5,
+                 "fp64_overlap": one(precond=nesa.PRECOND_OVERLAP),
                  "mixed_none": one(mixed=True, inner_tol=3e-3),
                  "mixed_overlap": one(mixed=True, inner_tol=3e-3, precond=nesa.PRECOND_OVERLAP),
                  "overlap_setup_seconds": setup_s,
-                 "method": "FP64 iterative refinement, inner GMRES(100) on the mixed product to 3e-3; overlapping "
-                           "block-Jacobi = near-field restricted additive Schwarz over touching leaves"}
+                 "method": "fp64_*: GMRES(100) on the FP64 product; mixed_*: FP64 iterative refinement, inner "
+                           "GMRES(100) on the mixed product to 3e-3; overlapping block-Jacobi = near-field "
+                           "restricted additive Schwarz over touching leaves (setup reported apart)"}
         if args.fp64_solve:
             solve["fp64_none"] = one()
 
@@ -498,10 +625,27 @@ def run_ours(args, world, rank, local):
         ranks.close()
         return 0
 
+    peaks = _peaks()
+    hbm_peak = peaks.get("hbm_gbs", 6790.0)
+    bf16_peak = peaks.get("bf16_tflops", 1901.0)
+
+    # roofline of the headline (FP64) product: its dominant kernel is the translation
+    # (k_translate<double2>, Eqs. 12-13), bound by the FP64 pipe (a complex multiply-add
+    # is 4 DFMA against 16 bytes of matrix data)
+    tr64 = prof64["translation"]
+    ach64 = tr64["flops"] / (tr64["ms"] * 1e-3) / 1e12
+    roof = {"kernel": "k_translate<double2>", "bound": "alu", "achieved": ach64, "peak": FP64_PEAK_TFLOPS,
+            "unit": "TFLOP/s", "frac": ach64 / FP64_PEAK_TFLOPS,
+            "peak_note": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (derived from unit counts and the "
+                         "maximum clock); achieved counts 8 flops per complex multiply-add",
+            "traffic": (K_TRANSLATE64_DRAM_BYTES_C2 if (args.workload == CONFIG and nrhs == 1) else None),
+            "traffic_unit": "bytes per product (all launches of the kernel in one product)",
+            "share_of_product": tr64["ms"] / sum(v["ms"] for k, v in prof64.items() if k != "translation_tensor_gemm"),
+            "ms_per_step": tr64["ms"] / args.steps}
+
     # roofline of the dominant kernel of the mixed product (largest device time); the
     # tensor-core GEMMs are timed alone (stage 4), the rest of the translation stage is
     # their split and reduction kernels
-    peaks = _peaks()
     gemm = prof_mx["translation_tensor_gemm"]
     rest = {"ms": max(0.0, prof_mx["translation"]["ms"] - gemm["ms"]), "flops": 0.0,
             "bytes": max(0.0, prof_mx["translation"]["bytes"] - gemm["bytes"])}
@@ -513,46 +657,53 @@ def run_ours(args, world, rank, local):
     d, bound = kernels[kernel]
     sec = d["ms"] * 1e-3
     if bound == "tensor":
-        roof = {"bound": "tensor", "achieved": d["flops"] / sec / 1e12, "unit": "TFLOP/s",
-                "peak": peaks.get("bf16_tflops_sustained", 1700.0),
-                "peak_note": "BF16 dense, sustained, measured (MEASURED_PEAKS.json); achieved counts 8 flops per "
-                             "complex multiply-add of the translations and potential transfers, the BF16 hi/lo "
-                             "split executes 3x that"}
-    elif bound == "hbm":
-        roof = {"bound": "hbm", "achieved": d["bytes"] / sec / 1e9, "unit": "GB/s",
-                "peak": peaks.get("hbm_gbs", 6800.0), "peak_note": "HBM copy bandwidth, measured"}
+        roof_mx = {"bound": "tensor", "achieved": d["flops"] / sec / 1e12, "unit": "TFLOP/s", "peak": bf16_peak,
+                   "peak_note": "BF16 dense, burst, measured (MEASURED_PEAKS.json; 1901 when absent); achieved "
+                                "counts 8 flops per complex multiply-add of the translations and potential transfers, "
+                                "the BF16 hi/lo split executes 3x that"}
     else:
-        roof = {"bound": "alu", "achieved": d["flops"] / sec / 1e12, "unit": "TFLOP/s", "peak": FP32_PEAK_TFLOPS,
-                "peak_note": "FP32: 152 SMs x 256 flop/clk x 2070 MHz (derived)"}
+        roof_mx = {"bound": "hbm", "achieved": d["bytes"] / sec / 1e9, "unit": "GB/s", "peak": hbm_peak,
+                   "peak_note": "HBM copy bandwidth, measured"}
     # DRAM bytes (read + written) per product of the stage-4 launches, from the ncu capture
-    # in profiles/k_tc_gemm_C2_dram.md (r = 3 sphere, 1 RHS, this kernel version)
+    # (r = 3 sphere, 1 RHS, this kernel version)
     traffic = GEMM_DRAM_BYTES_C2 if (kernel == "k_tc_gemm" and args.workload == CONFIG and nrhs == 1) else None
-    roof.update({"kernel": kernel, "frac": roof["achieved"] / roof["peak"], "traffic": traffic,
-                 "traffic_unit": "bytes per product (all launches of the kernel in one product)",
-                 "ms_per_step": d["ms"] / args.steps})
+    roof_mx.update({"kernel": kernel, "frac": roof_mx["achieved"] / roof_mx["peak"], "traffic": traffic,
+                    "traffic_unit": "bytes per product (all launches of the kernel in one product)",
+                    "ms_per_step": d["ms"] / args.steps})
     # kernels launched in the timed region: one product captured into a CUDA graph by the
     # library's batch API, its kernel nodes counted, times the timed products
-    b1 = nesa.Batch([g], [x], [y], parts=mixed)
-    per_product = b1.kernel_nodes
-    b1.close()
-    launches = per_product * args.steps
+    counts = {}
+    for name, parts in (("fp64", nesa.PART_ALL), ("mixed", mixed)):
+        b1 = nesa.Batch([g], [x], [y], parts=parts)
+        counts[name] = b1.kernel_nodes
+        b1.close()
+    launches = counts["fp64"] * args.steps
 
     cpu = None
     if not args.no_cpu_baseline:
         o = build_oracle(cfg)
         xo = random_coefficients(n, 1, seed=2024)[0]
-        sec, parts, desc = oracle_sampled_product(o, xo, seed=3)
-        cpu = {"value": 1.0 / sec, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
-               "seconds_per_matvec": sec, "stage_seconds": parts}
+        sec1, parts1, desc1 = oracle_sampled_product(o, xo, seed=3)
+        procs = os.cpu_count() or 1
+        pool = OraclePool(CONFIG if args.workload == CONFIG else args.workload, procs)
+        try:
+            secp, partsp, descp = pool.sampled_product(o, seed=3)
+        finally:
+            pool.close()
+        cpu = {"value": 1.0 / secp, "unit": UNIT, "cores": procs, "kind": "oracle", "sample": descp,
+               "seconds_per_matvec": secp, "stage_seconds": partsp, "host_cpu_count": os.cpu_count(),
+               "single_core": {"value": 1.0 / sec1, "cores": 1, "seconds_per_matvec": sec1,
+                               "stage_seconds": parts1, "sample": desc1}}
 
+    solve_fp64 = solve["fp64_overlap"]["seconds"] if solve else None
+    solve_mx = solve["mixed_overlap"]["seconds"] if solve else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": max(3, args.warmup), "ms_per_step": ms_mx, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "warmup": max(3, args.warmup), "ms_per_step": ms64, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": ("%s: %s" % (CONFIG, SPEC)) if args.workload == CONFIG else args.workload,
                    "nrhs": nrhs, "n_unknowns": n,
-                   "product": "mixed precision: translations on tcgen05 tensor cores (BF16 hi/lo, 3 products, FP32 "
-                              "accumulate), other stages complex64; rel err vs FP64 product %.1e" % mixed_err,
+                   "product": "FP64: complex128 operator, FP64 kernels (the paper's arithmetic)",
                    "levels": info["n_levels"], "l0": info["l0"], "q": info["q"][info["l0"]:],
                    "near_nnz": info["near_nnz"], "device_gb": info["device_bytes"] / 1e9,
                    "build_s": info["build_seconds"],
@@ -565,16 +716,21 @@ def run_ours(args, world, rank, local):
                 "d2h_bytes_per_step": 16 * n * nrhs, "ms_per_step": e2e_ms},
         "gpu_launches": launches,
         "roofline": roof,
-        "stages": _stages(prof_mx, args.steps),
-        "tensor_tiles": {str(l): t for l, t in g.tuning().items()},
-        "fp64": {"value": job_throughput(world, nrhs, ms64), "unit": UNIT, "ms_per_step": ms64, "dtype": "f64",
-                 "stages": _stages(prof64, args.steps),
-                 "roofline": {"kernel": "k_translate<double2>", "bound": "alu",
-                              "achieved": prof64["translation"]["flops"] / (prof64["translation"]["ms"] * 1e-3) / 1e12,
-                              "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                              "frac": prof64["translation"]["flops"] / (prof64["translation"]["ms"] * 1e-3) / 1e12
-                              / FP64_PEAK_TFLOPS}},
+        "fp64_value": value,
+        "mixed_value": job_throughput(world, nrhs, ms_mx),
         "mixed_vs_fp64": ms64 / ms_mx,
+        "solve_fp64_s": solve_fp64,
+        "solve_mixed_s": solve_mx,
+        "solve_mixed_vs_fp64": (solve_fp64 / solve_mx) if solve else None,
+        "stages": _stages(prof64, args.steps),
+        "mixed": {"value": job_throughput(world, nrhs, ms_mx), "unit": UNIT, "ms_per_step": ms_mx, "dtype": "f32",
+                  "product": "mixed precision: translations on tcgen05 tensor cores (BF16 hi/lo, 3 products, FP32 "
+                             "accumulate), other stages complex64; rel err vs FP64 product %.1e" % mixed_err,
+                  "rel_err_vs_fp64": mixed_err,
+                  "e2e": {"value": job_throughput(world, nrhs, e2e_mx_ms), "unit": UNIT, "ms_per_step": e2e_mx_ms},
+                  "gpu_launches_per_product": counts["mixed"],
+                  "roofline": roof_mx, "stages": _stages(prof_mx, args.steps),
+                  "tensor_tiles": {str(l): t for l, t in g.tuning().items()}},
         "solve": solve,
         "learned": learned,
         "batch": batch,
@@ -597,7 +753,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-model2d", action="store_true", help="skip the 2D model problem block")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner block (aircraft body)")
-    ap.add_argument("--fp64-solve", action="store_true", help="also time the plain FP64 solve (about 2 minutes)")
+    ap.add_argument("--fp64-solve", action="store_true", help="also time the unpreconditioned FP64 solve (about 2.5 minutes)")
     ap.add_argument("--workload", default=CONFIG, help="workload name (smaller ones are for profiling runs)")
     ap.add_argument("--tile-n", type=int, default=0, choices=[0, 64, 128, 256],
                     help="fixed column-tile width of the tensor GEMMs (0: autotune); for runs under a profiler")

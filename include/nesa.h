@@ -104,7 +104,19 @@ typedef struct {
  *               the autotuner time the three widths at the first mixed product and
  *               keep the fastest per GEMM family (a fixed width makes runs under a
  *               profiler, which distorts the tuner's timings, use the tuned layout)
+ *   points_per_leaf  P of the paper's depth rule (Sec. 3: groups are subdivided while
+ *               they hold at least P sources on average), used when leaf_size is 0: the
+ *               root cube is the cube of the largest side of the vertex bounding box
+ *               (same centre), and the leaf level is the deepest level l <= 19 whose
+ *               occupied boxes hold on average at least P quadrature points (7 per
+ *               triangle).  n_levels is then ignored.  0 when leaf_size > 0.
+ *   n_levels    with leaf_size > 0, 0 selects the fewest levels whose root cube
+ *               (leaf_size * 2^(levels-1)) spans the largest side of the bounding box
+ *   singular_mode  NESA_SINGULAR_TOUCHING (default) or NESA_SINGULAR_SELF
  */
+#define NESA_SINGULAR_TOUCHING 0 /* singularity extraction for every triangle pair sharing a vertex */
+#define NESA_SINGULAR_SELF 1     /* extraction for T = T' only; pairs sharing a vertex or an edge use the
+                                    plain 7 x 7 rule (its nodes are interior, R > 0); Z symmetric to rounding */
 typedef struct {
   double leaf_size;
   int32_t n_levels;
@@ -117,7 +129,8 @@ typedef struct {
   double pinv_eps;
   int32_t translate;
   int32_t tile_n;
-  int32_t reserved[2];
+  int32_t points_per_leaf;
+  int32_t singular_mode;
 } nesa_params;
 
 /* Sizes of a built operator (host struct filled by nesa_get_info). */
@@ -141,7 +154,8 @@ typedef struct {
 } nesa_info;
 
 /* Default parameters: leaf 0.25, 3 levels, NESA_Q_AUTO, q_fixed 100, q_digits 5,
-   rho_eq 1, rho_test (2 - sqrt3/2)/(sqrt3/2), pinv_eps 1e-9, NESA_FP64. */
+   rho_eq 1, rho_test (2 - sqrt3/2)/(sqrt3/2), pinv_eps 1e-9, NESA_FP64, points_per_leaf 0,
+   NESA_SINGULAR_TOUCHING. */
 void nesa_default_params(nesa_params *p);
 
 /*
@@ -380,9 +394,10 @@ int nesa_profile_read(nesa_ctx *ctx, nesa_profile *out);
  * 22 MB per right-hand side for 30,720 unknowns, 52 MB for 122,880).
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress, with that device current): make that first call before any
- * stream capture.  Call it with the context's device current.  All calls share the
- * array, which keeps the last call's data; calls whose kernels overlap on the GPU race
- * on it.  Asynchronous on the context's stream.
+ * stream capture.  Call it with the context's device (the device current at nesa_build)
+ * current: with another device current it returns NESA_ERR_INVALID_ARG and launches
+ * nothing.  All calls share the array, which keeps the last call's data; calls whose
+ * kernels overlap on the GPU race on it.  Asynchronous on the context's stream.
  */
 #define NESA_NOALLOC_SCRATCH_BYTES (32u << 20)
 int nesa_matvec_noalloc(nesa_ctx *ctx, const nesa_c128 *x_dev, nesa_c128 *y_dev, int nrhs);
@@ -403,6 +418,15 @@ int nesa_matvec_noalloc(nesa_ctx *ctx, const nesa_c128 *x_dev, nesa_c128 *y_dev,
  * nesa_batch_launch is asynchronous on `stream`.
  */
 typedef struct nesa_batch nesa_batch;
+/*
+ * Build the operators of n meshes for a batched pass (the several meshes of uneven size
+ * of one sweep): out[i] = the context of meshes[i] at wavenumber k[i] (host array of n),
+ * each exactly as nesa_build with the shared params.  Each mesh keeps its own tree, Q_l
+ * and lists; nesa_batch_create then puts their products into one graph.  On failure
+ * every context built so far is destroyed, out[] holds NULL, and the status of the first
+ * mesh that failed is returned (its index is in nesa_last_error).  Synchronous.
+ */
+int nesa_build_batch(const nesa_mesh *meshes, int n, const double *k, const nesa_params *params, nesa_ctx **out);
 int nesa_batch_create(nesa_ctx *const *ctxs, int n, const nesa_c128 *const *x_dev, nesa_c128 *const *y_dev,
                       const int *nrhs, int parts, nesa_batch **out);
 int nesa_batch_launch(nesa_batch *batch, void *cuda_stream);
@@ -424,6 +448,18 @@ int nesa_get_tuning(nesa_ctx *ctx, int32_t *tile_n, float *ms);
  * out; that product's result is then invalid.  Clears the status.  Synchronous.
  */
 int nesa_device_status(nesa_ctx *ctx);
+
+/*
+ * Failure-detection hook (not part of the method; for tests of the timeout path).
+ * While stall = 1, the producer warps of the tensor-core GEMMs (NESA_TRANSLATE_TENSOR
+ * mixed products) issue no copies and publish no stage, so the consumers' bounded
+ * mbarrier waits run out: the kernel leaves early without touching memory it does not
+ * own, the product's result is invalid, and nesa_device_status returns
+ * NESA_ERR_TIMEOUT.  Nothing faults, traps or hangs.  wait_limit is the number of
+ * try-wait iterations of every bounded wait (0 restores the default, 2^26); stall = 0
+ * restores normal products.  Host state only; takes effect at the next launch.
+ */
+int nesa_inject_stall(nesa_ctx *ctx, int stall, uint32_t wait_limit);
 
 /* Release all memory of the context (NULL is allowed). */
 void nesa_destroy(nesa_ctx *ctx);

@@ -24,7 +24,8 @@ def lib():
         P = ctypes.c_void_p
         _lib.orc_efie_rows.restype = ctypes.c_int
         _lib.orc_efie_rows.argtypes = [ctypes.c_int64, P, ctypes.c_int64, P, P, P, ctypes.c_int64, P, P, P, P,
-                                       ctypes.c_double, ctypes.c_double, ctypes.c_int64, P, ctypes.c_int, P, P]
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_int64, P, ctypes.c_int, P,
+                                       ctypes.c_int, P]
         _lib.orc_static_integrals.restype = None
         _lib.orc_static_integrals.argtypes = [P, P, P, P]
         _lib.orc_green_matrix.restype = None
@@ -54,12 +55,17 @@ def green_matrix(k, a, b):
     return G
 
 
-def efie_rows(vertices, triangles, rwg, k, rows=None, near_leaf_ijk=None, eta=ETA0):
+SINGULAR_MODES = {"touching": 0, "self": 1}
+
+
+def efie_rows(vertices, triangles, rwg, k, rows=None, near_leaf_ijk=None, eta=ETA0, singular_mode="touching"):
     """Rows ``rows`` (default all) of the EFIE matrix Z (complex128 [len(rows), N]).
 
     ``near_leaf_ijk`` None: the full dense MoM matrix.  Otherwise an int array
     [nt, 7, 3] of the leaf coordinates of every quadrature point, and only the near
-    part is returned: point pairs whose leaves touch (|di|,|dj|,|dk| <= 1)."""
+    part is returned: point pairs whose leaves touch (|di|,|dj|,|dk| <= 1).
+    ``singular_mode`` "touching": singularity extraction for every triangle pair that
+    shares a vertex; "self": for T = T' only (see efie_oracle.c)."""
     verts = np.ascontiguousarray(vertices, np.float64)
     tris = np.ascontiguousarray(triangles, np.int32)
     q = np.ascontiguousarray(triangle_points(verts, tris))
@@ -77,7 +83,7 @@ def efie_rows(vertices, triangles, rwg, k, rows=None, near_leaf_ijk=None, eta=ET
         mode, leaf = 1, np.ascontiguousarray(near_leaf_ijk, np.int32)
     st = lib().orc_efie_rows(len(verts), _p(verts), len(tris), _p(tris), _p(q), _p(w), n, _p(tri_rwg), _p(tri_sl),
                              _p(rwg_tri), _p(rwg_free), float(k), float(eta), len(rows), _p(rows), mode, _p(leaf),
-                             _p(out))
+                             SINGULAR_MODES[singular_mode], _p(out))
     if st != 0:
         raise ValueError("a singular (touching) triangle pair straddles non-touching leaves: "
                          "triangles too large for the leaf size")

@@ -27,6 +27,12 @@
  * rule.  The singular pair value is computed with the lower-numbered triangle as the
  * outer one and transposed for the mirrored pair; a self pair is symmetrised, so that
  * the assembled Z is exactly symmetric (reciprocity).
+ *
+ * singular_mode 1 ("self only") restricts the extraction to T = T': pairs that share
+ * only a vertex or an edge then use the plain 7x7 rule (its nodes are interior, so R > 0),
+ * and Z is symmetric to rounding only.  Touching pairs must still lie entirely in
+ * touching leaves in the near-part mode (the leaf-size rule does not depend on the
+ * integration rule).
  */
 #include <complex.h>
 #include <math.h>
@@ -234,14 +240,16 @@ static void pair_matrix_sym(int64_t ta, int64_t tb, const double *verts, const i
  *   rows [nrows]                          requested RWG rows m
  *   mode 0: full matrix (dense MoM)
  *   mode 1: near part only: point pairs (p,q) whose leaves touch, leaf integer coordinates
- *           given per point in leaf_ijk [nt*7*3]; singular pairs must be entirely near
+ *           given per point in leaf_ijk [nt*7*3]; touching pairs must be entirely near
+ *   singular_mode 0: extraction for every pair sharing a vertex; 1: for T = T' only
  *   out [nrows * n] complex (row-major)
  * Returns 0, or -1 if (mode 1) a singular pair has a point pair in non-touching leaves.
  */
 int orc_efie_rows(int64_t nv, const double *verts, int64_t nt, const int32_t *tris, const double *qpts,
                   const double *w, int64_t n, const int32_t *tri_rwg, const double *tri_sl,
                   const int32_t *rwg_tri, const int32_t *rwg_free, double k, double eta,
-                  int64_t nrows, const int64_t *rows, int mode, const int32_t *leaf_ijk, double complex *out) {
+                  int64_t nrows, const int64_t *rows, int mode, const int32_t *leaf_ijk, int singular_mode,
+                  double complex *out) {
   (void)nv;
   (void)rwg_free;
   const cplx pref = -I * eta * k;
@@ -267,7 +275,8 @@ int orc_efie_rows(int64_t nv, const double *verts, int64_t nt, const int32_t *tr
           }
       }
       for (int64_t tb = 0; tb < nt; ++tb) {
-        int singular = share_vertex(tris + 3 * ta, tris + 3 * tb);
+        int touching = share_vertex(tris + 3 * ta, tris + 3 * tb);
+        int singular = touching && (singular_mode == 0 || ta == tb);
         unsigned char mask[49];
         const unsigned char *mp = NULL;
         if (mode == 1) {
@@ -279,7 +288,7 @@ int orc_efie_rows(int64_t nv, const double *verts, int64_t nt, const int32_t *tr
                 cq[2] >= lo[2] - 1 && cq[2] <= hi[2] + 1)
               any = 1;
           }
-          if (!any && !singular) continue;
+          if (!any && !touching) continue;
           int cnt = 0;
           for (int p = 0; p < 7; ++p)
             for (int q = 0; q < 7; ++q) {
@@ -289,7 +298,7 @@ int orc_efie_rows(int64_t nv, const double *verts, int64_t nt, const int32_t *tr
               mask[p * 7 + q] = (unsigned char)near;
               cnt += near;
             }
-          if (singular && cnt != 49) status = -1;
+          if (touching && cnt != 49) status = -1;
           if (cnt == 0) continue;
           mp = mask;
         }

@@ -77,14 +77,16 @@ def q_for_level(k, width, q_mode, q_fixed, q_digits):
 
 class NesaOracle:
     def __init__(self, vertices, triangles, k, leaf_size, n_levels, q_mode="auto", q_fixed=100, q_digits=5.0,
-                 rho_eq=1.0, rho_test=RHO_TEST_DEFAULT, pinv_eps=1e-9, eta=ETA0):
+                 rho_eq=1.0, rho_test=RHO_TEST_DEFAULT, pinv_eps=1e-9, eta=ETA0, singular_mode="touching",
+                 points_per_leaf=0):
+        self.singular_mode = singular_mode
         self.vertices = np.asarray(vertices, np.float64)
         self.triangles = np.asarray(triangles, np.int64)
         self.k = float(k)
         self.eta = float(eta)
         self.rwg = build_rwg(self.vertices, self.triangles)
         self.n = self.rwg["n"]
-        self.tree = Tree(self.vertices, self.triangles, leaf_size, n_levels)
+        self.tree = Tree(self.vertices, self.triangles, leaf_size, n_levels, points_per_leaf)
         t = self.tree
         self.L, self.l0 = t.L, t.l0
         self.Q, self.E, self.T, self.K = {}, {}, {}, {}
@@ -156,7 +158,8 @@ class NesaOracle:
     # ---------------------------------------------------------------- near field
     def near_rows(self, rows=None):
         ijk = self.tree.point_leaf_ijk.reshape(-1, 7, 3)
-        return efie_rows(self.vertices, self.triangles, self.rwg, self.k, rows=rows, near_leaf_ijk=ijk, eta=self.eta)
+        return efie_rows(self.vertices, self.triangles, self.rwg, self.k, rows=rows, near_leaf_ijk=ijk, eta=self.eta,
+                         singular_mode=self.singular_mode)
 
     def near_matrix(self):
         if self._near is None:

@@ -6,6 +6,11 @@ Readings (the paper delegates the details to its NESA reference):
 * the root cube has side leaf_size * 2**(n_levels-1) and is centred on the centre of
   the mesh's vertex bounding box; level l boxes have side w_l = root / 2**l;
   leaf index of a point = floor((x - origin)/w_L) clamped to [0, 2**L - 1] per axis;
+  n_levels = 0 takes the fewest levels whose root spans the largest side of the box;
+* with points_per_leaf = P > 0 instead (Sec. 3: a group is subdivided while it holds
+  at least P sources on average), the root cube is the bounding cube (side = the
+  largest side of the box, same centre) and the leaf level L is the deepest level
+  l <= 19 whose occupied boxes hold on average at least P points;
 * two boxes of one level touch when their integer coordinates differ by at most one
   in every axis (a box touches itself);
 * near field (Eq. 9): at the leaf level, every pair of touching leaves;
@@ -19,17 +24,44 @@ import numpy as np
 from .quadrature import triangle_points
 
 
+MAX_DEPTH = 19
+
+
+def depth_for_points_per_leaf(points, origin, root, P):
+    """Deepest level l <= MAX_DEPTH whose occupied boxes hold at least P points on average."""
+    best = 0
+    for l in range(MAX_DEPTH + 1):
+        w = root / 2.0 ** l
+        ijk = np.clip(np.floor((points - origin) / w).astype(np.int64), 0, 2 ** l - 1)
+        nbox = len(np.unique(ijk, axis=0))
+        if len(points) >= P * nbox:
+            best = l
+        else:
+            break
+    return best
+
+
 class Tree:
-    def __init__(self, vertices, triangles, leaf_size, n_levels):
-        if n_levels < 1:
-            raise ValueError("n_levels >= 1")
-        self.L = n_levels - 1
+    def __init__(self, vertices, triangles, leaf_size, n_levels, points_per_leaf=0):
         lo, hi = vertices.min(0), vertices.max(0)
         self.center = 0.5 * (lo + hi)
-        self.root = leaf_size * 2.0 ** self.L
-        self.origin = self.center - 0.5 * self.root
         self.extent = hi - lo
         self.points = triangle_points(vertices, triangles).reshape(-1, 3)  # point id = 7 t + p
+        if points_per_leaf > 0:
+            self.root = float(self.extent.max())
+            self.origin = self.center - 0.5 * self.root
+            self.L = depth_for_points_per_leaf(self.points, self.origin, self.root, points_per_leaf)
+        else:
+            if n_levels < 0:
+                raise ValueError("n_levels >= 0")
+            if n_levels > 0:
+                self.L = n_levels - 1
+            else:
+                self.L = 0
+                while self.L < MAX_DEPTH and leaf_size * 2.0 ** self.L < self.extent.max():
+                    self.L += 1
+            self.root = leaf_size * 2.0 ** self.L
+            self.origin = self.center - 0.5 * self.root
         nb = 2 ** self.L
         ijk = np.floor((self.points - self.origin) / self.width(self.L)).astype(np.int64)
         self.point_leaf_ijk = np.clip(ijk, 0, nb - 1)

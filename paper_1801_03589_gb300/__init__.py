@@ -40,7 +40,8 @@ class Params(ctypes.Structure):
     _fields_ = [("leaf_size", ctypes.c_double), ("n_levels", ctypes.c_int32), ("q_mode", ctypes.c_int32),
                 ("q_fixed", ctypes.c_int32), ("precision", ctypes.c_int32), ("q_digits", ctypes.c_double),
                 ("rho_eq", ctypes.c_double), ("rho_test", ctypes.c_double), ("pinv_eps", ctypes.c_double),
-                ("translate", ctypes.c_int32), ("tile_n", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("translate", ctypes.c_int32), ("tile_n", ctypes.c_int32), ("points_per_leaf", ctypes.c_int32),
+                ("singular_mode", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -87,6 +88,7 @@ class LearnInfo(ctypes.Structure):
 
 
 PRECOND_NONE, PRECOND_BLOCK_JACOBI, PRECOND_LEARNED, PRECOND_OVERLAP = 0, 1, 2, 3
+SINGULAR_TOUCHING, SINGULAR_SELF = 0, 1
 LEARN_PARAMS = 1542
 
 
@@ -127,6 +129,7 @@ def lib():
             "nesa_default_solve_opts": (None, [P]),
             "nesa_solve": (I, [P, P, P, I, D, P, P]),
             "nesa_device_status": (I, [P]),
+            "nesa_inject_stall": (I, [P, I, ctypes.c_uint32]),
             "nesa_precond_setup": (I, [P]),
             "nesa_precond_apply": (I, [P, I, P, P, I]),
             "nesa_default_learn_opts": (None, [P]),
@@ -134,6 +137,7 @@ def lib():
             "nesa_precond_params": (I, [P, I, P]),
             "nesa_precond_features": (I, [P, P]),
             "nesa_precond_loss_grad": (I, [P, P, P, I, P, P]),
+            "nesa_build_batch": (I, [P, I, P, P, P]),
             "nesa_batch_create": (I, [P, I, P, P, P, I, P]),
             "nesa_batch_launch": (I, [P, P]),
             "nesa_batch_kernels": (I, [P, P]),
@@ -299,6 +303,30 @@ def plan(vertices, triangles, k, **params):
     return i.as_dict()
 
 
+def build_batch(meshes, ks, **params):
+    """Operators of several meshes built by one nesa_build_batch call: meshes is a list of
+    (vertices, triangles), ks their wavenumbers.  Returns a list of Nesa objects."""
+    n = len(meshes)
+    arrays = [(np.ascontiguousarray(v, dtype=np.float64), np.ascontiguousarray(t, dtype=np.int32))
+              for v, t in meshes]
+    m = (Mesh * n)(*[Mesh(len(v), len(t), v.ctypes.data, t.ctypes.data) for v, t in arrays])
+    k = (ctypes.c_double * n)(*[float(x) for x in ks])
+    p = default_params(**params)
+    h = (ctypes.c_void_p * n)()
+    _check(lib().nesa_build_batch(m, n, k, ctypes.byref(p), h))
+    out = []
+    for i in range(n):
+        g = Nesa.__new__(Nesa)
+        g._h = ctypes.c_void_p(h[i])
+        g.params = p
+        g.k = float(ks[i])
+        nn = ctypes.c_int64()
+        _check(lib().nesa_num_unknowns(g._h, ctypes.byref(nn)))
+        g.n = nn.value
+        out.append(g)
+    return out
+
+
 class Nesa:
     """One built operator (owns its device memory)."""
 
@@ -436,6 +464,15 @@ class Nesa:
         if check and st != OK:
             raise NesaError(st, str(info))
         return x, info
+
+    def device_status(self):
+        """Status of the context's kernels since the last call (OK or ERR_TIMEOUT); clears it."""
+        return lib().nesa_device_status(self._h)
+
+    def inject_stall(self, stall, wait_limit=0):
+        """Failure-detection hook: stall the tensor GEMM producers so its bounded waits
+        (wait_limit iterations; 0 = default) run out at the next mixed product."""
+        _check(lib().nesa_inject_stall(self._h, int(stall), int(wait_limit)))
 
     def profile_enable(self, on=True):
         _check(lib().nesa_profile_enable(self._h, 1 if on else 0))

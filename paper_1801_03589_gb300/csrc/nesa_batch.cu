@@ -6,6 +6,7 @@
 // work vectors exist and the tile widths of the tensor-core translations are tuned;
 // the capture then holds only kernel launches.  The graph binds the given x and y
 // buffers: a pass reads x and writes y of every member.
+#include <string>
 #include <vector>
 
 #include "nesa_device.cuh"
@@ -31,6 +32,24 @@ static void batch_free(nesa_batch *b) {
 }
 
 extern "C" {
+
+int nesa_build_batch(const nesa_mesh *meshes, int n, const double *k, const nesa_params *params, nesa_ctx **out) {
+  if (!meshes || !k || !params || !out || n < 1 || n > 1024) return NESA_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i) out[i] = nullptr;
+  for (int i = 0; i < n; ++i) {
+    const int st = nesa_build(&meshes[i], k[i], params, &out[i]);
+    if (st != NESA_OK) {
+      const std::string why = nesa_last_error();
+      for (int j = 0; j < i; ++j) {
+        nesa_destroy(out[j]);
+        out[j] = nullptr;
+      }
+      set_last_error("nesa_build_batch: mesh " + std::to_string(i) + ": " + why);
+      return st;
+    }
+  }
+  return NESA_OK;
+}
 
 int nesa_batch_create(nesa_ctx *const *ctxs, int n, const nesa_c128 *const *x, nesa_c128 *const *y, const int *nrhs,
                       int parts, nesa_batch **out) {

@@ -228,8 +228,10 @@ __device__ __forceinline__ bool leaves_touch(const int32_t *a, const int32_t *b)
 
 // M[9] (row-major over free vertices of the outer triangle ta and the inner tb).
 // singular: extraction of 1/(4 pi R) with the inner integral in closed form.
-__device__ void pair_block(int32_t ta, int32_t tb, bool singular, const int32_t *tris, const double *verts,
-                           const double *pts, const int32_t *pt_ijk, double k, cplx M[9], int *bad) {
+// must_near: the pair shares a vertex, so all 49 point pairs must lie in touching leaves.
+__device__ void pair_block(int32_t ta, int32_t tb, bool singular, bool must_near, const int32_t *tris,
+                           const double *verts, const double *pts, const int32_t *pt_ijk, double k, cplx M[9],
+                           int *bad) {
   const double *va[3], *vb[3];
   for (int c = 0; c < 3; ++c) {
     va[c] = verts + 3 * (int64_t)tris[3 * ta + c];
@@ -287,7 +289,7 @@ __device__ void pair_block(int32_t ta, int32_t tb, bool singular, const int32_t 
       }
     }
   }
-  if (singular && nnear != 49) atomicExch(bad, 1);
+  if (must_near && nnear != 49) atomicExch(bad, 1);
   const double ik2 = 1.0 / (k * k);
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) {
@@ -337,7 +339,7 @@ __device__ __forceinline__ bool share_vertex(const int32_t *a, const int32_t *b)
 // one thread per near triangle pair (CSR by outer triangle)
 __global__ void k_pair_matrices(cplx *out, const int64_t *tp_ptr, const int32_t *tp_col, int64_t nt,
                                 const int32_t *tris, const double *verts, const double *pts, const int32_t *pt_ijk,
-                                double k, int *bad) {
+                                double k, int self_only, int *bad) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= tp_ptr[nt]) return;
   // outer triangle: last t with tp_ptr[t] <= e
@@ -350,16 +352,18 @@ __global__ void k_pair_matrices(cplx *out, const int64_t *tp_ptr, const int32_t 
       hi = mid;
   }
   int32_t ta = (int32_t)lo, tb = tp_col[e];
-  bool sing = share_vertex(tris + 3 * ta, tris + 3 * tb);
+  // triangles sharing a vertex: singular (extraction) unless only self pairs are
+  const bool touching = share_vertex(tris + 3 * ta, tris + 3 * tb);
+  const bool sing = touching && (!self_only || ta == tb);
   cplx M[9];
   if (sing && ta > tb) {
     // computed with the lower-numbered triangle outside, then transposed: exact symmetry
     cplx Mt[9];
-    pair_block(tb, ta, true, tris, verts, pts, pt_ijk, k, Mt, bad);
+    pair_block(tb, ta, true, true, tris, verts, pts, pt_ijk, k, Mt, bad);
     for (int i = 0; i < 3; ++i)
       for (int j = 0; j < 3; ++j) M[3 * i + j] = Mt[3 * j + i];
   } else {
-    pair_block(ta, tb, sing, tris, verts, pts, pt_ijk, k, M, bad);
+    pair_block(ta, tb, sing, touching, tris, verts, pts, pt_ijk, k, M, bad);
     if (sing && ta == tb)
       for (int i = 0; i < 3; ++i)
         for (int j = i + 1; j < 3; ++j) {
@@ -466,6 +470,7 @@ static void compute_k(nesa_ctx *c, cublasHandle_t hb, cusolverDnHandle_t hs, con
 
 static void build_device(nesa_ctx *c, const nesa_params &p) {
   HostModel &h = c->h;
+  check_cuda(cudaGetDevice(&c->device), "current device");
   c->n = h.n;
   c->nt = h.nt;
   c->np = h.np;
@@ -500,7 +505,8 @@ static void build_device(nesa_ctx *c, const nesa_params &p) {
     check_cuda(cudaMalloc(&d_bad, sizeof(int)), "flag");
     check_cuda(cudaMemsetAsync(d_bad, 0, sizeof(int), st), "flag");
     k_pair_matrices<<<grid_for(ntp, 128), 128, 0, st>>>(pairM, d_tp_ptr, d_tp_col, h.nt, c->d_tris, c->d_verts,
-                                                        c->d_pts, d_pt_ijk, c->k, d_bad);
+                                                        c->d_pts, d_pt_ijk, c->k,
+                                                        p.singular_mode == NESA_SINGULAR_SELF ? 1 : 0, d_bad);
     check_cuda(cudaGetLastError(), "pair kernel");
     c->d_nz_ptr = upload(c, h.nz_ptr);
     c->d_nz_col = upload(c, h.nz_col);
@@ -703,7 +709,13 @@ static void free_ctx(nesa_ctx *c) {
 static bool build_args_ok(const nesa_mesh *mesh, double k, const nesa_params *params) {
   if (!mesh || !params || !mesh->vertices || !mesh->triangles || mesh->n_vertices < 3 || mesh->n_triangles < 1)
     return false;
-  return (k > 0.0) && (params->leaf_size > 0.0) && params->n_levels >= 1 && params->n_levels <= NESA_MAX_LEVELS &&
+  // leaf_size > 0 with n_levels in 1..MAX (or 0: the fewest levels spanning the mesh), or
+  // leaf_size = 0 with points_per_leaf > 0 (the depth rule of Sec. 3)
+  const bool by_size = params->leaf_size > 0.0 && params->points_per_leaf == 0 && params->n_levels >= 0 &&
+                       params->n_levels <= NESA_MAX_LEVELS;
+  const bool by_points = params->leaf_size == 0.0 && params->points_per_leaf > 0;
+  return (k > 0.0) && (by_size || by_points) &&
+         (params->singular_mode == NESA_SINGULAR_TOUCHING || params->singular_mode == NESA_SINGULAR_SELF) &&
          (params->q_mode == NESA_Q_FIXED || params->q_mode == NESA_Q_AUTO) && params->q_fixed >= 1 &&
          (params->precision == NESA_FP64 || params->precision == NESA_MIXED) && params->translate >= 0 &&
          params->translate <= 1 &&

@@ -72,6 +72,7 @@ struct DevLevel {
 struct nesa_ctx {
   nesa::HostModel h;
   cudaStream_t stream = nullptr;
+  int device = -1;               // CUDA device current at nesa_build (holds all device memory)
   double k = 0.0, eta = 0.0;
   int64_t n = 0, nt = 0, np = 0, nleaf = 0;
   int L = 0, l0 = 0;
@@ -130,6 +131,8 @@ struct nesa_ctx {
   void *tc_state = nullptr;      // tensor-core translation state (nesa_tc.cu)
   void *precond = nullptr;       // preconditioner state (nesa_precond.cu)
   bool tc_enabled = false;
+  int tc_stall = 0;                   // failure-detection hook (nesa_inject_stall)
+  uint32_t tc_wait_limit = 1u << 26;  // iterations of the tensor GEMM's bounded waits
   bool autotune = true;          // tune the GEMM tile width at the first product per chunk size
   int fixed_tn = 0;              // tile width used when the autotuner is off
   std::vector<void *> allocs;    // every device allocation owned by the context

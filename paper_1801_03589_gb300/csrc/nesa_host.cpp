@@ -130,7 +130,11 @@ void build_host_model(const nesa_mesh &mesh, double k, const nesa_params &p, Hos
     const double *a = &m.verts[3 * (size_t)tv[0]], *b = &m.verts[3 * (size_t)tv[1]], *c = &m.verts[3 * (size_t)tv[2]];
     double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]}, e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
     double cr[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
-    if (!(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2] > 0.0)) fail(NESA_ERR_MESH, "degenerate triangle");
+    // zero area, or an area at the rounding level of its edges (sine of the angle at a
+    // below 1e-12): the RWG functions would divide by it
+    const double c2 = cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2];
+    const double l1 = e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2], l2 = e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2];
+    if (!(c2 > 1e-24 * l1 * l2)) fail(NESA_ERR_MESH, "degenerate triangle");
   }
   build_rwg(m);
 
@@ -150,7 +154,6 @@ void build_host_model(const nesa_mesh &mesh, double k, const nesa_params &p, Hos
       }
 
   // root cube and leaf coordinates
-  m.L = p.n_levels - 1;
   double lo[3], hi[3];
   for (int x = 0; x < 3; ++x) {
     lo[x] = hi[x] = m.verts[x];
@@ -159,7 +162,50 @@ void build_host_model(const nesa_mesh &mesh, double k, const nesa_params &p, Hos
       hi[x] = std::max(hi[x], m.verts[3 * v + x]);
     }
   }
-  double root = p.leaf_size * std::ldexp(1.0, m.L);
+  const double extent = std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
+  if (!(extent > 0.0)) fail(NESA_ERR_MESH, "mesh has no extent");
+  double root = 0.0;
+  if (p.points_per_leaf > 0) {
+    // Sec. 3: subdivide while the groups hold at least P sources on average.  The root
+    // is the bounding cube; the leaf level is the deepest l <= 19 whose occupied boxes
+    // average >= P points.  Boxes of level l are the depth-19 keys shifted by 3 (19 - l)
+    // (dividing by a power of two is exact, so these are the level's own coordinates).
+    constexpr int DMAX = NESA_MAX_LEVELS - 1;
+    root = extent;
+    double org[3];
+    for (int x = 0; x < 3; ++x) org[x] = 0.5 * (lo[x] + hi[x]) - 0.5 * root;
+    const double wd = root / std::ldexp(1.0, DMAX);
+    const int32_t nbd = 1 << DMAX;
+    std::vector<uint64_t> kd(m.np);
+    for (int64_t q = 0; q < m.np; ++q) {
+      int32_t c[3];
+      for (int x = 0; x < 3; ++x) {
+        double f = std::floor((m.pts[3 * q + x] - org[x]) / wd);
+        c[x] = f < 0.0 ? 0 : (f > nbd - 1 ? nbd - 1 : (int32_t)f);
+      }
+      kd[q] = morton(c[0], c[1], c[2]);
+    }
+    std::sort(kd.begin(), kd.end());
+    m.L = 0;
+    for (int l = 0; l <= DMAX; ++l) {
+      const int sh = 3 * (DMAX - l);
+      int64_t nbox = 0;
+      for (int64_t q = 0; q < m.np; ++q)
+        if (q == 0 || (kd[q] >> sh) != (kd[q - 1] >> sh)) ++nbox;
+      if ((double)m.np >= (double)p.points_per_leaf * (double)nbox)
+        m.L = l;
+      else
+        break;
+    }
+  } else {
+    if (p.n_levels > 0) {
+      m.L = p.n_levels - 1;
+    } else {  // the fewest levels whose root cube spans the bounding box
+      m.L = 0;
+      while (m.L < NESA_MAX_LEVELS - 1 && p.leaf_size * std::ldexp(1.0, m.L) < extent) ++m.L;
+    }
+    root = p.leaf_size * std::ldexp(1.0, m.L);
+  }
   for (int x = 0; x < 3; ++x) m.origin[x] = 0.5 * (lo[x] + hi[x]) - 0.5 * root;
   const double wl = root / std::ldexp(1.0, m.L);
   const int32_t nb = 1 << m.L;

@@ -955,6 +955,13 @@ int nesa_device_status(nesa_ctx *c) {
   return NESA_OK;
 }
 
+int nesa_inject_stall(nesa_ctx *c, int stall, uint32_t wait_limit) {
+  if (!c || (stall != 0 && stall != 1)) return NESA_ERR_INVALID_ARG;
+  c->tc_stall = stall;
+  c->tc_wait_limit = wait_limit ? wait_limit : (1u << 26);
+  return NESA_OK;
+}
+
 int nesa_matvec(nesa_ctx *c, const nesa_c128 *x, nesa_c128 *y, int nrhs) {
   return nesa_matvec_parts(c, x, y, nrhs, NESA_PART_ALL);
 }

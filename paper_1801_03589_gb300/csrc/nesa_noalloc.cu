@@ -14,7 +14,9 @@
 // The array is NESA_NOALLOC_SCRATCH_BYTES (32 MiB) on every GPU that loads the
 // library, held until the process exits.  Its address is looked up once per device
 // (cudaGetSymbolAddress, with that device current) by the first call made on that
-// device; make that first call before starting any stream capture.  All calls share
+// device; make that first call before starting any stream capture.  Call it with the
+// context's device current: another current device is refused (NESA_ERR_INVALID_ARG),
+// since its copy of the array is not the one the kernels should use.  All calls share
 // the array and leave their data in it: two calls whose kernels overlap on the GPU
 // (different streams, or different contexts used concurrently) race on it.  Nothing
 // in the array needs to start at zero: every kernel writes each work-vector element
@@ -54,7 +56,23 @@ static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 using namespace nesa;
 
 extern "C" int nesa_matvec_noalloc(nesa_ctx *c, const nesa_c128 *x, nesa_c128 *y, int nrhs) {
-  if (!c || !x || !y || nrhs < 1 || nrhs > 64) return NESA_ERR_INVALID_ARG;
+  if (!c || !x || !y || nrhs < 1 || nrhs > 64) {
+    set_last_error("nesa_matvec_noalloc: null pointer or nrhs outside 1..64");
+    return NESA_ERR_INVALID_ARG;
+  }
+  // The scratch address is looked up on the current device; the kernels run on the
+  // context's device.  They must be the same, or the kernels would reach into another
+  // GPU's copy of the array.
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) {
+    set_last_error("nesa_matvec_noalloc: cudaGetDevice failed");
+    return NESA_ERR_CUDA;
+  }
+  if (cur != c->device) {
+    set_last_error("nesa_matvec_noalloc: the current device (" + std::to_string(cur) +
+                   ") is not the context's device (" + std::to_string(c->device) + "); make it current first");
+    return NESA_ERR_INVALID_ARG;
+  }
   // bytes of the work vectors s_l and o_l for l0..L
   size_t need = 0;
   for (int l = c->l0; l <= c->L; ++l)
@@ -89,8 +107,10 @@ extern "C" int nesa_matvec_noalloc(nesa_ctx *c, const nesa_c128 *x, nesa_c128 *y
     launch_matvec(c, (const cplx *)x, (cplx *)y, nrhs, NESA_PART_ALL);
     check_cuda(cudaGetLastError(), "matvec launch");
   } catch (const Error &e) {
+    set_last_error(e.what);
     status = e.status;
   } catch (const std::bad_alloc &) {
+    set_last_error("host allocation failed");
     status = NESA_ERR_OOM;
   }
   for (int l = c->l0; l <= c->L; ++l) {

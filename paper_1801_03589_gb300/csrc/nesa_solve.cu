@@ -236,6 +236,13 @@ __global__ void k_cycle_start(cplx *g, int m, const double *beta, const double *
   if (r >= nrhs) return;
   for (int i = 0; i <= m; ++i) g[(int64_t)r * (m + 1) + i] = make_double2(i == 0 ? beta[r] : 0.0, 0.0);
   steps[r] = 0;
+  // a NaN/Inf in b or in the residual stops the right-hand side with a numeric error
+  // (a NaN norm would otherwise fail the test bnorm > 0 and read as a zero residual)
+  if (!isfinite(bnorm[r]) || !isfinite(beta[r])) {
+    est[r] = NAN;
+    state[r] = 3;
+    return;
+  }
   const double e = bnorm[r] > 0.0 ? beta[r] / bnorm[r] : 0.0;
   est[r] = e;
   state[r] = (e <= tol) ? 1 : (isfinite(e) ? 0 : 3);
@@ -479,6 +486,7 @@ static int gmres_run(nesa_ctx *c, const cplx *b, cplx *x, int nrhs, double tol, 
     I.iterations += total;
     for (int r = 0; r < nrhs; ++r) {
       double rr = bn[r] > 0.0 ? rn[r] / bn[r] : 0.0;
+      if (!std::isfinite(bn[r]) || !std::isfinite(rn[r])) rr = NAN;
       I.rel_residual[r] = rr;
       if (!std::isfinite(rr)) status = NESA_ERR_NUMERIC;
       // the true residual decides convergence (the estimate can be slightly optimistic)
@@ -524,7 +532,10 @@ static int refine_run(nesa_ctx *c, const cplx *b, cplx *x, int nrhs, double tol,
     double emax = 0.0;
     for (int r = 0; r < nrhs; ++r) {
       double e = bn[r] > 0.0 ? rn[r] / bn[r] : 0.0;
-      if (!std::isfinite(e)) return NESA_ERR_NUMERIC;
+      if (!std::isfinite(bn[r]) || !std::isfinite(rn[r]) || !std::isfinite(e)) {
+        I.rel_residual[r] = NAN;
+        return NESA_ERR_NUMERIC;
+      }
       done &= e <= tol;
       emax = std::max(emax, e);
     }

@@ -313,6 +313,8 @@ static void launch_gemm(nesa_ctx *c, const TcGemm &g, const __nv_bfloat16 *B_hi,
   if (g.nwork == 0) return;
   (void)rc;
   tc::GemmArgs a{g.work, g.wsrc, g.wdst, g.nwork, g.A, B_hi, B_lo, P, g.q, g.nk16, g.nmt, S->err};
+  a.wait_limit = c->tc_wait_limit;
+  a.stall = c->tc_stall;
   const unsigned grid = (unsigned)std::min<int64_t>(g.nwork, S->nsm);
   cudaStream_t st = c->stream;
   switch (g.work_tn) {
@@ -385,6 +387,8 @@ static void launch_gemm_seg(nesa_ctx *c, const TcGemm &g, const __nv_bfloat16 *B
   const int chunk = std::max(1, 32 / g.nk16);
   tc::GemmArgs a{g.swork, nullptr, g.swdst, g.snwork, g.A, B_hi, B_lo, out, g.q, g.nk16, g.nmt, S->err,
                  g.sseg, accum ? 1 : 0, chunk};
+  a.wait_limit = c->tc_wait_limit;
+  a.stall = c->tc_stall;
   const unsigned grid = (unsigned)std::min<int64_t>(g.snwork, S->nsm);
   tc::k_tc_gemm<SEG_TN, true><<<grid, tc::THREADS, tc::smem_bytes<SEG_TN>(), c->stream>>>(a);
 }

@@ -66,3 +66,20 @@ def test_reference_arm_nonzero_rank_exits_without_work():
     import bench
     args = argparse.Namespace(steps=1, warmup=0)
     assert bench.run_reference(args, world=2, rank=1) == 0
+
+
+def test_all_core_oracle_timing_runs_on_a_spawned_pool():
+    """The CPU baseline's all-core leg: two spawned workers, each with its own oracle,
+    run one task per worker for every sampled stage of the product."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from workloads import get_config
+    pool = bench.OraclePool("tiny", 2)
+    try:
+        o = bench.build_oracle(get_config("tiny"))
+        sec, parts, desc = pool.sampled_product(o, n_leaves=2, n_boxes=2, n_rows=4, seed=5)
+    finally:
+        pool.close()
+    assert sec > 0 and "2 worker processes" in desc
+    assert set(parts) == {"sources", "near", "radiation", "source_transfer", "translation", "reception", "testing"}
+    assert all(v >= 0 for v in parts.values())

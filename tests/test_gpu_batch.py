@@ -78,3 +78,28 @@ def test_batch_members_keep_their_right_hand_sides():
     b.close()
     y1 = g.matvec(x[:1].contiguous(), parts=parts)
     assert float((y1[0] - same[0]).abs().max() / same[0].abs().max()) < 1e-5
+
+
+def test_build_batch_then_one_graph_pass():
+    """nesa_build_batch builds every mesh's operator in one call; each context equals a
+    separately built one (same product bits), and the contexts form a batch pass."""
+    import paper_1801_03589_gb300 as nesa
+    names = ("tiny", "C1", "C1b")
+    cfgs = [get_config(n) for n in names]
+    members = nesa.build_batch([(c["vertices"], c["triangles"]) for c in cfgs], [c["k"] for c in cfgs],
+                               leaf_size=0.25, n_levels=0)
+    for c, m in zip(cfgs, members):
+        alone = nesa.Nesa(c["vertices"], c["triangles"], c["k"], leaf_size=0.25, n_levels=0)
+        x = torch.from_numpy(random_coefficients(m.n, 1, seed=98)).cuda()
+        assert torch.equal(m.matvec(x), alone.matvec(x))
+        alone.close()
+    xs = [torch.from_numpy(random_coefficients(m.n, 1, seed=99 + i)).cuda() for i, m in enumerate(members)]
+    ys = [torch.zeros_like(x) for x in xs]
+    b = nesa.Batch(members, xs, ys)
+    b.launch()
+    torch.cuda.synchronize()
+    for m, x, y in zip(members, xs, ys):
+        assert float((y - m.matvec(x)).abs().max()) == 0.0
+    b.close()
+    for m in members:
+        m.close()

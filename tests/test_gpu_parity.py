@@ -138,3 +138,44 @@ def test_invalid_arguments_rejected():
     with pytest.raises(nesa.NesaError) as e:
         nesa.Nesa(c["vertices"], c["triangles"], -1.0)
     assert e.value.status == nesa.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("name,P", [("C1", 100), ("C1b", 150)])
+def test_points_per_leaf_build_bit_exact_and_product(name, P):
+    """The paper's depth rule (Sec. 3, points_per_leaf = P with leaf_size = 0): the leaf
+    of every quadrature point equals the oracle's tree built with the same rule, and the
+    FP64 product matches the oracle's NESA on that tree."""
+    import paper_1801_03589_gb300 as nesa
+    c = get_config(name)
+    o = NesaOracle(c["vertices"], c["triangles"], c["k"], 0.0, 0, points_per_leaf=P)
+    g = nesa.Nesa(c["vertices"], c["triangles"], c["k"], leaf_size=0.0, n_levels=0, points_per_leaf=P)
+    info = g.info()
+    assert info["n_levels"] == o.L + 1 and info["l0"] == o.l0
+    assert np.array_equal(g.export_point_leaf(), o.tree.point_leaf_ijk)
+    x = random_coefficients(o.n, 1, seed=17)[0]
+    y = g.matvec(torch.from_numpy(x).cuda().view(1, -1)).cpu().numpy()[0]
+    rows = np.unique(np.linspace(0, o.n - 1, 24).astype(np.int64))
+    assert rel(y[rows], o.matvec_rows(x, rows)) < TOL
+    g.close()
+
+
+@pytest.mark.parametrize("name", ["tiny", "C1"])
+def test_self_only_singular_mode_parity(name):
+    """singular_mode = self (extraction for T = T' only): near and whole FP64 products
+    against the oracle built with the same rule."""
+    import paper_1801_03589_gb300 as nesa
+    c = get_config(name)
+    o = NesaOracle(c["vertices"], c["triangles"], c["k"], c["leaf_size"], c["n_levels"], singular_mode="self")
+    g = nesa.Nesa(c["vertices"], c["triangles"], c["k"], leaf_size=c["leaf_size"], n_levels=c["n_levels"],
+                  singular_mode=nesa.SINGULAR_SELF)
+    x = random_coefficients(o.n, 1, seed=18)[0]
+    xd = torch.from_numpy(x).cuda().view(1, -1)
+    yn = g.matvec(xd, parts=nesa.PART_NEAR).cpu().numpy()[0]
+    assert rel(yn, o.near_matrix() @ x) < TOL
+    y = g.matvec(xd).cpu().numpy()[0]
+    assert rel(y, o.matvec(x)) < TOL
+    # and it differs from the default rule (the mode is not ignored)
+    _, _, gt = pair(name)
+    yt = gt.matvec(xd, parts=nesa.PART_NEAR).cpu().numpy()[0]
+    assert rel(yn, yt) > 1e-4
+    g.close()

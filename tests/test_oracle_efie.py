@@ -110,3 +110,24 @@ def test_nesa_matches_dense_c1b_rows():
     dense = efie_rows(c["vertices"], c["triangles"], o.rwg, c["k"], rows=rows) @ x
     err = np.linalg.norm(o.matvec_rows(x, rows) - dense) / np.linalg.norm(dense)
     assert err < 1e-4
+
+
+def test_self_only_singular_mode():
+    """singular_mode 'self' (extraction for T = T' only) changes exactly the entries whose
+    supports contain two distinct triangles sharing a vertex; every other entry is the
+    same number.  Z stays symmetric to rounding, and the plain 7x7 rule on adjacent
+    triangles stays within a few per cent of the extracted value overall."""
+    from oracle.rwg import build_rwg
+    c = get_config("tiny")
+    r = build_rwg(c["vertices"], c["triangles"])
+    Zt = efie_rows(c["vertices"], c["triangles"], r, c["k"])
+    Zs = efie_rows(c["vertices"], c["triangles"], r, c["k"], singular_mode="self")
+    T = c["triangles"]
+    shares = [[len(set(T[a]) & set(T[b])) > 0 and a != b for b in range(len(T))] for a in range(len(T))]
+    n = r["n"]
+    adj = np.array([[any(shares[a][b] for a in r["tri"][m] for b in r["tri"][k]) for k in range(n)] for m in range(n)])
+    d = np.abs(Zs - Zt)
+    assert d[~adj].max() == 0.0
+    assert np.count_nonzero(d[adj]) > 0.9 * adj.sum()
+    assert np.abs(Zs - Zs.T).max() <= 1e-13 * np.abs(Zs).max()
+    assert np.linalg.norm(Zs - Zt) / np.linalg.norm(Zt) < 0.1

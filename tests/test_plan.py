@@ -60,3 +60,35 @@ def test_plan_rejects_bad_arguments():
         bad = np.array(c["triangles"]).copy()
         bad[0, 0] = len(c["vertices"]) + 5
         nesa.plan(c["vertices"], bad, c["k"], leaf_size=c["leaf_size"], n_levels=c["n_levels"])
+
+
+@pytest.mark.parametrize("name,P", [("C1", 100), ("C1b", 150), ("C3c", 120)])
+def test_points_per_leaf_depth_rule_matches_oracle(name, P):
+    """The paper's depth rule (Sec. 3: subdivide while the groups average at least P
+    sources), chosen by leaf_size = 0 and points_per_leaf = P: the library's host model
+    and the oracle's tree pick the same depth and the same boxes and lists."""
+    import paper_1801_03589_gb300 as nesa
+    from oracle.tree import Tree
+    c = get_config(name)
+    info = nesa.plan(c["vertices"], c["triangles"], c["k"], leaf_size=0.0, n_levels=0, points_per_leaf=P)
+    t = Tree(c["vertices"], c["triangles"], 0.0, 0, points_per_leaf=P)
+    npts = 7 * len(c["triangles"])
+    assert npts >= P * len(t.boxes[t.L])  # the rule itself, on the oracle's boxes
+    deeper = Tree(c["vertices"], c["triangles"], t.width(t.L) / 2, t.L + 2)
+    assert npts < P * len(deeper.boxes[deeper.L])
+    assert info["n_levels"] == t.L + 1 and info["l0"] == t.l0
+    for l in range(t.L + 1):
+        assert info["n_boxes"][l] == len(t.boxes[l])
+    for l in range(t.l0, t.L + 1):
+        assert info["n_interactions"][l] == sum(len(t.interaction_list(l, b)) for b in t.boxes[l])
+
+
+def test_auto_levels_from_leaf_size():
+    """n_levels = 0 with a leaf size: the fewest levels whose root cube spans the mesh."""
+    import paper_1801_03589_gb300 as nesa
+    from oracle.tree import Tree
+    c = get_config("C1b")  # r = 1 sphere: extent 2, leaf 0.25 -> root 2 = 0.25 * 2^3
+    info = nesa.plan(c["vertices"], c["triangles"], c["k"], leaf_size=0.25, n_levels=0)
+    t = Tree(c["vertices"], c["triangles"], 0.25, 0)
+    assert info["n_levels"] == t.L + 1 == 4
+    assert info["n_boxes"][t.L] == len(t.boxes[t.L])

@@ -36,18 +36,41 @@ def _build(name):
 
 @pytest.mark.parametrize("name,nrhs", [("tiny", 1), ("C1b", 2)])
 def test_noalloc_matches_matvec_twice(name, nrhs):
+    """On a fresh context (no work vectors allocated yet) the no-allocation product
+    comes first and must leave the context's device memory unchanged; the reference
+    product comes after it.  Two calls in a row with different inputs."""
     nesa, f = _entry()
     g = _build(name)
     torch.cuda.synchronize()
     for call in range(2):
         x = torch.from_numpy(random_coefficients(g.n, nrhs, seed=40 + call)).cuda()
-        ref = g.matvec(x)
         y = torch.full_like(x, complex(np.nan, np.nan))
+        torch.cuda.synchronize()
+        before = g.info()["device_bytes"]
         assert f(g._h, x.data_ptr(), y.data_ptr(), nrhs) == nesa.OK
         torch.cuda.synchronize()
+        assert g.info()["device_bytes"] == before
+        ref = g.matvec(x)
         yr, rr = y.cpu().numpy(), ref.cpu().numpy()
         assert np.all(np.isfinite(yr))
         assert np.linalg.norm(yr - rr) <= TOL * np.linalg.norm(rr)
+    g.close()
+
+
+def test_noalloc_reports_why_it_refused():
+    """A refusal inside the product (here: the context belongs to a batch captured with
+    another number of right-hand sides) returns the status and leaves its reason in
+    nesa_last_error."""
+    nesa, f = _entry()
+    g = _build("tiny")
+    x1 = torch.from_numpy(random_coefficients(g.n, 1, seed=44)).cuda()
+    y1 = torch.empty_like(x1)
+    b = nesa.Batch([g], [x1], [y1])
+    x2 = torch.zeros((2, g.n), dtype=torch.complex128, device="cuda")
+    y2 = torch.zeros_like(x2)
+    assert f(g._h, x2.data_ptr(), y2.data_ptr(), 2) == nesa.ERR_INVALID_ARG
+    assert b"batch" in nesa.lib().nesa_last_error()
+    b.close()
     g.close()
 
 
