@@ -346,6 +346,14 @@ class OraclePool:
         return sum(parts.values()), parts, desc
 
 
+def host_cores():
+    """Cores this process may run on (its affinity mask; os.cpu_count() counts the whole host)."""
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
 def build_oracle(cfg):
     from oracle.nesa import NesaOracle
     return NesaOracle(cfg["vertices"], cfg["triangles"], cfg["k"], cfg["leaf_size"], cfg["n_levels"])
@@ -357,7 +365,7 @@ def run_reference(args, world, rank):
         return 0
     cfg = get_config(CONFIG)
     o = build_oracle(cfg)
-    procs = os.cpu_count() or 1
+    procs = host_cores()
     pool = OraclePool(CONFIG, procs)
     try:
         for _ in range(args.warmup):
@@ -684,7 +692,7 @@ def run_ours(args, world, rank, local):
         o = build_oracle(cfg)
         xo = random_coefficients(n, 1, seed=2024)[0]
         sec1, parts1, desc1 = oracle_sampled_product(o, xo, seed=3)
-        procs = os.cpu_count() or 1
+        procs = host_cores()
         pool = OraclePool(CONFIG if args.workload == CONFIG else args.workload, procs)
         try:
             secp, partsp, descp = pool.sampled_product(o, seed=3)
