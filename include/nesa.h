@@ -113,7 +113,22 @@ typedef struct {
  *   n_levels    with leaf_size > 0, 0 selects the fewest levels whose root cube
  *               (leaf_size * 2^(levels-1)) spans the largest side of the bounding box
  *   singular_mode  NESA_SINGULAR_TOUCHING (default) or NESA_SINGULAR_SELF
+ *   translation_tables  NESA_TABLES_AUTO (default), NESA_TABLES_STORED or
+ *               NESA_TABLES_GENERATED: whether the translation matrices D_l(o) of Eq. 12
+ *               are kept in device memory per offset or built from the equivalent points
+ *               when a product needs them (D_l(o)_ij = g(|E_i + o w_l - E_j|), a plain
+ *               Green's-function matrix).  Generated, the FP64 product fills them into a
+ *               bounded work buffer (at most 64 offsets and about 1.5 GB at a time) just
+ *               before the translations that use them, and the tensor-core product forms
+ *               each BF16 tile in the GEMM's producer warps (FP32 arithmetic, phase taken
+ *               relative to the offset's centre distance).  AUTO generates the FP64 tables
+ *               of a level above 6 GB, and the tensor tiles of such levels and of levels
+ *               whose offsets serve fewer than 32 pairs each (the coarse levels, where a
+ *               stored tile would be streamed from DRAM for little reuse).
  */
+#define NESA_TABLES_AUTO 0      /* translation matrices: generated where large or little reused */
+#define NESA_TABLES_STORED 1    /* every translation matrix stored */
+#define NESA_TABLES_GENERATED 2 /* every translation matrix generated when used */
 #define NESA_SINGULAR_TOUCHING 0 /* singularity extraction for every triangle pair sharing a vertex */
 #define NESA_SINGULAR_SELF 1     /* extraction for T = T' only; pairs sharing a vertex or an edge use the
                                     plain 7 x 7 rule (its nodes are interior, R > 0); Z symmetric to rounding */
@@ -131,6 +146,8 @@ typedef struct {
   int32_t tile_n;
   int32_t points_per_leaf;
   int32_t singular_mode;
+  int32_t translation_tables;
+  int32_t reserved;
 } nesa_params;
 
 /* Sizes of a built operator (host struct filled by nesa_get_info). */

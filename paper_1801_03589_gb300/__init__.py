@@ -41,7 +41,8 @@ class Params(ctypes.Structure):
                 ("q_fixed", ctypes.c_int32), ("precision", ctypes.c_int32), ("q_digits", ctypes.c_double),
                 ("rho_eq", ctypes.c_double), ("rho_test", ctypes.c_double), ("pinv_eps", ctypes.c_double),
                 ("translate", ctypes.c_int32), ("tile_n", ctypes.c_int32), ("points_per_leaf", ctypes.c_int32),
-                ("singular_mode", ctypes.c_int32)]
+                ("singular_mode", ctypes.c_int32), ("translation_tables", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -89,6 +90,7 @@ class LearnInfo(ctypes.Structure):
 
 PRECOND_NONE, PRECOND_BLOCK_JACOBI, PRECOND_LEARNED, PRECOND_OVERLAP = 0, 1, 2, 3
 SINGULAR_TOUCHING, SINGULAR_SELF = 0, 1
+TABLES_AUTO, TABLES_STORED, TABLES_GENERATED = 0, 1, 2
 LEARN_PARAMS = 1542
 
 

@@ -547,12 +547,46 @@ static void build_device(nesa_ctx *c, const nesa_params &p) {
       k_green_matrix<<<grid_for(2LL * q * q, 256), 256, 0, st>>>(A, 2 * q, d_T, 2 * q, d_E, q, c->k, 0, 0, 0, 0, 0, 0);
       dl.K = (cplx *)dalloc(c, sizeof(cplx) * 2 * (size_t)q * q);
       compute_k(c, hb, hs, A, q, p.pinv_eps, dl.K);
-      // D_l for every offset in use
+      // D_l for every offset in use: stored, or generated by the products (Eq. 12's
+      // matrices are Green's-function matrices between equivalent points)
       int32_t *d_off = upload(c, hl.offsets);
-      dl.D = (cplx *)dalloc(c, sizeof(cplx) * (size_t)dl.noff * q * q);
-      k_translation_fill<<<grid_for(dl.noff * q * (int64_t)q, 256), 256, 0, st>>>(dl.D, d_E, q, d_off, dl.noff,
-                                                                                   hl.width, c->k);
-      check_cuda(cudaGetLastError(), "translation fill");
+      const double table_bytes = sizeof(cplx) * (double)dl.noff * q * q;
+      dl.gen = c->tables_mode == NESA_TABLES_GENERATED || (c->tables_mode == NESA_TABLES_AUTO && table_bytes > 6e9);
+      if (!dl.gen) {
+        dl.D = (cplx *)dalloc(c, sizeof(cplx) * (size_t)dl.noff * q * q);
+        k_translation_fill<<<grid_for(dl.noff * q * (int64_t)q, 256), 256, 0, st>>>(dl.D, d_E, q, d_off, dl.noff,
+                                                                                     hl.width, c->k);
+        check_cuda(cudaGetLastError(), "translation fill");
+      } else {
+        dl.E = d_E;
+        dl.offs = d_off;
+        // chunks of offset slots whose tables fit a ~1.5 GB work buffer (at most 64)
+        const double per_slot = sizeof(cplx) * (double)q * q;
+        dl.chunk_slots = (int)std::max<double>(1.0, std::min<double>(64.0, std::floor(1.5e9 / per_slot)));
+        dl.chunk_slots = (int)std::min<int64_t>(dl.chunk_slots, std::max<int64_t>(1, dl.noff));
+        dl.nchunk = (int)((dl.noff + dl.chunk_slots - 1) / dl.chunk_slots);
+        std::vector<int32_t> cptr((size_t)dl.nchunk * (dl.nbox + 1)), csrc(dl.nil), cslot(dl.nil);
+        int64_t at = 0;
+        for (int ch = 0; ch < dl.nchunk; ++ch) {
+          const int32_t s0 = ch * dl.chunk_slots, s1 = s0 + dl.chunk_slots;
+          int32_t *ptr = cptr.data() + (size_t)ch * (dl.nbox + 1);
+          for (int64_t a = 0; a < dl.nbox; ++a) {
+            ptr[a] = (int32_t)at;
+            for (int32_t e = hl.il_ptr[a]; e < hl.il_ptr[a + 1]; ++e)
+              if (hl.il_slot[e] >= s0 && hl.il_slot[e] < s1) {
+                csrc[at] = hl.il_src[e];
+                cslot[at] = hl.il_slot[e] - s0;
+                ++at;
+              }
+          }
+          ptr[dl.nbox] = (int32_t)at;
+        }
+        if (at != dl.nil) fail(NESA_ERR_INVALID_ARG, "translation chunks do not cover the interaction lists");
+        dl.cil_ptr = upload(c, cptr);
+        dl.cil_src = upload(c, csrc);
+        dl.cil_slot = upload(c, cslot);
+        dl.Dw = (cplx *)dalloc(c, sizeof(cplx) * (size_t)dl.chunk_slots * q * q);
+      }
       // C_l (l > l0): K_{l-1} G(T_{l-1}, E_l + delta)
       if (l > h.l0) {
         const int qp = h.lev[l - 1].q;
@@ -716,6 +750,7 @@ static bool build_args_ok(const nesa_mesh *mesh, double k, const nesa_params *pa
   const bool by_points = params->leaf_size == 0.0 && params->points_per_leaf > 0;
   return (k > 0.0) && (by_size || by_points) &&
          (params->singular_mode == NESA_SINGULAR_TOUCHING || params->singular_mode == NESA_SINGULAR_SELF) &&
+         params->translation_tables >= NESA_TABLES_AUTO && params->translation_tables <= NESA_TABLES_GENERATED &&
          (params->q_mode == NESA_Q_FIXED || params->q_mode == NESA_Q_AUTO) && params->q_fixed >= 1 &&
          (params->precision == NESA_FP64 || params->precision == NESA_MIXED) && params->translate >= 0 &&
          params->translate <= 1 &&
@@ -771,6 +806,8 @@ int nesa_build(const nesa_mesh *mesh, double k, const nesa_params *params, nesa_
   auto t0 = std::chrono::steady_clock::now();
   nesa_ctx *c = new nesa_ctx();
   c->k = k;
+  c->tables_mode = params->translation_tables;
+  c->translate_engine = params->translate;
   c->eta = 4e-7 * 3.14159265358979323846 * 299792458.0;
   try {
     build_host_model(*mesh, k, *params, c->h);
@@ -896,8 +933,23 @@ int nesa_export_op(const nesa_ctx *c, int which, int level, int index, void *buf
       std::memcpy(buf, c->h.lev[level].offsets.data() + 3 * (size_t)index, bytes);
       return NESA_OK;
     }
-    src = d.D + (int64_t)index * d.q * d.q;
     need = sizeof(cplx) * (size_t)d.q * d.q;
+    if (d.gen) {  // generated level: fill the one block into a temporary buffer
+      if (bytes != need) return NESA_ERR_INVALID_ARG;
+      cplx *tmp = nullptr;
+      if (cudaMalloc(&tmp, need) != cudaSuccess) return NESA_ERR_OOM;
+      int st = NESA_OK;
+      try {
+        fill_translations(const_cast<nesa_ctx *>(c), level, index, 1, tmp);
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess || cudaMemcpy(buf, tmp, need, cudaMemcpyDeviceToHost) != cudaSuccess)
+          st = NESA_ERR_CUDA;
+      } catch (const Error &e) {
+        st = e.status;
+      }
+      cudaFree(tmp);
+      return st;
+    }
+    src = d.D + (int64_t)index * d.q * d.q;
   } else if (which == NESA_OP_C) {
     if (level == c->l0 || index >= 8) return NESA_ERR_INVALID_ARG;
     const int qp = c->lev[level - 1].q;

@@ -62,6 +62,17 @@ struct DevLevel {
   cplx *C = nullptr;   // [8][q_{l-1}][q] column-major (rows: parent's sources)
   cplx *Ct = nullptr;  // [8][q][q_{l-1}] column-major (transpose of C)
   cplx *K = nullptr;   // [q][2q] column-major
+  // generated translations (D == nullptr): equivalent points and offsets on the device,
+  // and the pairs grouped in chunks of chunk_slots offset slots: chunk c's pairs by
+  // target in cil_ptr[c (nbox + 1) ..], slots relative to the chunk's first slot; D of a
+  // chunk is filled into Dw (FP64 product) or Dw32 (complex64 engine) before use
+  bool gen = false;
+  double *E = nullptr;
+  int32_t *offs = nullptr;
+  int chunk_slots = 0, nchunk = 0;
+  int32_t *cil_ptr = nullptr, *cil_src = nullptr, *cil_slot = nullptr;
+  cplx *Dw = nullptr;
+  cplxf *Dw32 = nullptr;
   cplx *s = nullptr;   // workspace [nbox][4*nrhs][q] outgoing equivalent sources
   cplx *o = nullptr;   // workspace [nbox][4*nrhs][q] incoming field at the equivalent points
 };
@@ -131,6 +142,8 @@ struct nesa_ctx {
   void *tc_state = nullptr;      // tensor-core translation state (nesa_tc.cu)
   void *precond = nullptr;       // preconditioner state (nesa_precond.cu)
   bool tc_enabled = false;
+  int tables_mode = NESA_TABLES_AUTO; // nesa_params.translation_tables
+  int translate_engine = NESA_TRANSLATE_FP32;  // nesa_params.translate
   int tc_stall = 0;                   // failure-detection hook (nesa_inject_stall)
   uint32_t tc_wait_limit = 1u << 26;  // iterations of the tensor GEMM's bounded waits
   bool autotune = true;          // tune the GEMM tile width at the first product per chunk size
@@ -146,6 +159,10 @@ void check_cuda(cudaError_t e, const char *what);
 void launch_matvec(nesa_ctx *c, const cplx *x, cplx *y, int nrhs, int parts);
 // converted copies of the operator for the mixed-precision product
 void build_mixed(nesa_ctx *c);
+// D_l(o) for the offset slots slot0 .. slot0 + ns - 1 of a generated level, into D
+// ([ns][q][q] column-major, complex128 or complex64), on the context's stream
+void fill_translations(nesa_ctx *c, int level, int64_t slot0, int64_t ns, cplx *D);
+void fill_translations(nesa_ctx *c, int level, int64_t slot0, int64_t ns, cplxf *D);
 // an event from the context's pool (stage timing)
 cudaEvent_t take_event(nesa_ctx *c);
 // tensor-core translations of the mixed product (nesa_tc.cu)

@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(512) k_translate(CT *__restrict__ o, const CT 
                                                    const int32_t *__restrict__ il_slot, const CT *__restrict__ op,
                                                    const CT *__restrict__ Ct, const int32_t *__restrict__ parent,
                                                    const int32_t *__restrict__ octant, int nrhs, int q, int qp,
-                                                   int tr) {
+                                                   int tr, int accum) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CT *col = (CT *)smem_raw;  // [4][JC]
   const int32_t a = blockIdx.x;
@@ -270,8 +270,10 @@ __global__ void __launch_bounds__(512) k_translate(CT *__restrict__ o, const CT 
   const int i = tile * tr + threadIdx.x % tr;
   const bool active = ch < 4 && i < q;
   const int32_t e0 = il_ptr[a], e1 = il_ptr[a + 1];
+  if (accum && e0 == e1) return;  // a later chunk of offsets without pairs of this box
   for (int r = 0; r < nrhs; ++r) {
     CT acc = {0, 0};
+    if (accum && active) acc = o[((int64_t)a * 4 * nrhs + 4 * r + ch) * q + i];  // earlier chunks
     if (op)  // potential transfer from the parent (Eq. 13): o_a += C^T o_P
       matvec_chunked(acc, col, op + ((int64_t)parent[a] * 4 * nrhs + 4 * r) * qp,
                      Ct + (int64_t)octant[a] * q * qp + i, q, qp, ch, active);
@@ -587,6 +589,39 @@ __global__ void k_gather_near(cplxf *__restrict__ val4, const int64_t *__restric
 
 static inline unsigned grid_for(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
+// ------------------------------------------------------------------ generated translations
+// D[(s q + j) q + i] = g(|E_i + o_{slot0+s} w - E_j|) for s < ns (Eq. 12), evaluated in FP64
+template <typename CT>
+__global__ void k_fill_translations(CT *__restrict__ D, const double *__restrict__ E, int q,
+                                    const int32_t *__restrict__ offs, int64_t ns, double w, double k) {
+  const int64_t total = ns * q * (int64_t)q;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % q);
+    const int j = (int)((idx / q) % q);
+    const int64_t sl = idx / ((int64_t)q * q);
+    const double R = dist3(E[3 * i] + offs[3 * sl] * w, E[3 * i + 1] + offs[3 * sl + 1] * w,
+                           E[3 * i + 2] + offs[3 * sl + 2] * w, E[3 * j], E[3 * j + 1], E[3 * j + 2]);
+    D[idx] = from64<CT>(green(k, R));
+  }
+}
+
+template <typename CT>
+static void fill_translations_t(nesa_ctx *c, int level, int64_t slot0, int64_t ns, CT *D) {
+  const DevLevel &d = c->lev[level];
+  if (!d.E || !d.offs) fail(NESA_ERR_INVALID_ARG, "level has no generation data");
+  const int64_t total = ns * d.q * (int64_t)d.q;
+  k_fill_translations<CT><<<(unsigned)std::min<int64_t>((total + 255) / 256, 1 << 20), 256, 0, c->stream>>>(
+      D, d.E, d.q, d.offs + 3 * slot0, ns, d.width, c->k);
+  check_cuda(cudaGetLastError(), "fill translations");
+}
+void fill_translations(nesa_ctx *c, int level, int64_t slot0, int64_t ns, cplx *D) {
+  fill_translations_t<cplx>(c, level, slot0, ns, D);
+}
+void fill_translations(nesa_ctx *c, int level, int64_t slot0, int64_t ns, cplxf *D) {
+  fill_translations_t<cplxf>(c, level, slot0, ns, D);
+}
+
 // Stage timing: an event before and after a launch when profiling is on.
 cudaEvent_t take_event(nesa_ctx *c) {
   if (!c->event_pool.empty()) {
@@ -687,9 +722,26 @@ static void run_product(nesa_ctx *c, const OpView<CT> &op, const cplx *x, cplx *
           continue;
         }
       }
+      if (d.gen) {  // translation matrices built chunk by chunk into the work buffer
+        CT *Dw = nullptr;
+        if constexpr (std::is_same<CT, cplx>::value)
+          Dw = d.Dw;
+        else
+          Dw = d.Dw32;
+        if (!Dw) fail(NESA_ERR_INVALID_ARG, "generated level without a work buffer for this precision");
+        for (int chk = 0; chk < d.nchunk; ++chk) {
+          const int64_t slot0 = (int64_t)chk * d.chunk_slots, ns = std::min<int64_t>(d.chunk_slots, d.noff - slot0);
+          fill_translations(c, l, slot0, ns, Dw);
+          k_translate<CT><<<dim3((unsigned)d.nbox, t.ntile), t.threads, smem, st>>>(
+              op.o[l], op.s[l], Dw, d.cil_ptr + (int64_t)chk * (d.nbox + 1), d.cil_src, d.cil_slot,
+              (down && chk == 0) ? op.o[l - 1] : nullptr, (down && chk == 0) ? op.Ct[l] : nullptr, d.parent,
+              d.octant, nrhs, d.q, qp, t.tr, chk > 0 ? 1 : 0);
+        }
+        continue;
+      }
       k_translate<CT><<<dim3((unsigned)d.nbox, t.ntile), t.threads, smem, st>>>(
           op.o[l], op.s[l], op.D[l], d.il_ptr, d.il_src, d.il_slot, down ? op.o[l - 1] : nullptr,
-          down ? op.Ct[l] : nullptr, d.parent, d.octant, nrhs, d.q, qp, t.tr);
+          down ? op.Ct[l] : nullptr, d.parent, d.octant, nrhs, d.q, qp, t.tr, 0);
     }
   }
   const DevLevel &dL = c->lev[L];
@@ -837,7 +889,10 @@ void build_mixed(nesa_ctx *c) {
   c->d_V32 = copy_c64(c, c->d_V, 4 * c->info.v_columns * (int64_t)c->lev[c->L].q);
   for (int l = c->l0; l <= c->L; ++l) {
     DevLevel &d = c->lev[l];
-    d.D32 = copy_c64(c, d.D, d.noff * (int64_t)d.q * d.q);
+    if (!d.gen)
+      d.D32 = copy_c64(c, d.D, d.noff * (int64_t)d.q * d.q);
+    else if (c->translate_engine == NESA_TRANSLATE_FP32)  // complex64 work buffer of the CUDA-core engine
+      d.Dw32 = (cplxf *)dalloc(c, sizeof(cplxf) * (size_t)d.chunk_slots * d.q * d.q);
     if (l > c->l0) {
       const int64_t cn = 8LL * c->lev[l - 1].q * d.q;
       d.C32 = copy_c64(c, d.C, cn);

@@ -20,6 +20,7 @@
 // item are the same as in the offset-grouped form, whose column tiles then hold about
 // two right-hand-side groups of each pair.
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "nesa_device.cuh"
@@ -30,6 +31,11 @@ namespace nesa {
 // One family of equal-shaped GEMMs (all offsets of a level, or its eight octants).
 struct TcGemm {
   int q = 0, kdim = 0;  // complex rows and columns of each matrix
+  // translations generated in the GEMM's producers instead of read from A (see GemmArgs)
+  bool gen = false;
+  float4 *gen_E = nullptr, *gen_S = nullptr;
+  float2 *gen_P = nullptr;
+  float gen_kap = 0.0f;
   int nk16 = 0, nkc = 0, nmt = 0;
   int64_t nslot = 0, nent = 0;
   __nv_bfloat16 *A = nullptr;  // [slot][nmt][nkc][2][4096]: hi then lo plane of every tile
@@ -170,11 +176,13 @@ static void gemm_setup(nesa_ctx *c, TcGemm &g, const cplx *M, int64_t nslot, int
   g.nmt = (2 * q + tc::TM - 1) / tc::TM;
   g.nslot = nslot;
   g.nent = (int64_t)ent_slot.size();
-  const int64_t nel = nslot * g.nmt * (int64_t)g.nkc * tc::TILE_ELEMS;
-  g.A = (__nv_bfloat16 *)dalloc(c, sizeof(__nv_bfloat16) * 2 * nel);
-  k_prep_A<<<(unsigned)std::min<int64_t>((nel + 255) / 256, 1 << 20), 256, 0, c->stream>>>(g.A, M, nslot, q, kdim,
-                                                                                         g.nmt, g.nkc);
-  check_cuda(cudaGetLastError(), "prep A");
+  if (M) {  // stored A tiles (a generated family has none)
+    const int64_t nel = nslot * g.nmt * (int64_t)g.nkc * tc::TILE_ELEMS;
+    g.A = (__nv_bfloat16 *)dalloc(c, sizeof(__nv_bfloat16) * 2 * nel);
+    k_prep_A<<<(unsigned)std::min<int64_t>((nel + 255) / 256, 1 << 20), 256, 0, c->stream>>>(g.A, M, nslot, q, kdim,
+                                                                                           g.nmt, g.nkc);
+    check_cuda(cudaGetLastError(), "prep A");
+  }
   // entries grouped by slot (stable: ascending entry order within a slot)
   g.h_ptr.assign(nslot + 1, 0);
   g.h_dst.resize(g.nent);
@@ -210,20 +218,52 @@ static void seg_setup(TcGemm &g, int64_t ntarget, int64_t nsource, const std::ve
   for (int64_t t = 0; t < ntarget; ++t) g.any_empty |= g.t_ptr[t + 1] == g.t_ptr[t];
 }
 
-template <int TN, bool SEG>
+template <int TN, bool SEG, bool GEN>
 static void set_smem() {
-  check_cuda(cudaFuncSetAttribute(tc::k_tc_gemm<TN, SEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  check_cuda(cudaFuncSetAttribute(tc::k_tc_gemm<TN, SEG, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   tc::smem_bytes<TN>()),
              "smem attribute");
+}
+
+// Generation data of the translation family of a level (Eq. 12 in the producers):
+// equivalent points about the box centre in FP32, and per offset slot s = o w as
+// (2 s, |s|) in FP32 with the phase exp(-i k |s|) evaluated in FP64.
+static void gen_setup(nesa_ctx *c, TcGemm &g, const HostLevel &hl) {
+  const int q = hl.q;
+  std::vector<float4> E(q);
+  for (int i = 0; i < q; ++i)
+    E[i] = make_float4((float)hl.eq_pts[3 * i], (float)hl.eq_pts[3 * i + 1], (float)hl.eq_pts[3 * i + 2], 0.0f);
+  const int64_t ns = (int64_t)hl.offsets.size() / 3;
+  std::vector<float4> S(std::max<int64_t>(1, ns));
+  std::vector<float2> P(std::max<int64_t>(1, ns));
+  for (int64_t o = 0; o < ns; ++o) {
+    const double sx = hl.offsets[3 * o] * hl.width, sy = hl.offsets[3 * o + 1] * hl.width,
+                 sz = hl.offsets[3 * o + 2] * hl.width;
+    const double R0 = std::sqrt(sx * sx + sy * sy + sz * sz);
+    S[o] = make_float4((float)(2.0 * sx), (float)(2.0 * sy), (float)(2.0 * sz), (float)R0);
+    P[o] = make_float2((float)std::cos(c->k * R0), (float)-std::sin(c->k * R0));
+  }
+  g.gen_E = (float4 *)dalloc(c, sizeof(float4) * E.size());
+  g.gen_S = (float4 *)dalloc(c, sizeof(float4) * S.size());
+  g.gen_P = (float2 *)dalloc(c, sizeof(float2) * P.size());
+  check_cuda(cudaMemcpy(g.gen_E, E.data(), sizeof(float4) * E.size(), cudaMemcpyHostToDevice), "gen E");
+  check_cuda(cudaMemcpy(g.gen_S, S.data(), sizeof(float4) * S.size(), cudaMemcpyHostToDevice), "gen S");
+  check_cuda(cudaMemcpy(g.gen_P, P.data(), sizeof(float2) * P.size(), cudaMemcpyHostToDevice), "gen P");
+  g.gen_kap = (float)(c->k / (2.0 * 3.14159265358979323846));
+  g.gen = true;
 }
 
 void tc_build(nesa_ctx *c) {
   TcState *S = new TcState();
   c->tc_state = S;
-  set_smem<64, false>();
-  set_smem<128, false>();
-  set_smem<256, false>();
-  set_smem<SEG_TN, true>();
+  set_smem<64, false, false>();
+  set_smem<128, false, false>();
+  set_smem<256, false, false>();
+  set_smem<SEG_TN, true, false>();
+  set_smem<64, false, true>();
+  set_smem<128, false, true>();
+  set_smem<256, false, true>();
+  set_smem<SEG_TN, true, true>();
   int dev = 0;
   check_cuda(cudaGetDevice(&dev), "device");
   check_cuda(cudaDeviceGetAttribute(&S->nsm, cudaDevAttrMultiProcessorCount, dev), "SM count");
@@ -236,7 +276,13 @@ void tc_build(nesa_ctx *c) {
     // translations: entry = pair e, slot = its offset, source = il_src[e]
     std::vector<int32_t> dst(hl.il_slot.size());
     for (size_t e = 0; e < dst.size(); ++e) dst[e] = (int32_t)e;
-    gemm_setup(c, t.tr, d.D, d.noff, d.q, d.q, hl.il_slot, dst, hl.il_src);
+    // translations generated in the producers where the level has no stored FP64 table,
+    // where the context asks for it, or (automatic) where an offset serves fewer than 32
+    // pairs, so that its stored tiles would be streamed from DRAM for little reuse
+    const bool gen = d.gen || c->tables_mode == NESA_TABLES_GENERATED ||
+                     (c->tables_mode == NESA_TABLES_AUTO && d.noff > 0 && d.nil < 32 * d.noff);
+    gemm_setup(c, t.tr, gen ? nullptr : d.D, d.noff, d.q, d.q, hl.il_slot, dst, hl.il_src);
+    if (gen) gen_setup(c, t.tr, hl);
     std::vector<int32_t> il_tgt(hl.il_slot.size());  // pair e belongs to target box a
     for (int64_t a = 0; a < d.nbox; ++a)
       for (int32_t e = hl.il_ptr[a]; e < hl.il_ptr[a + 1]; ++e) il_tgt[e] = (int32_t)a;
@@ -315,17 +361,31 @@ static void launch_gemm(nesa_ctx *c, const TcGemm &g, const __nv_bfloat16 *B_hi,
   tc::GemmArgs a{g.work, g.wsrc, g.wdst, g.nwork, g.A, B_hi, B_lo, P, g.q, g.nk16, g.nmt, S->err};
   a.wait_limit = c->tc_wait_limit;
   a.stall = c->tc_stall;
+  a.gen_E = g.gen_E;
+  a.gen_S = g.gen_S;
+  a.gen_P = g.gen_P;
+  a.gen_kap = g.gen_kap;
   const unsigned grid = (unsigned)std::min<int64_t>(g.nwork, S->nsm);
   cudaStream_t st = c->stream;
-  switch (g.work_tn) {
-    case 64:
-      tc::k_tc_gemm<64><<<grid, tc::THREADS, tc::smem_bytes<64>(), st>>>(a);
+  constexpr int T0 = tc::Roles<false>::THREADS, T1 = tc::Roles<true>::THREADS;
+  switch (g.work_tn * 2 + (g.gen ? 1 : 0)) {
+    case 128:
+      tc::k_tc_gemm<64, false, false><<<grid, T0, tc::smem_bytes<64>(), st>>>(a);
       break;
-    case 256:
-      tc::k_tc_gemm<256><<<grid, tc::THREADS, tc::smem_bytes<256>(), st>>>(a);
+    case 129:
+      tc::k_tc_gemm<64, false, true><<<grid, T1, tc::smem_bytes<64>(), st>>>(a);
+      break;
+    case 512:
+      tc::k_tc_gemm<256, false, false><<<grid, T0, tc::smem_bytes<256>(), st>>>(a);
+      break;
+    case 513:
+      tc::k_tc_gemm<256, false, true><<<grid, T1, tc::smem_bytes<256>(), st>>>(a);
+      break;
+    case 257:
+      tc::k_tc_gemm<128, false, true><<<grid, T1, tc::smem_bytes<128>(), st>>>(a);
       break;
     default:
-      tc::k_tc_gemm<128><<<grid, tc::THREADS, tc::smem_bytes<128>(), st>>>(a);
+      tc::k_tc_gemm<128, false, false><<<grid, T0, tc::smem_bytes<128>(), st>>>(a);
   }
 }
 
@@ -389,8 +449,15 @@ static void launch_gemm_seg(nesa_ctx *c, const TcGemm &g, const __nv_bfloat16 *B
                  g.sseg, accum ? 1 : 0, chunk};
   a.wait_limit = c->tc_wait_limit;
   a.stall = c->tc_stall;
+  a.gen_E = g.gen_E;
+  a.gen_S = g.gen_S;
+  a.gen_P = g.gen_P;
+  a.gen_kap = g.gen_kap;
   const unsigned grid = (unsigned)std::min<int64_t>(g.snwork, S->nsm);
-  tc::k_tc_gemm<SEG_TN, true><<<grid, tc::THREADS, tc::smem_bytes<SEG_TN>(), c->stream>>>(a);
+  if (g.gen)
+    tc::k_tc_gemm<SEG_TN, true, true><<<grid, tc::Roles<true>::THREADS, tc::smem_bytes<SEG_TN>(), c->stream>>>(a);
+  else
+    tc::k_tc_gemm<SEG_TN, true, false><<<grid, tc::Roles<false>::THREADS, tc::smem_bytes<SEG_TN>(), c->stream>>>(a);
 }
 
 // Autotuner of the column-tile width: every candidate runs three times on the current
@@ -500,7 +567,7 @@ void tc_translate_level(nesa_ctx *c, int l, const cplxf *s, cplxf *o, const cplx
       cudaEvent_t ev1 = take_event(c);
       cudaEventRecord(ev1, st);
       double fl = 32.0 * nrhs * (double)d.nil * d.q * d.q;
-      double by = 4.0 * (double)d.noff * t.tr.nmt * t.tr.nkc * tc::TILE_ELEMS +
+      double by = (t.tr.gen ? 0.0 : 4.0 * (double)d.noff * t.tr.nmt * t.tr.nkc * tc::TILE_ELEMS) +
                   4.0 * (double)d.nil * nrhs * t.tr.nkc * tc::GROUP_ELEMS + 8.0 * (double)d.nbox * 4 * nrhs * d.q;
       if (down) {
         const int qp = c->lev[l - 1].q;
@@ -541,7 +608,7 @@ void tc_translate_level(nesa_ctx *c, int l, const cplxf *s, cplxf *o, const cplx
       cudaEvent_t ev1 = take_event(c);
       cudaEventRecord(ev1, st);
       double fl = 32.0 * rc * (double)d.nil * d.q * d.q;
-      double by = 4.0 * (double)d.noff * t.tr.nmt * t.tr.nkc * tc::TILE_ELEMS +
+      double by = (t.tr.gen ? 0.0 : 4.0 * (double)d.noff * t.tr.nmt * t.tr.nkc * tc::TILE_ELEMS) +
                   4.0 * (double)d.nil * rc * t.tr.nkc * tc::GROUP_ELEMS + 32.0 * (double)d.nil * rc * d.q;
       if (down) {
         const int qp = c->lev[l - 1].q;
