@@ -121,10 +121,9 @@ typedef struct {
  *               bounded work buffer (at most 64 offsets and about 1.5 GB at a time) just
  *               before the translations that use them, and the tensor-core product forms
  *               each BF16 tile in the GEMM's producer warps (FP32 arithmetic, phase taken
- *               relative to the offset's centre distance).  AUTO generates the FP64 tables
- *               of a level above 6 GB, and the tensor tiles of such levels and of levels
- *               whose offsets serve fewer than 32 pairs each (the coarse levels, where a
- *               stored tile would be streamed from DRAM for little reuse).
+ *               relative to the offset's centre distance).  AUTO generates the levels whose
+ *               FP64 tables would exceed 6 GB (both products), and stores the others:
+ *               generating a tile costs about twice streaming it from device memory.
  */
 #define NESA_TABLES_AUTO 0      /* translation matrices: generated where large or little reused */
 #define NESA_TABLES_STORED 1    /* every translation matrix stored */
@@ -473,7 +472,8 @@ int nesa_device_status(nesa_ctx *ctx);
  * mbarrier waits run out: the kernel leaves early without touching memory it does not
  * own, the product's result is invalid, and nesa_device_status returns
  * NESA_ERR_TIMEOUT.  Nothing faults, traps or hangs.  wait_limit is the number of
- * try-wait iterations of every bounded wait (0 restores the default, 2^26); stall = 0
+ * try-wait iterations of every bounded wait (0 restores the default, 2^20; a try-wait
+ * sleeps up to 20 us while the phase is incomplete); stall = 0
  * restores normal products.  Host state only; takes effect at the next launch.
  */
 int nesa_inject_stall(nesa_ctx *ctx, int stall, uint32_t wait_limit);

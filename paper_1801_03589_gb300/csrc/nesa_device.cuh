@@ -145,7 +145,7 @@ struct nesa_ctx {
   int tables_mode = NESA_TABLES_AUTO; // nesa_params.translation_tables
   int translate_engine = NESA_TRANSLATE_FP32;  // nesa_params.translate
   int tc_stall = 0;                   // failure-detection hook (nesa_inject_stall)
-  uint32_t tc_wait_limit = 1u << 26;  // iterations of the tensor GEMM's bounded waits
+  uint32_t tc_wait_limit = 1u << 20;  // try-wait iterations of the tensor GEMM's bounded waits
   bool autotune = true;          // tune the GEMM tile width at the first product per chunk size
   int fixed_tn = 0;              // tile width used when the autotuner is off
   std::vector<void *> allocs;    // every device allocation owned by the context

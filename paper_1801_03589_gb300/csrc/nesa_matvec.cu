@@ -1013,7 +1013,7 @@ int nesa_device_status(nesa_ctx *c) {
 int nesa_inject_stall(nesa_ctx *c, int stall, uint32_t wait_limit) {
   if (!c || (stall != 0 && stall != 1)) return NESA_ERR_INVALID_ARG;
   c->tc_stall = stall;
-  c->tc_wait_limit = wait_limit ? wait_limit : (1u << 26);
+  c->tc_wait_limit = wait_limit ? wait_limit : (1u << 20);
   return NESA_OK;
 }
 

@@ -276,11 +276,11 @@ void tc_build(nesa_ctx *c) {
     // translations: entry = pair e, slot = its offset, source = il_src[e]
     std::vector<int32_t> dst(hl.il_slot.size());
     for (size_t e = 0; e < dst.size(); ++e) dst[e] = (int32_t)e;
-    // translations generated in the producers where the level has no stored FP64 table,
-    // where the context asks for it, or (automatic) where an offset serves fewer than 32
-    // pairs, so that its stored tiles would be streamed from DRAM for little reuse
-    const bool gen = d.gen || c->tables_mode == NESA_TABLES_GENERATED ||
-                     (c->tables_mode == NESA_TABLES_AUTO && d.noff > 0 && d.nil < 32 * d.noff);
+    // translations generated in the producers where the level has no stored FP64 table
+    // (automatic: tables too large to store) or where the context asks for it.  Measured
+    // on the r = 3 sphere (1 RHS), generating a level's tiles costs about twice streaming
+    // them from DRAM (0.35 against 0.17 ms at Q = 576), so it is used for memory only.
+    const bool gen = d.gen || c->tables_mode == NESA_TABLES_GENERATED;
     gemm_setup(c, t.tr, gen ? nullptr : d.D, d.noff, d.q, d.q, hl.il_slot, dst, hl.il_src);
     if (gen) gen_setup(c, t.tr, hl);
     std::vector<int32_t> il_tgt(hl.il_slot.size());  // pair e belongs to target box a
