@@ -464,6 +464,75 @@ def run_model2d(args, stream, world, barrier, max_over_ranks):
     return out
 
 
+def run_large(args, stream, world, barrier, max_over_ranks):
+    """The r = 16 sphere (1,966,080 RWG, 9 levels, Q up to 4,096), 16 right-hand sides:
+    build, the mixed product of all 16 columns, the FP64 product of one column, and the
+    mixed product's error against it.  The two coarsest far levels (FP64 tables of 85
+    and 10.5 GB) are generated when used."""
+    import torch
+
+    import paper_1801_03589_gb300 as nesa
+    cfg = get_config("C5")
+    nrhs = cfg["nrhs"]
+    t0 = time.perf_counter()
+    g = nesa.Nesa(cfg["vertices"], cfg["triangles"], cfg["k"], leaf_size=cfg["leaf_size"],
+                  n_levels=cfg["n_levels"], precision=nesa.MIXED, translate=nesa.TRANSLATE_TENSOR)
+    build_s = time.perf_counter() - t0
+    g.set_stream(stream)
+    info = g.info()
+    mixed = nesa.PART_ALL | nesa.PART_MIXED
+    x = torch.from_numpy(random_coefficients(g.n, nrhs, seed=2024)).cuda()
+    y = torch.empty_like(x)
+    torch.cuda.synchronize()
+
+    def timed(xx, yy, parts, reps):
+        with torch.cuda.stream(stream):
+            g.matvec(xx, yy, parts=parts)  # warm-up (allocations, tile tuning)
+        stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(reps):
+                g.matvec(xx, yy, parts=parts)
+            e1.record(stream)
+        stream.synchronize()
+        return max_over_ranks(e0.elapsed_time(e1) / reps)
+
+    ms_mx = timed(x, y, mixed, 3)
+    g.profile_enable(True)
+    with torch.cuda.stream(stream):
+        g.matvec(x, y, parts=mixed)
+    stream.synchronize()
+    prof = g.profile_read()
+    g.profile_enable(False)
+    x1, y1 = x[:1].contiguous(), torch.empty_like(x[:1])
+    ms64 = timed(x1, y1, nesa.PART_ALL, 1)
+    y64 = y1.clone()
+    ym = g.matvec(x1, parts=mixed)
+    torch.cuda.synchronize()
+    err = float((ym - y64).abs().pow(2).sum().sqrt() / y64.abs().pow(2).sum().sqrt())
+    gemm = prof["translation_tensor_gemm"]
+    gemm_tf = gemm["flops"] / (gemm["ms"] * 1e-3) / 1e12 if gemm["ms"] > 0 else None
+    l0, L = info["l0"], info["n_levels"] - 1
+    generated = [l for l in range(l0, L + 1) if 16.0 * info["n_offsets"][l] * info["q"][l] ** 2 > 6e9]
+    out = {"workload": "C5: %s; %d right-hand sides" % (cfg["description"], nrhs),
+           "n_unknowns": g.n, "levels": info["n_levels"], "l0": l0, "q": info["q"][l0:],
+           "near_nnz": info["near_nnz"], "device_gb": g.info()["device_bytes"] / 1e9, "build_s": build_s,
+           "generated_levels": generated,
+           "mixed": {"ms_per_product": ms_mx, "nrhs": nrhs, "matvec_per_s": job_throughput(world, nrhs, ms_mx),
+                     "tensor_gemm_ms": gemm["ms"], "tensor_gemm_tflops": gemm_tf,
+                     "tensor_gemm_frac_of_bf16_burst": (gemm_tf / _peaks().get("bf16_tflops", 1901.0))
+                     if gemm_tf else None,
+                     "stages_ms": {k: v["ms"] for k, v in prof.items()}},
+           "fp64": {"ms_per_product": ms64, "nrhs": 1, "matvec_per_s": job_throughput(world, 1, ms64)},
+           "mixed_rel_err_vs_fp64": err}
+    g.close()
+    del g
+    torch.cuda.empty_cache()
+    return out
+
+
 def _stages(prof, steps):
     return {k: {"launches": v["launches"], "ms_per_step": v["ms"] / steps,
                 "tflops": (v["flops"] / (v["ms"] * 1e-3) / 1e12) if v["ms"] > 0 else None,
@@ -620,6 +689,15 @@ def run_ours(args, world, rank, local):
                  "tile_n": [{l: t["tile_n"] for l, t in m.tuning().items()} for m in members]}
         bt.close()
 
+    # the r = 16 sphere at full size (generated coarse translations); a failure here is
+    # reported in the block and leaves the rest of the line intact
+    large = None
+    if not args.no_large:
+        try:
+            large = run_large(args, stream, world, barrier, max_over_ranks)
+        except Exception as e:  # noqa: BLE001
+            large = {"error": "%s: %s" % (type(e).__name__, e)}
+
     # the paper's 2D model problem at its size (a separate library path; a failure here
     # is reported in the block and leaves the rest of the line intact)
     model2d = None
@@ -742,6 +820,7 @@ def run_ours(args, world, rank, local):
         "solve": solve,
         "learned": learned,
         "batch": batch,
+        "large": large,
         "model2d": model2d,
         "cpu_baseline": cpu,
     }
@@ -760,6 +839,7 @@ def main():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-model2d", action="store_true", help="skip the 2D model problem block")
+    ap.add_argument("--no-large", action="store_true", help="skip the r = 16 sphere block (about 90 s)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner block (aircraft body)")
     ap.add_argument("--fp64-solve", action="store_true", help="also time the unpreconditioned FP64 solve (about 2.5 minutes)")
     ap.add_argument("--workload", default=CONFIG, help="workload name (smaller ones are for profiling runs)")

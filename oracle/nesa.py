@@ -75,6 +75,45 @@ def q_for_level(k, width, q_mode, q_fixed, q_digits):
     return max(int(q_fixed), (nl + 1) ** 2)
 
 
+def channel_sources(vertices, triangles, rwg, points, x):
+    """Channel point sources J [npts, 4] (x, y, z current and charge at every quadrature
+    point, weights included) from RWG coefficients x [N]; points [7 nt, 3]."""
+    r = rwg
+    pts = np.asarray(points).reshape(-1, 7, 3)
+    J = np.zeros((len(triangles), 7, 4), np.complex128)
+    for t in range(len(triangles)):
+        for c in range(3):
+            n = r["tri_rwg"][t, c]
+            if n < 0:
+                continue
+            sl = r["tri_sl"][t, c]
+            v = vertices[triangles[t, c]]
+            J[t, :, :3] += (WEIGHTS * sl * x[n] / 2.0)[:, None] * (pts[t] - v)
+            J[t, :, 3] += WEIGHTS * sl * x[n]
+    return J.reshape(-1, 4)
+
+
+def test_fields(vertices, triangles, rwg, points, k, eta, F, rows=None):
+    """Testing (Eq. 3) of channel fields F [npts, 4] at the quadrature points:
+    y_m = -i eta k sum_p w_p sl [ (r_p - v).F_p/2 - F^rho_p / k^2 ] for m in rows."""
+    r = rwg
+    pts = np.asarray(points).reshape(-1, 7, 3)
+    F = F.reshape(-1, 7, 4)
+    rows = range(r["n"]) if rows is None else rows
+    y = np.zeros(len(rows), np.complex128)
+    for i, m in enumerate(rows):
+        acc = 0.0 + 0.0j
+        for side in range(2):
+            t = r["tri"][m, side]
+            c = r["free"][m, side]
+            sl = r["tri_sl"][t, c]
+            v = vertices[triangles[t, c]]
+            acc += np.sum(WEIGHTS * sl * (np.einsum("px,px->p", pts[t] - v, F[t, :, :3]) / 2.0
+                                           - F[t, :, 3] / k ** 2))
+        y[i] = -1j * eta * k * acc
+    return y
+
+
 class NesaOracle:
     def __init__(self, vertices, triangles, k, leaf_size, n_levels, q_mode="auto", q_fixed=100, q_digits=5.0,
                  rho_eq=1.0, rho_test=RHO_TEST_DEFAULT, pinv_eps=1e-9, eta=ETA0, singular_mode="touching",
@@ -122,38 +161,11 @@ class NesaOracle:
     # ---------------------------------------------------------------- point maps
     def sources(self, x):
         """Channel point sources J [npts, 4] from RWG coefficients x [N]."""
-        r = self.rwg
-        pts = self.tree.points.reshape(-1, 7, 3)
-        J = np.zeros((len(self.triangles), 7, 4), np.complex128)
-        for t in range(len(self.triangles)):
-            for c in range(3):
-                n = r["tri_rwg"][t, c]
-                if n < 0:
-                    continue
-                sl = r["tri_sl"][t, c]
-                v = self.vertices[self.triangles[t, c]]
-                J[t, :, :3] += (WEIGHTS * sl * x[n] / 2.0)[:, None] * (pts[t] - v)
-                J[t, :, 3] += WEIGHTS * sl * x[n]
-        return J.reshape(-1, 4)
+        return channel_sources(self.vertices, self.triangles, self.rwg, self.tree.points, x)
 
     def test(self, F, rows=None):
         """y_m = -i eta k sum_p w_p sl [ (r_p - v).F_p/2 - F^rho_p / k^2 ] for m in rows."""
-        r = self.rwg
-        pts = self.tree.points.reshape(-1, 7, 3)
-        F = F.reshape(-1, 7, 4)
-        rows = range(self.n) if rows is None else rows
-        y = np.zeros(len(rows), np.complex128)
-        for i, m in enumerate(rows):
-            acc = 0.0 + 0.0j
-            for side in range(2):
-                t = r["tri"][m, side]
-                c = r["free"][m, side]
-                sl = r["tri_sl"][t, c]
-                v = self.vertices[self.triangles[t, c]]
-                acc += np.sum(WEIGHTS * sl * (np.einsum("px,px->p", pts[t] - v, F[t, :, :3]) / 2.0
-                                               - F[t, :, 3] / self.k ** 2))
-            y[i] = -1j * self.eta * self.k * acc
-        return y
+        return test_fields(self.vertices, self.triangles, self.rwg, self.tree.points, self.k, self.eta, F, rows)
 
     # ---------------------------------------------------------------- near field
     def near_rows(self, rows=None):

@@ -41,6 +41,21 @@ def depth_for_points_per_leaf(points, origin, root, P):
     return best
 
 
+def point_leaf_coords(points, origin, leaf_width, levels):
+    """Integer leaf coordinates of points: floor((x - origin) / w_L) clamped to
+    [0, 2**L - 1] per axis (L = levels - 1)."""
+    nb = 2 ** (levels - 1)
+    ijk = np.floor((np.asarray(points) - origin) / leaf_width).astype(np.int64)
+    return np.clip(ijk, 0, nb - 1)
+
+
+def leaf_geometry(vertices, leaf_size, n_levels):
+    """(origin, leaf width) of the tree with a given leaf size and number of levels."""
+    lo, hi = vertices.min(0), vertices.max(0)
+    root = leaf_size * 2.0 ** (n_levels - 1)
+    return 0.5 * (lo + hi) - 0.5 * root, root / 2.0 ** (n_levels - 1)
+
+
 class Tree:
     def __init__(self, vertices, triangles, leaf_size, n_levels, points_per_leaf=0):
         lo, hi = vertices.min(0), vertices.max(0)
@@ -62,9 +77,7 @@ class Tree:
                     self.L += 1
             self.root = leaf_size * 2.0 ** self.L
             self.origin = self.center - 0.5 * self.root
-        nb = 2 ** self.L
-        ijk = np.floor((self.points - self.origin) / self.width(self.L)).astype(np.int64)
-        self.point_leaf_ijk = np.clip(ijk, 0, nb - 1)
+        self.point_leaf_ijk = point_leaf_coords(self.points, self.origin, self.width(self.L), self.L + 1)
         # boxes per level: sorted list of integer coordinate triples
         self.boxes = {}
         for l in range(self.L + 1):
