@@ -423,6 +423,8 @@ def _time_products(g, x, y, parts, steps, warmup, stream, barrier):
 # the paper's CPU timings of the complete 2D product at N = 100,000 (Sec. 5, Tables 3
 # and 7): context for the 2D block, other hardware
 MODEL2D_PAPER_MS = {(300, 100): {"1 core (Table 3)": 1192.0, "64 cores (Table 7)": 127.0},
+                    (400, 100): {"far field, 1 core (Table 1)": 95.0, "far field, 16 cores (Table 1)": 19.0,
+                                 "near field, 1 core (Table 2)": 3848.0, "near field, 16 cores (Table 2)": 398.0},
                     (50, 10): {"1 core (Table 3)": 244.0, "16 cores (Table 3)": 156.0}}
 
 
@@ -439,26 +441,37 @@ def run_model2d(args, stream, world, barrier, max_over_ranks):
     torch.cuda.synchronize()  # the copy above ran on torch's stream, the products run on `stream`
     out = {"workload": "N = 100,000 charges on a seeded closed curve (the paper's curve is not available); "
                        "phi = K q, K = -log|x_i - x_j|; FP64", "cases": []}
-    for P, Q in ((300, 100), (50, 10)):
+    peak = _peaks().get("hbm_gbs", 6790.0)
+    for P, Q in ((300, 100), (400, 100), (50, 10)):
         t0 = time.perf_counter()
         g = nesa.Model2D(x, P, Q)
         build_s = time.perf_counter() - t0
         g.set_stream(stream)
         info = g.info()
-        for _ in range(max(3, args.warmup)):
-            g.matvec(qd, y)
-        stream.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        barrier()
-        e0.record(stream)
-        for _ in range(args.steps):
-            g.matvec(qd, y)
-        e1.record(stream)
-        stream.synchronize()
-        ms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+
+        def timed(parts):
+            for _ in range(max(3, args.warmup)):
+                g.matvec(qd, y, parts=parts)
+            stream.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            barrier()
+            e0.record(stream)
+            for _ in range(args.steps):
+                g.matvec(qd, y, parts=parts)
+            e1.record(stream)
+            stream.synchronize()
+            return max_over_ranks(e0.elapsed_time(e1) / args.steps)
+
+        ms = timed(nesa.PART2D_ALL)
+        ms_near, ms_far = timed(nesa.PART2D_NEAR), timed(nesa.PART2D_FAR)
+        near_bytes = 8.0 * info["near_entries"] + 8.0 * 2 * n  # stored blocks once, charges in, potentials out
         out["cases"].append({"P": P, "Q": Q, "levels": [info["l0"], info["L"]], "leaves": info["n_boxes"][info["L"]],
                              "near_entries": info["near_entries"], "near_gb": 8e-9 * info["near_entries"],
                              "ms_per_matvec": ms, "matvec_per_s": job_throughput(world, 1, ms),
+                             "near_only_ms": ms_near, "far_only_ms": ms_far,
+                             "near_roofline": {"kernel": "k2_near (+ the two permutations)", "bound": "hbm",
+                                               "achieved_gbs": near_bytes / (ms_near * 1e-3) / 1e9, "peak_gbs": peak,
+                                               "frac": near_bytes / (ms_near * 1e-3) / 1e9 / peak},
                              "build_s": build_s, "paper_cpu_ms": MODEL2D_PAPER_MS[(P, Q)]})
         g.close()
     return out

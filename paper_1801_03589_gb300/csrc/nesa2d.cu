@@ -34,6 +34,9 @@
 
 namespace nesa2d_impl {
 
+// near-field kernel shape (k2_near): 8 warps, 4 rows per lane, tiles of 128 rows
+constexpr int NEAR_WARPS = 8, NEAR_RB = 4, NEAR_TROWS = 32 * NEAR_RB;
+
 using nesa::Error;
 using nesa::fail;
 
@@ -71,6 +74,8 @@ struct nesa2d_ctx {
   // device
   int32_t *d_perm = nullptr, *d_leaf_ptr = nullptr, *d_nptr = nullptr, *d_nleaf = nullptr;
   int64_t *d_noff = nullptr;
+  int2 *d_tiles = nullptr;  // near-field row tiles (leaf, first row)
+  int64_t ntile = 0;
   double *d_Z = nullptr, *d_V = nullptr, *d_qp = nullptr, *d_yp = nullptr;
   int nrhs_cap = 0;
   std::vector<void *> allocs;
@@ -438,6 +443,14 @@ static void build(nesa2d_ctx *c, const double *x) {
   c->d_nptr = upload(c, nptr);
   c->d_nleaf = upload(c, nlist);
   c->d_noff = upload(c, noff);
+  {  // row tiles of the near-field kernel
+    std::vector<int2> tiles;
+    for (int64_t a = 0; a < c->nleaf; ++a)
+      for (int32_t r0 = 0; r0 < c->leaf_ptr[a + 1] - c->leaf_ptr[a]; r0 += NEAR_TROWS)
+        tiles.push_back(make_int2((int32_t)a, r0));
+    c->ntile = (int64_t)tiles.size();
+    c->d_tiles = upload(c, tiles);
+  }
   c->d_Z = upload(c, Z);
   c->d_V = upload(c, V);
 }
@@ -457,23 +470,56 @@ __global__ void k2_perm_out(double *phi, const double *yp, const int32_t *perm, 
   }
 }
 
-// Eq. 9: block a, thread = row of a; near leaves in ascending order, columns in order
-__global__ void k2_near(double *yp, const double *qp, int64_t n, int nrhs, const int32_t *leaf_ptr,
-                        const int32_t *nptr, const int32_t *nleaf, const int64_t *noff, const double *Z, int on) {
-  const int64_t a = blockIdx.x;
+// Eq. 9.  The near blocks of a leaf a are stored one after the other, each column-major
+// |a| x |b|, so together they form one column-major panel of |a| rows.  A CTA owns a tile
+// of NEAR_TROWS rows of one leaf (work list `tiles`: leaf, first row); its 8 warps split
+// the columns of every block between them (warp w: columns [w nb / 8, (w+1) nb / 8)), each
+// lane accumulating NEAR_RB rows 32 apart, so that every column is one coalesced 256-byte
+// load per row group and the panel is streamed once.  The 8 partial sums of a row are
+// added in warp order (deterministic).  Rows past |a| are skipped.
+__global__ void __launch_bounds__(32 * NEAR_WARPS) k2_near(double *__restrict__ yp, const double *__restrict__ qp,
+                                                          int64_t n, int nrhs, const int32_t *__restrict__ leaf_ptr,
+                                                          const int32_t *__restrict__ nptr,
+                                                          const int32_t *__restrict__ nleaf,
+                                                          const int64_t *__restrict__ noff,
+                                                          const double *__restrict__ Z, const int2 *__restrict__ tiles,
+                                                          int on) {
+  __shared__ double red[NEAR_WARPS][NEAR_TROWS];
+  const int2 tl = tiles[blockIdx.x];
+  const int32_t a = tl.x, row0 = tl.y;
   const int32_t ra = leaf_ptr[a], na = leaf_ptr[a + 1] - ra;
-  for (int i = threadIdx.x; i < na; i += blockDim.x)
-    for (int r = 0; r < nrhs; ++r) {
-      double acc = 0.0;
-      if (on)
-        for (int32_t e = nptr[a]; e < nptr[a + 1]; ++e) {
-          const int32_t b = nleaf[e], rb = leaf_ptr[b], nbb = leaf_ptr[b + 1] - rb;
-          const double *blk = Z + noff[e] + i;
-          const double *qb = qp + (int64_t)r * n + rb;
-          for (int32_t j = 0; j < nbb; ++j) acc += blk[(int64_t)j * na] * qb[j];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int r = 0; r < nrhs; ++r) {
+    double acc[NEAR_RB];
+#pragma unroll
+    for (int rr = 0; rr < NEAR_RB; ++rr) acc[rr] = 0.0;
+    if (on)
+      for (int32_t e = nptr[a]; e < nptr[a + 1]; ++e) {
+        const int32_t b = nleaf[e], rb = leaf_ptr[b], nb = leaf_ptr[b + 1] - rb;
+        const double *__restrict__ col = Z + noff[e] + row0 + lane;
+        const double *__restrict__ xb = qp + (int64_t)r * n + rb;
+        const int32_t j0 = (int32_t)((int64_t)warp * nb / NEAR_WARPS);
+        const int32_t j1 = (int32_t)((int64_t)(warp + 1) * nb / NEAR_WARPS);
+#pragma unroll 2
+        for (int32_t j = j0; j < j1; ++j) {
+          const double xj = __ldg(xb + j);
+          const double *cj = col + (int64_t)j * na;
+#pragma unroll
+          for (int rr = 0; rr < NEAR_RB; ++rr)
+            if (row0 + lane + 32 * rr < na) acc[rr] = fma(__ldcs(cj + 32 * rr), xj, acc[rr]);
         }
-      yp[(int64_t)r * n + ra + i] = acc;
+      }
+#pragma unroll
+    for (int rr = 0; rr < NEAR_RB; ++rr) red[warp][lane + 32 * rr] = acc[rr];
+    __syncthreads();
+    if (threadIdx.x < NEAR_TROWS && row0 + (int32_t)threadIdx.x < na) {
+      double sum = 0.0;
+#pragma unroll
+      for (int w = 0; w < NEAR_WARPS; ++w) sum += red[w][threadIdx.x];
+      yp[(int64_t)r * n + ra + row0 + threadIdx.x] = sum;
     }
+    __syncthreads();
+  }
 }
 
 // Eq. 10: block b, thread = equivalent point k
@@ -580,8 +626,9 @@ static void matvec(nesa2d_ctx *c, const double *q, double *phi, int nrhs, int pa
   const int Q = c->Q, L = c->L, l0 = c->l0;
   const int tq = std::min(256, ((Q + 31) / 32) * 32);
   k2_perm_in<<<grid_of(c->n * nrhs), 256, 0, st>>>(c->d_qp, q, c->d_perm, c->n, nrhs);
-  k2_near<<<(unsigned)c->nleaf, 256, 0, st>>>(c->d_yp, c->d_qp, c->n, nrhs, c->d_leaf_ptr, c->d_nptr, c->d_nleaf,
-                                              c->d_noff, c->d_Z, (parts & NESA2D_PART_NEAR) ? 1 : 0);
+  k2_near<<<(unsigned)c->ntile, 32 * NEAR_WARPS, 0, st>>>(c->d_yp, c->d_qp, c->n, nrhs, c->d_leaf_ptr, c->d_nptr,
+                                                          c->d_nleaf, c->d_noff, c->d_Z, c->d_tiles,
+                                                          (parts & NESA2D_PART_NEAR) ? 1 : 0);
   if (parts & NESA2D_PART_FAR) {
     k2_radiate<<<(unsigned)c->nleaf, tq, 0, st>>>(c->lev[L].s, c->d_V, c->d_qp, c->n, nrhs, c->d_leaf_ptr, Q);
     for (int l = L; l > l0; --l)

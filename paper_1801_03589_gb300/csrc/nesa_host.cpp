@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstring>
 #include <numeric>
+#include <thread>
 #include <unordered_map>
 
 #include "nesa_internal.h"
@@ -17,6 +18,60 @@
 namespace nesa {
 
 void fail(int status, const std::string &what) { throw Error{status, what}; }
+
+// Rows 0..n-1 of a CSR pattern computed in parallel: row_fn(r, out, mark) appends row r
+// to out.  Rows are computed in contiguous chunks on the host threads and concatenated
+// in row order, so the result does not depend on the number of threads.  mark is the
+// thread's scratch of mark_size entries, -1 at the start; a thread meets its rows in
+// ascending order, so a row may use its own index as the mark value.
+template <typename PtrT, typename RowFn>
+static void parallel_rows(int64_t n, int64_t mark_size, std::vector<PtrT> &ptr, std::vector<int32_t> &col,
+                          RowFn row_fn) {
+  const int nth = (int)std::max<unsigned>(1, std::min<unsigned>(32, std::thread::hardware_concurrency()));
+  const int nchunk = (int)std::min<int64_t>(std::max<int64_t>(n, 1), 4 * nth);
+  std::vector<std::vector<int32_t>> cols(nchunk);
+  std::vector<std::vector<PtrT>> lens(nchunk);
+  std::vector<char> failed(nchunk, 0);
+  std::vector<std::string> what(nchunk);
+  std::vector<int> status(nchunk, 0);
+  auto work = [&](int t) {
+    std::vector<int32_t> mark(std::max<int64_t>(mark_size, 0), -1);
+    for (int ch = t; ch < nchunk; ch += nth) {
+      const int64_t r0 = n * ch / nchunk, r1 = n * (ch + 1) / nchunk;
+      try {
+        for (int64_t r = r0; r < r1; ++r) {
+          const size_t before = cols[ch].size();
+          row_fn(r, cols[ch], mark);
+          lens[ch].push_back((PtrT)(cols[ch].size() - before));
+        }
+      } catch (const Error &e) {
+        failed[ch] = 1;
+        status[ch] = e.status;
+        what[ch] = e.what;
+        return;
+      }
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nth; ++t) pool.emplace_back(work, t);
+  for (auto &th : pool) th.join();
+  for (int ch = 0; ch < nchunk; ++ch)
+    if (failed[ch]) fail(status[ch], what[ch]);
+  ptr.assign(n + 1, 0);
+  size_t total = 0;
+  for (auto &c : cols) total += c.size();
+  col.clear();
+  col.reserve(total);
+  int64_t r = 0;
+  for (int ch = 0; ch < nchunk; ++ch) {
+    for (PtrT len : lens[ch]) {
+      ptr[r + 1] = ptr[r] + len;
+      ++r;
+    }
+    col.insert(col.end(), cols[ch].begin(), cols[ch].end());
+    std::vector<int32_t>().swap(cols[ch]);
+  }
+}
 
 // Radon's 7-point degree-5 rule (Stroud T2:5-1): centroid, and the orbits (a, b, b)
 // with a = (9 -+ 2 sqrt15)/21, b = (6 +- sqrt15)/21.
@@ -418,62 +473,70 @@ void build_host_model(const nesa_mesh &mesh, double k, const nesa_params &p, Hos
           }
       nl_ptr[b + 1] = (int32_t)nl.size();
     }
-    std::vector<int32_t> mark(m.nt, -1);
-    m.tp_ptr.assign(m.nt + 1, 0);
-    m.tp_col.clear();
-    std::vector<int32_t> row;
-    for (int64_t t = 0; t < m.nt; ++t) {
-      row.clear();
-      for (int i = 0; i < 7; ++i) {
-        int32_t lf = m.pt_leaf[7 * t + i];
-        for (int32_t e = nl_ptr[lf]; e < nl_ptr[lf + 1]; ++e) {
-          int32_t b = nl[e];
-          for (int32_t f = leaf_tri_ptr[b]; f < leaf_tri_ptr[b + 1]; ++f) {
-            int32_t t2 = leaf_tri[f];
-            if (mark[t2] != t) {
-              mark[t2] = (int32_t)t;
-              row.push_back(t2);
+    // near triangles of triangle t (ascending): every triangle with a point in a leaf
+    // touching a leaf of one of t's points; rows computed in parallel
+    {
+      parallel_rows(m.nt, m.nt, m.tp_ptr, m.tp_col, [&](int64_t t, std::vector<int32_t> &out,
+                                                         std::vector<int32_t> &mark) {
+        const size_t at = out.size();
+        for (int i = 0; i < 7; ++i) {
+          int32_t lf = m.pt_leaf[7 * t + i];
+          for (int32_t e = nl_ptr[lf]; e < nl_ptr[lf + 1]; ++e) {
+            int32_t b = nl[e];
+            for (int32_t f = leaf_tri_ptr[b]; f < leaf_tri_ptr[b + 1]; ++f) {
+              int32_t t2 = leaf_tri[f];
+              if (mark[t2] != t) {
+                mark[t2] = (int32_t)t;
+                out.push_back(t2);
+              }
             }
           }
         }
-      }
-      std::sort(row.begin(), row.end());
-      m.tp_col.insert(m.tp_col.end(), row.begin(), row.end());
-      m.tp_ptr[t + 1] = (int64_t)m.tp_col.size();
+        std::sort(out.begin() + at, out.end());
+      });
     }
     // every pair of triangles sharing a vertex must be a near pair
     {
-      std::vector<std::vector<int32_t>> vt(m.nv);
+      std::vector<int32_t> vt_ptr(m.nv + 1, 0), vt(3 * m.nt);
       for (int64_t t = 0; t < m.nt; ++t)
-        for (int c = 0; c < 3; ++c) vt[m.tris[3 * t + c]].push_back((int32_t)t);
-      for (int64_t t = 0; t < m.nt; ++t)
-        for (int c = 0; c < 3; ++c)
-          for (int32_t t2 : vt[m.tris[3 * t + c]])
-            if (!std::binary_search(m.tp_col.begin() + m.tp_ptr[t], m.tp_col.begin() + m.tp_ptr[t + 1], t2))
+        for (int c = 0; c < 3; ++c) vt_ptr[m.tris[3 * t + c] + 1]++;
+      for (int64_t v = 0; v < m.nv; ++v) vt_ptr[v + 1] += vt_ptr[v];
+      {
+        std::vector<int32_t> fill(vt_ptr.begin(), vt_ptr.end() - 1);
+        for (int64_t t = 0; t < m.nt; ++t)
+          for (int c = 0; c < 3; ++c) vt[fill[m.tris[3 * t + c]]++] = (int32_t)t;
+      }
+      std::vector<int64_t> dummy_ptr;
+      std::vector<int32_t> dummy_col;
+      parallel_rows(m.nt, 0, dummy_ptr, dummy_col, [&](int64_t t, std::vector<int32_t> &, std::vector<int32_t> &) {
+        for (int c = 0; c < 3; ++c) {
+          const int32_t v = m.tris[3 * t + c];
+          for (int32_t e = vt_ptr[v]; e < vt_ptr[v + 1]; ++e)
+            if (!std::binary_search(m.tp_col.begin() + m.tp_ptr[t], m.tp_col.begin() + m.tp_ptr[t + 1], vt[e]))
               fail(NESA_ERR_MESH, "triangles sharing a vertex lie in non-touching leaves: leaf too small");
+        }
+      });
     }
     // RWG pattern: union over the supports of m of the RWG functions of near triangles
-    std::vector<int32_t> mk(m.n, -1);
-    m.nz_ptr.assign(m.n + 1, 0);
-    m.nz_col.clear();
-    for (int64_t r = 0; r < m.n; ++r) {
-      row.clear();
-      for (int s = 0; s < 2; ++s) {
-        int32_t t = m.rwg_tri[2 * r + s];
-        for (int64_t e = m.tp_ptr[t]; e < m.tp_ptr[t + 1]; ++e) {
-          int32_t t2 = m.tp_col[e];
-          for (int c = 0; c < 3; ++c) {
-            int32_t r2 = m.tri_rwg[3 * (size_t)t2 + c];
-            if (r2 >= 0 && mk[r2] != r) {
-              mk[r2] = (int32_t)r;
-              row.push_back(r2);
+    {
+      parallel_rows(m.n, m.n, m.nz_ptr, m.nz_col, [&](int64_t r, std::vector<int32_t> &out,
+                                                       std::vector<int32_t> &mk) {
+        const size_t at = out.size();
+        for (int s = 0; s < 2; ++s) {
+          int32_t t = m.rwg_tri[2 * r + s];
+          for (int64_t e = m.tp_ptr[t]; e < m.tp_ptr[t + 1]; ++e) {
+            int32_t t2 = m.tp_col[e];
+            for (int c = 0; c < 3; ++c) {
+              int32_t r2 = m.tri_rwg[3 * (size_t)t2 + c];
+              if (r2 >= 0 && mk[r2] != r) {
+                mk[r2] = (int32_t)r;
+                out.push_back(r2);
+              }
             }
           }
         }
-      }
-      std::sort(row.begin(), row.end());
-      m.nz_col.insert(m.nz_col.end(), row.begin(), row.end());
-      m.nz_ptr[r + 1] = (int64_t)m.nz_col.size();
+        std::sort(out.begin() + at, out.end());
+      });
     }
   }
 }

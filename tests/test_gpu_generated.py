@@ -90,14 +90,18 @@ def test_auto_stores_the_tables_that_fit():
     """Automatic choice: levels whose FP64 tables fit the budget (every level here) are
     stored, so the product is the stored-table product bit for bit."""
     import paper_1801_03589_gb300 as nesa
-    ga = ctx("C3a", nesa.TABLES_AUTO, precision=nesa.MIXED, translate=nesa.TRANSLATE_TENSOR)
-    gs = ctx("C3a", nesa.TABLES_STORED, precision=nesa.MIXED, translate=nesa.TRANSLATE_TENSOR)
-    assert ga.info()["device_bytes"] == gs.info()["device_bytes"]
+    c = get_config("C3a")
+    ga, gs = [nesa.Nesa(c["vertices"], c["triangles"], c["k"], leaf_size=c["leaf_size"], n_levels=c["n_levels"],
+                        precision=nesa.MIXED, translate=nesa.TRANSLATE_TENSOR, translation_tables=t)
+              for t in (nesa.TABLES_AUTO, nesa.TABLES_STORED)]
+    assert ga.info()["device_bytes"] == gs.info()["device_bytes"]  # both fresh: nothing generated
     x = torch.from_numpy(random_coefficients(ga.n, 1, seed=74)).cuda()
     mixed = nesa.PART_ALL | nesa.PART_MIXED
     assert torch.equal(ga.matvec(x), gs.matvec(x))
     ya, ys = ga.matvec(x, parts=mixed), gs.matvec(x, parts=mixed)
     assert rel(ya.cpu().numpy(), ys.cpu().numpy()) < 1e-6  # tile widths are tuned per context
+    ga.close()
+    gs.close()
 
 
 def test_generated_fp32_engine():

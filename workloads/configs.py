@@ -28,6 +28,9 @@ CONFIGS = {
     "C4": (lambda: meshes.aircraft(edge=0.1, length=10.0, seed=4), 0.25, 7, 8,
            "aircraft-like PEC body: 10 wavelength prolate fuselage, two wing plates and a tail plate, "
            "edges about 0.1 wavelength (12,560 triangles, 18,727 RWG)"),
+    "C4L": (lambda: meshes.aircraft(edge=0.1, length=52.0, seed=4), 0.25, 9, 8,
+            "aircraft-like PEC body scaled to 52 wavelengths (fuselage 52 long, span 47), edges about 0.1 "
+            "wavelength (344,676 triangles, 516,413 RWG), 9 levels"),
     "C5": (lambda: meshes.icosphere(8, 16.0), 0.25, 9, 16,
            "PEC sphere r=16, icosphere subdiv 8 (1,310,720 triangles, 1,966,080 RWG), 9 levels"),
 }
