@@ -93,7 +93,7 @@ def channel_sources(vertices, triangles, rwg, points, x):
     return J.reshape(-1, 4)
 
 
-def test_fields(vertices, triangles, rwg, points, k, eta, F, rows=None):
+def apply_testing(vertices, triangles, rwg, points, k, eta, F, rows=None):
     """Testing (Eq. 3) of channel fields F [npts, 4] at the quadrature points:
     y_m = -i eta k sum_p w_p sl [ (r_p - v).F_p/2 - F^rho_p / k^2 ] for m in rows."""
     r = rwg
@@ -165,7 +165,7 @@ class NesaOracle:
 
     def test(self, F, rows=None):
         """y_m = -i eta k sum_p w_p sl [ (r_p - v).F_p/2 - F^rho_p / k^2 ] for m in rows."""
-        return test_fields(self.vertices, self.triangles, self.rwg, self.tree.points, self.k, self.eta, F, rows)
+        return apply_testing(self.vertices, self.triangles, self.rwg, self.tree.points, self.k, self.eta, F, rows)
 
     # ---------------------------------------------------------------- near field
     def near_rows(self, rows=None):

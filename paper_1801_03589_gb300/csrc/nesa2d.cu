@@ -33,9 +33,9 @@
 #include "nesa_internal.h"
 
 namespace nesa2d_impl {
-
-// near-field kernel shape (k2_near): 8 warps, 4 rows per lane, tiles of 128 rows
-constexpr int NEAR_WARPS = 8, NEAR_RB = 4, NEAR_TROWS = 32 * NEAR_RB;
+// near-field kernel shape (k2_near): 8 warps, 2 rows per lane, tiles of 64 rows (leaves average P or
+// more points, so a 64-row tile leaves few lanes idle)
+constexpr int NEAR_WARPS = 8, NEAR_RB = 2, NEAR_TROWS = 32 * NEAR_RB;
 
 using nesa::Error;
 using nesa::fail;
@@ -500,7 +500,7 @@ __global__ void __launch_bounds__(32 * NEAR_WARPS) k2_near(double *__restrict__ 
         const double *__restrict__ xb = qp + (int64_t)r * n + rb;
         const int32_t j0 = (int32_t)((int64_t)warp * nb / NEAR_WARPS);
         const int32_t j1 = (int32_t)((int64_t)(warp + 1) * nb / NEAR_WARPS);
-#pragma unroll 2
+#pragma unroll 4
         for (int32_t j = j0; j < j1; ++j) {
           const double xj = __ldg(xb + j);
           const double *cj = col + (int64_t)j * na;

@@ -21,7 +21,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 from oracle.efie import ETA0, efie_rows  # noqa: E402
-from oracle.nesa import channel_sources, green, test_fields  # noqa: E402
+from oracle.nesa import channel_sources, green, apply_testing  # noqa: E402
 from oracle.quadrature import triangle_points  # noqa: E402
 from oracle.rwg import build_rwg  # noqa: E402
 from oracle.tree import leaf_geometry, point_leaf_coords  # noqa: E402
@@ -84,7 +84,7 @@ def test_large_far_rows_vs_exact_far_field(big):
             for p in range(7 * t, 7 * t + 7):
                 far = np.abs(leaf - leaf[p]).max(1) > 1
                 F[p] = green(c["k"], pts[p:p + 1], pts[far])[0] @ J[far]
-    exact = test_fields(c["vertices"], c["triangles"], rwg, pts, c["k"], ETA0, F, rows)
+    exact = apply_testing(c["vertices"], c["triangles"], rwg, pts, c["k"], ETA0, F, rows)
     yf = g.matvec(big["xd"], parts=nesa.PART_FAR).cpu().numpy()[0][rows]
     yfm = g.matvec(big["xd"], parts=nesa.PART_FAR | nesa.PART_MIXED).cpu().numpy()[0][rows]
     e, em = rel(yf, exact), rel(yfm, exact)
