@@ -167,6 +167,9 @@ typedef struct {
   int64_t device_bytes;             /* device memory held by the context */
   double build_seconds;             /* wall time of nesa_build */
   int64_t max_leaf_columns;         /* largest number of V columns of one leaf */
+  double build_split[4];            /* seconds of nesa_build in: mesh and RWG functions (host),
+                                       octree and box lists (device), near pattern and V lists
+                                       (host threads), operator fill (device); 0 from nesa_plan */
 } nesa_info;
 
 /* Default parameters: leaf 0.25, 3 levels, NESA_Q_AUTO, q_fixed 100, q_digits 5,

@@ -51,7 +51,8 @@ class Info(ctypes.Structure):
                 ("n_boxes", ctypes.c_int64 * MAX_LEVELS), ("n_interactions", ctypes.c_int64 * MAX_LEVELS),
                 ("n_offsets", ctypes.c_int64 * MAX_LEVELS), ("near_nnz", ctypes.c_int64),
                 ("near_tri_pairs", ctypes.c_int64), ("v_columns", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
-                ("build_seconds", ctypes.c_double), ("max_leaf_columns", ctypes.c_int64)]
+                ("build_seconds", ctypes.c_double), ("max_leaf_columns", ctypes.c_int64),
+                ("build_split", ctypes.c_double * 4)]
 
     def as_dict(self):
         nl = self.n_levels
@@ -60,6 +61,8 @@ class Info(ctypes.Structure):
                     n_interactions=list(self.n_interactions[:nl]), n_offsets=list(self.n_offsets[:nl]),
                     near_nnz=self.near_nnz, near_tri_pairs=self.near_tri_pairs, v_columns=self.v_columns,
                     device_bytes=self.device_bytes, build_seconds=self.build_seconds,
+                    build_split=dict(zip(("mesh_rwg_host", "tree_lists_device", "near_pattern_host",
+                                          "operators_device"), list(self.build_split))),
                     max_leaf_columns=self.max_leaf_columns)
 
 

@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnesa.so")
-SOURCES = ["nesa_host.cpp", "nesa_build.cu", "nesa_matvec.cu", "nesa_solve.cu", "nesa_noalloc.cu", "nesa_tc.cu", "nesa_precond.cu", "nesa_batch.cu", "nesa2d.cu"]
+SOURCES = ["nesa_host.cpp", "nesa_build.cu", "nesa_matvec.cu", "nesa_solve.cu", "nesa_noalloc.cu", "nesa_tree.cu", "nesa_tc.cu", "nesa_precond.cu", "nesa_batch.cu", "nesa2d.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 

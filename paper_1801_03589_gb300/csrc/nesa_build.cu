@@ -486,9 +486,9 @@ static void build_device(nesa_ctx *c, const nesa_params &p) {
   check_blas(cublasSetStream(hb, st), "stream");
   check_solver(cusolverDnSetStream(hs, st), "stream");
   try {
-    c->d_pts = upload(c, h.pts);
-    c->d_verts = upload(c, h.verts);
-    c->d_tris = upload(c, h.tris);
+    if (!c->d_pts) c->d_pts = upload(c, h.pts);  // the device tree uploaded these already
+    if (!c->d_verts) c->d_verts = upload(c, h.verts);
+    if (!c->d_tris) c->d_tris = upload(c, h.tris);
     c->d_tri_rwg = upload(c, h.tri_rwg);
     c->d_tri_sl = upload(c, h.tri_sl);
     c->d_rwg_tri = upload(c, h.rwg_tri);
@@ -810,9 +810,22 @@ int nesa_build(const nesa_mesh *mesh, double k, const nesa_params *params, nesa_
   c->translate_engine = params->translate;
   c->eta = 4e-7 * 3.14159265358979323846 * 299792458.0;
   try {
-    build_host_model(*mesh, k, *params, c->h);
+    // the host model with its octree and box lists built on the device
+    const auto th0 = std::chrono::steady_clock::now();
+    host_mesh(*mesh, c->h);
+    check_cuda(cudaGetDevice(&c->device), "current device");
+    const auto th1 = std::chrono::steady_clock::now();
+    device_tree(c, *params, c->h);
+    const auto th2 = std::chrono::steady_clock::now();
+    host_level_q(k, *params, c->h);
+    host_patterns(c->h);
+    const auto th3 = std::chrono::steady_clock::now();
+    c->build_split[0] = std::chrono::duration<double>(th1 - th0).count();
+    c->build_split[1] = std::chrono::duration<double>(th2 - th1).count();
+    c->build_split[2] = std::chrono::duration<double>(th3 - th2).count();
     c->info.near_tri_pairs = c->h.tp_ptr.empty() ? 0 : c->h.tp_ptr.back();
     build_device(c, *params);
+    c->build_split[3] = std::chrono::duration<double>(std::chrono::steady_clock::now() - th3).count();
     // drop the host arrays that the device copies replace
     c->h.tp_ptr.clear();
     c->h.tp_col.clear();
@@ -870,6 +883,7 @@ int nesa_build(const nesa_mesh *mesh, double k, const nesa_params *params, nesa_
   }
   I.device_bytes = (int64_t)c->device_bytes;
   I.build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  for (int i = 0; i < 4; ++i) I.build_split[i] = c->build_split[i];
   *out = c;
   return NESA_OK;
 }

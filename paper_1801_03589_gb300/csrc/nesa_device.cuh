@@ -84,6 +84,9 @@ struct nesa_ctx {
   nesa::HostModel h;
   cudaStream_t stream = nullptr;
   int device = -1;               // CUDA device current at nesa_build (holds all device memory)
+  // build time split (seconds): mesh and RWG functions (host), octree and box lists
+  // (device), near pattern and V lists (host threads), operator fill (device)
+  double build_split[4] = {0, 0, 0, 0};
   double k = 0.0, eta = 0.0;
   int64_t n = 0, nt = 0, np = 0, nleaf = 0;
   int L = 0, l0 = 0;
@@ -159,6 +162,10 @@ void check_cuda(cudaError_t e, const char *what);
 void launch_matvec(nesa_ctx *c, const cplx *x, cplx *y, int nrhs, int parts);
 // converted copies of the operator for the mixed-precision product
 void build_mixed(nesa_ctx *c);
+// the octree, its leaf lists and box lists on the device (nesa_tree.cu); fills the fields
+// of c->h that host_tree fills, identically, and leaves the mesh and the quadrature
+// points on the device (c->d_verts, c->d_tris, c->d_pts)
+void device_tree(nesa_ctx *c, const nesa_params &p, HostModel &m);
 // D_l(o) for the offset slots slot0 .. slot0 + ns - 1 of a generated level, into D
 // ([ns][q][q] column-major, complex128 or complex64), on the context's stream
 void fill_translations(nesa_ctx *c, int level, int64_t slot0, int64_t ns, cplx *D);

@@ -105,6 +105,8 @@ static uint64_t spread3(uint64_t x) {  // 21 bits -> every third bit
 static uint64_t morton(int32_t i, int32_t j, int32_t k) {
   return spread3((uint64_t)i) | (spread3((uint64_t)j) << 1) | (spread3((uint64_t)k) << 2);
 }
+uint64_t morton_key(int32_t i, int32_t j, int32_t k) { return morton(i, j, k); }
+void rule7_nodes(double bary[7][3]) { rule7(bary); }
 
 static void fibonacci_sphere(int n, double radius, std::vector<double> &out) {
   out.resize((size_t)n * 3);
@@ -172,7 +174,60 @@ static void build_rwg(HostModel &m) {
   if (m.n == 0) fail(NESA_ERR_MESH, "mesh has no interior edge");
 }
 
-void build_host_model(const nesa_mesh &mesh, double k, const nesa_params &p, HostModel &m) {
+// Integer coordinates of the boxes of a level from their Morton keys.
+void decode_keys(HostLevel &lv) {
+  lv.ijk.resize(lv.key.size() * 3);
+  for (size_t b = 0; b < lv.key.size(); ++b) {
+    uint64_t kk = lv.key[b];
+    int32_t c[3] = {0, 0, 0};
+    for (int bit = 0; bit < 21; ++bit)
+      for (int x = 0; x < 3; ++x) c[x] |= (int32_t)((kk >> (3 * bit + x)) & 1ULL) << bit;
+    for (int x = 0; x < 3; ++x) lv.ijk[3 * b + x] = c[x];
+  }
+}
+
+// Coarsest far level (Sec. 3): the coarsest level with at least 4 occupied boxes along
+// the longest extent of the vertex bounding box (the leaf level if none).
+int coarsest_far_level(const HostModel &m, const double lo[3], const double hi[3]) {
+  int axis = 0;
+  for (int x = 1; x < 3; ++x)
+    if (hi[x] - lo[x] > hi[axis] - lo[axis]) axis = x;
+  for (int l = 0; l <= m.L; ++l) {
+    std::vector<int32_t> c;
+    for (size_t b = 0; b < m.lev[l].key.size(); ++b) c.push_back(m.lev[l].ijk[3 * b + axis]);
+    std::sort(c.begin(), c.end());
+    c.erase(std::unique(c.begin(), c.end()), c.end());
+    if (c.size() >= 4) return l;
+  }
+  return m.L;
+}
+
+// Interaction list of a level from its pairs in list order (targets ascending): CSR by
+// target, and the slot of every pair's offset among the level's distinct offsets
+// (target - source, sorted lexicographically).
+void finish_interactions(HostLevel &lv, const std::vector<int32_t> &tgt, const std::vector<int32_t> &src,
+                         const std::vector<int32_t> &off) {
+  const size_t nbx = lv.key.size();
+  std::vector<std::array<int32_t, 3>> offs;
+  for (size_t e = 0; e < tgt.size(); ++e) offs.push_back({off[3 * e], off[3 * e + 1], off[3 * e + 2]});
+  std::sort(offs.begin(), offs.end());
+  offs.erase(std::unique(offs.begin(), offs.end()), offs.end());
+  lv.offsets.clear();
+  for (auto &o : offs) lv.offsets.insert(lv.offsets.end(), o.begin(), o.end());
+  lv.il_ptr.assign(nbx + 1, 0);
+  for (int32_t a : tgt) lv.il_ptr[a + 1]++;
+  for (size_t a = 0; a < nbx; ++a) lv.il_ptr[a + 1] += lv.il_ptr[a];
+  lv.il_src.resize(tgt.size());
+  lv.il_slot.resize(tgt.size());
+  for (size_t e = 0; e < tgt.size(); ++e) {  // tgt is ascending already
+    std::array<int32_t, 3> o = {off[3 * e], off[3 * e + 1], off[3 * e + 2]};
+    lv.il_src[e] = src[e];
+    lv.il_slot[e] = (int32_t)(std::lower_bound(offs.begin(), offs.end(), o) - offs.begin());
+  }
+}
+
+// Mesh copy, validation and RWG functions.
+void host_mesh(const nesa_mesh &mesh, HostModel &m) {
   m.nv = mesh.n_vertices;
   m.nt = mesh.n_triangles;
   m.verts.assign(mesh.vertices, mesh.vertices + 3 * m.nv);
@@ -192,24 +247,12 @@ void build_host_model(const nesa_mesh &mesh, double k, const nesa_params &p, Hos
     if (!(c2 > 1e-24 * l1 * l2)) fail(NESA_ERR_MESH, "degenerate triangle");
   }
   build_rwg(m);
+}
 
-  // quadrature points, lambda0 v0 + lambda1 v1 + lambda2 v2 evaluated left to right
-  double B[7][3];
-  rule7(B);
-  m.np = 7 * m.nt;
-  m.pts.resize((size_t)m.np * 3);
-  for (int64_t t = 0; t < m.nt; ++t)
-    for (int i = 0; i < 7; ++i)
-      for (int x = 0; x < 3; ++x) {
-        double v0 = m.verts[3 * (size_t)m.tris[3 * t + 0] + x];
-        double v1 = m.verts[3 * (size_t)m.tris[3 * t + 1] + x];
-        double v2 = m.verts[3 * (size_t)m.tris[3 * t + 2] + x];
-        double r = B[i][0] * v0 + B[i][1] * v1;
-        m.pts[(7 * t + i) * 3 + x] = r + B[i][2] * v2;
-      }
-
-  // root cube and leaf coordinates
-  double lo[3], hi[3];
+// Bounding box of the vertices and the root cube: sets m.L and m.origin, returns the root
+// side.  Needs the quadrature points (m.pts) only for the points_per_leaf rule.
+double host_root(const nesa_params &p, HostModel &m, double lo[3], double hi[3]) {
+  // root cube
   for (int x = 0; x < 3; ++x) {
     lo[x] = hi[x] = m.verts[x];
     for (int64_t v = 1; v < m.nv; ++v) {
@@ -262,6 +305,29 @@ void build_host_model(const nesa_mesh &mesh, double k, const nesa_params &p, Hos
     root = p.leaf_size * std::ldexp(1.0, m.L);
   }
   for (int x = 0; x < 3; ++x) m.origin[x] = 0.5 * (lo[x] + hi[x]) - 0.5 * root;
+  return root;
+}
+
+// Quadrature points, octree, leaf point lists, coarsest far level, interaction lists,
+// leaf triangle lists and leaf near lists (the part nesa_build runs on the device).
+void host_tree(const nesa_params &p, HostModel &m) {
+  // quadrature points, lambda0 v0 + lambda1 v1 + lambda2 v2 evaluated left to right
+  double B[7][3];
+  rule7(B);
+  m.np = 7 * m.nt;
+  m.pts.resize((size_t)m.np * 3);
+  for (int64_t t = 0; t < m.nt; ++t)
+    for (int i = 0; i < 7; ++i)
+      for (int x = 0; x < 3; ++x) {
+        double v0 = m.verts[3 * (size_t)m.tris[3 * t + 0] + x];
+        double v1 = m.verts[3 * (size_t)m.tris[3 * t + 1] + x];
+        double v2 = m.verts[3 * (size_t)m.tris[3 * t + 2] + x];
+        double r = B[i][0] * v0 + B[i][1] * v1;
+        m.pts[(7 * t + i) * 3 + x] = r + B[i][2] * v2;
+      }
+
+  double lo[3], hi[3];
+  const double root = host_root(p, m, lo, hi);
   const double wl = root / std::ldexp(1.0, m.L);
   const int32_t nb = 1 << m.L;
   m.pt_leaf_ijk.resize((size_t)m.np * 3);
@@ -295,14 +361,7 @@ void build_host_model(const nesa_mesh &mesh, double k, const nesa_params &p, Hos
           if (lv.key.empty() || lv.key.back() != pk) lv.key.push_back(pk);
         }
       }
-      lv.ijk.resize(lv.key.size() * 3);
-      for (size_t b = 0; b < lv.key.size(); ++b) {
-        uint64_t kk = lv.key[b];
-        int32_t c[3] = {0, 0, 0};
-        for (int bit = 0; bit < 21; ++bit)
-          for (int x = 0; x < 3; ++x) c[x] |= (int32_t)((kk >> (3 * bit + x)) & 1ULL) << bit;
-        for (int x = 0; x < 3; ++x) lv.ijk[3 * b + x] = c[x];
-      }
+      decode_keys(lv);
     }
     for (int l = 0; l <= m.L; ++l) {
       HostLevel &lv = m.lev[l];
@@ -327,23 +386,7 @@ void build_host_model(const nesa_mesh &mesh, double k, const nesa_params &p, Hos
     }
   }
 
-  // coarsest far level: at least 4 occupied boxes along the longest extent
-  {
-    int axis = 0;
-    for (int x = 1; x < 3; ++x)
-      if (hi[x] - lo[x] > hi[axis] - lo[axis]) axis = x;
-    m.l0 = m.L;
-    for (int l = 0; l <= m.L; ++l) {
-      std::vector<int32_t> c;
-      for (size_t b = 0; b < m.lev[l].key.size(); ++b) c.push_back(m.lev[l].ijk[3 * b + axis]);
-      std::sort(c.begin(), c.end());
-      c.erase(std::unique(c.begin(), c.end()), c.end());
-      if (c.size() >= 4) {
-        m.l0 = l;
-        break;
-      }
-    }
-  }
+  m.l0 = coarsest_far_level(m, lo, hi);
 
   // points per leaf
   const HostLevel &leaves = m.lev[m.L];
@@ -359,14 +402,9 @@ void build_host_model(const nesa_mesh &mesh, double k, const nesa_params &p, Hos
     for (int64_t q = 0; q < m.np; ++q) m.leaf_pt[fill[m.pt_leaf[q]]++] = (int32_t)q;
   }
 
-  // equivalent sources per level and interaction lists
+  // interaction lists
   for (int l = m.l0; l <= m.L; ++l) {
     HostLevel &lv = m.lev[l];
-    lv.q = q_for_level(k, lv.width, p);
-    if (lv.q <= 0 || lv.q > 16384) fail(NESA_ERR_INVALID_ARG, "number of equivalent sources out of range");
-    double R = std::sqrt(3.0) / 2.0 * lv.width;
-    fibonacci_sphere(lv.q, p.rho_eq * R, lv.eq_pts);
-    fibonacci_sphere(2 * lv.q, p.rho_test * R, lv.test_pts);
     const size_t nbx = lv.key.size();
     std::vector<int32_t> tgt, src, off;
     for (size_t a = 0; a < nbx; ++a) {
@@ -400,25 +438,59 @@ void build_host_model(const nesa_mesh &mesh, double k, const nesa_params &p, Hos
           for (int32_t b = pl.child_ptr[P2]; b < pl.child_ptr[P2 + 1]; ++b) add((size_t)b);
       }
     }
-    // distinct offsets, sorted lexicographically
-    std::vector<std::array<int32_t, 3>> offs;
-    for (size_t e = 0; e < tgt.size(); ++e) offs.push_back({off[3 * e], off[3 * e + 1], off[3 * e + 2]});
-    std::sort(offs.begin(), offs.end());
-    offs.erase(std::unique(offs.begin(), offs.end()), offs.end());
-    lv.offsets.clear();
-    for (auto &o : offs) lv.offsets.insert(lv.offsets.end(), o.begin(), o.end());
-    lv.il_ptr.assign(nbx + 1, 0);
-    for (int32_t a : tgt) lv.il_ptr[a + 1]++;
-    for (size_t a = 0; a < nbx; ++a) lv.il_ptr[a + 1] += lv.il_ptr[a];
-    lv.il_src.resize(tgt.size());
-    lv.il_slot.resize(tgt.size());
-    for (size_t e = 0; e < tgt.size(); ++e) {  // tgt is ascending already
-      std::array<int32_t, 3> o = {off[3 * e], off[3 * e + 1], off[3 * e + 2]};
-      lv.il_src[e] = src[e];
-      lv.il_slot[e] = (int32_t)(std::lower_bound(offs.begin(), offs.end(), o) - offs.begin());
+    finish_interactions(lv, tgt, src, off);
+  }
+  // triangles with a point in each leaf, and near leaves (touching, incl. itself) of each leaf
+  {
+    std::vector<int32_t> &leaf_tri_ptr = m.leaf_tri_ptr, &leaf_tri = m.leaf_tri;
+    leaf_tri_ptr.assign(nleaf + 1, 0);
+    leaf_tri.clear();
+    {
+      std::vector<std::pair<int32_t, int32_t>> lt;
+      lt.reserve(m.np);
+      for (int64_t q = 0; q < m.np; ++q) lt.push_back({m.pt_leaf[q], (int32_t)(q / 7)});
+      std::sort(lt.begin(), lt.end());
+      lt.erase(std::unique(lt.begin(), lt.end()), lt.end());
+      for (auto &x : lt) leaf_tri_ptr[x.first + 1]++;
+      for (int64_t b = 0; b < nleaf; ++b) leaf_tri_ptr[b + 1] += leaf_tri_ptr[b];
+      leaf_tri.resize(lt.size());
+      for (size_t i = 0; i < lt.size(); ++i) leaf_tri[i] = lt[i].second;
+    }
+    // near leaves of every leaf
+    std::vector<int32_t> &nl_ptr = m.nl_ptr, &nl = m.nl;
+    nl_ptr.assign(nleaf + 1, 0);
+    nl.clear();
+    for (int64_t b = 0; b < nleaf; ++b) {
+      const int32_t *c = &leaves.ijk[3 * b];
+      for (int dx = -1; dx <= 1; ++dx)
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dz = -1; dz <= 1; ++dz) {
+            int32_t x = c[0] + dx, y = c[1] + dy, z = c[2] + dz;
+            if (x < 0 || y < 0 || z < 0 || x >= nb || y >= nb || z >= nb) continue;
+            int nb2 = find_box(leaves, morton(x, y, z));
+            if (nb2 >= 0) nl.push_back(nb2);
+          }
+      nl_ptr[b + 1] = (int32_t)nl.size();
     }
   }
+}
 
+// Equivalent and test points of every far level (Q per level by the q_mode rule).
+void host_level_q(double k, const nesa_params &p, HostModel &m) {
+  for (int l = m.l0; l <= m.L; ++l) {
+    HostLevel &lv = m.lev[l];
+    lv.q = q_for_level(k, lv.width, p);
+    if (lv.q <= 0 || lv.q > 16384) fail(NESA_ERR_INVALID_ARG, "number of equivalent sources out of range");
+    double R = std::sqrt(3.0) / 2.0 * lv.width;
+    fibonacci_sphere(lv.q, p.rho_eq * R, lv.eq_pts);
+    fibonacci_sphere(2 * lv.q, p.rho_test * R, lv.test_pts);
+  }
+}
+
+// V columns and reception map, near triangle pairs (with the check that every pair of
+// triangles sharing a vertex is near) and the RWG near pattern.
+void host_patterns(HostModel &m) {
+  const int64_t nleaf = (int64_t)m.lev[m.L].key.size();
   // V columns: RWG functions with a point in each leaf
   {
     m.vc_ptr.assign(nleaf + 1, 0);
@@ -447,32 +519,7 @@ void build_host_model(const nesa_mesh &mesh, double k, const nesa_params &p, Hos
   // near triangle pairs: inner triangles with a point in a leaf touching a leaf of the
   // outer triangle's points
   {
-    std::vector<int32_t> leaf_tri_ptr(nleaf + 1, 0), leaf_tri;
-    {
-      std::vector<std::pair<int32_t, int32_t>> lt;
-      lt.reserve(m.np);
-      for (int64_t q = 0; q < m.np; ++q) lt.push_back({m.pt_leaf[q], (int32_t)(q / 7)});
-      std::sort(lt.begin(), lt.end());
-      lt.erase(std::unique(lt.begin(), lt.end()), lt.end());
-      for (auto &x : lt) leaf_tri_ptr[x.first + 1]++;
-      for (int64_t b = 0; b < nleaf; ++b) leaf_tri_ptr[b + 1] += leaf_tri_ptr[b];
-      leaf_tri.resize(lt.size());
-      for (size_t i = 0; i < lt.size(); ++i) leaf_tri[i] = lt[i].second;
-    }
-    // near leaves of every leaf
-    std::vector<int32_t> nl_ptr(nleaf + 1, 0), nl;
-    for (int64_t b = 0; b < nleaf; ++b) {
-      const int32_t *c = &leaves.ijk[3 * b];
-      for (int dx = -1; dx <= 1; ++dx)
-        for (int dy = -1; dy <= 1; ++dy)
-          for (int dz = -1; dz <= 1; ++dz) {
-            int32_t x = c[0] + dx, y = c[1] + dy, z = c[2] + dz;
-            if (x < 0 || y < 0 || z < 0 || x >= nb || y >= nb || z >= nb) continue;
-            int nb2 = find_box(leaves, morton(x, y, z));
-            if (nb2 >= 0) nl.push_back(nb2);
-          }
-      nl_ptr[b + 1] = (int32_t)nl.size();
-    }
+    const std::vector<int32_t> &leaf_tri_ptr = m.leaf_tri_ptr, &leaf_tri = m.leaf_tri, &nl_ptr = m.nl_ptr, &nl = m.nl;
     // near triangles of triangle t (ascending): every triangle with a point in a leaf
     // touching a leaf of one of t's points; rows computed in parallel
     {
@@ -539,6 +586,13 @@ void build_host_model(const nesa_mesh &mesh, double k, const nesa_params &p, Hos
       });
     }
   }
+}
+
+void build_host_model(const nesa_mesh &mesh, double k, const nesa_params &p, HostModel &m) {
+  host_mesh(mesh, m);
+  host_tree(p, m);
+  host_level_q(k, p, m);
+  host_patterns(m);
 }
 
 }  // namespace nesa

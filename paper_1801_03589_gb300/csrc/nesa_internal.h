@@ -63,6 +63,9 @@ struct HostModel {
   std::vector<int32_t> vc_ptr, vc_rwg;
   // reception map: for each RWG the global V columns it owns, CSR by RWG
   std::vector<int32_t> rx_ptr, rx_col;
+  // triangles with a point in each leaf (CSR by leaf, ascending) and the touching leaves
+  // of each leaf, itself included (CSR by leaf)
+  std::vector<int32_t> leaf_tri_ptr, leaf_tri, nl_ptr, nl;
   // near field: triangle pairs (CSR by outer triangle, ascending inner) and the RWG
   // pattern (CSR by row, ascending columns)
   std::vector<int64_t> tp_ptr;
@@ -72,6 +75,29 @@ struct HostModel {
 };
 
 void build_host_model(const nesa_mesh &mesh, double k, const nesa_params &p, HostModel &m);
+// The stages of build_host_model, in order (nesa_build replaces host_tree by its device
+// counterpart, which fills the same fields):
+//   host_mesh     mesh copy, validation, RWG functions
+//   host_tree     quadrature points, octree levels, leaf point lists, l0, interaction
+//                 lists, leaf triangle lists, leaf near lists
+//   host_level_q  Q, equivalent and test points per far level
+//   host_patterns V columns, reception map, near triangle pairs, RWG near pattern
+void host_mesh(const nesa_mesh &mesh, HostModel &m);
+void host_tree(const nesa_params &p, HostModel &m);
+void host_level_q(double k, const nesa_params &p, HostModel &m);
+void host_patterns(HostModel &m);
+// root cube of the tree (sets m.L and m.origin from the vertex bounding box lo, hi, which
+// it fills); m.pts must hold the quadrature points when p.points_per_leaf > 0
+double host_root(const nesa_params &p, HostModel &m, double lo[3], double hi[3]);
+// Morton key of integer box coordinates (bits of i, j, k interleaved, i lowest)
+uint64_t morton_key(int32_t i, int32_t j, int32_t k);
+// Radon's 7-point rule: barycentric coordinates of the nodes [7][3]
+void rule7_nodes(double bary[7][3]);
+// shared pieces of host_tree and its device counterpart
+void decode_keys(HostLevel &lv);
+int coarsest_far_level(const HostModel &m, const double lo[3], const double hi[3]);
+void finish_interactions(HostLevel &lv, const std::vector<int32_t> &tgt, const std::vector<int32_t> &src,
+                         const std::vector<int32_t> &off);
 
 // Q of one level (NESA_Q_FIXED / NESA_Q_AUTO rule).
 int q_for_level(double k, double width, const nesa_params &p);
