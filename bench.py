@@ -477,15 +477,16 @@ def run_model2d(args, stream, world, barrier, max_over_ranks):
     return out
 
 
-def run_large(args, stream, world, barrier, max_over_ranks):
-    """The r = 16 sphere (1,966,080 RWG, 9 levels, Q up to 4,096), 16 right-hand sides:
-    build, the mixed product of all 16 columns, the FP64 product of one column, and the
-    mixed product's error against it.  The two coarsest far levels (FP64 tables of 85
-    and 10.5 GB) are generated when used."""
+def run_large(args, stream, world, barrier, max_over_ranks, name):
+    """A large workload at full size: the r = 16 sphere (C5: 1,966,080 RWG, 9 levels, Q up
+    to 4,096, 16 right-hand sides) or the aircraft body scaled to 52 wavelengths (C4L:
+    516,413 RWG, Q up to 12,544, 8 right-hand sides).  Build, the mixed product of all
+    right-hand sides, the FP64 product of one, and the mixed product's error against it.
+    The coarse far levels whose FP64 tables would exceed 6 GB are generated when used."""
     import torch
 
     import paper_1801_03589_gb300 as nesa
-    cfg = get_config("C5")
+    cfg = get_config(name)
     nrhs = cfg["nrhs"]
     t0 = time.perf_counter()
     g = nesa.Nesa(cfg["vertices"], cfg["triangles"], cfg["k"], leaf_size=cfg["leaf_size"],
@@ -529,9 +530,10 @@ def run_large(args, stream, world, barrier, max_over_ranks):
     gemm_tf = gemm["flops"] / (gemm["ms"] * 1e-3) / 1e12 if gemm["ms"] > 0 else None
     l0, L = info["l0"], info["n_levels"] - 1
     generated = [l for l in range(l0, L + 1) if 16.0 * info["n_offsets"][l] * info["q"][l] ** 2 > 6e9]
-    out = {"workload": "C5: %s; %d right-hand sides" % (cfg["description"], nrhs),
+    out = {"workload": "%s: %s; %d right-hand sides" % (name, cfg["description"], nrhs),
            "n_unknowns": g.n, "levels": info["n_levels"], "l0": l0, "q": info["q"][l0:],
            "near_nnz": info["near_nnz"], "device_gb": g.info()["device_bytes"] / 1e9, "build_s": build_s,
+           "build_split_s": info["build_split"],
            "generated_levels": generated,
            "mixed": {"ms_per_product": ms_mx, "nrhs": nrhs, "matvec_per_s": job_throughput(world, nrhs, ms_mx),
                      "tensor_gemm_ms": gemm["ms"], "tensor_gemm_tflops": gemm_tf,
@@ -702,14 +704,17 @@ def run_ours(args, world, rank, local):
                  "tile_n": [{l: t["tile_n"] for l, t in m.tuning().items()} for m in members]}
         bt.close()
 
-    # the r = 16 sphere at full size (generated coarse translations); a failure here is
-    # reported in the block and leaves the rest of the line intact
+    # the r = 16 sphere and the 52-wavelength aircraft at full size (generated coarse
+    # translations); a failure here is reported in the block and leaves the rest of the
+    # line intact
     large = None
     if not args.no_large:
-        try:
-            large = run_large(args, stream, world, barrier, max_over_ranks)
-        except Exception as e:  # noqa: BLE001
-            large = {"error": "%s: %s" % (type(e).__name__, e)}
+        large = {}
+        for name in ("C5", "C4L"):
+            try:
+                large[name] = run_large(args, stream, world, barrier, max_over_ranks, name)
+            except Exception as e:  # noqa: BLE001
+                large[name] = {"error": "%s: %s" % (type(e).__name__, e)}
 
     # the paper's 2D model problem at its size (a separate library path; a failure here
     # is reported in the block and leaves the rest of the line intact)
@@ -805,7 +810,7 @@ def run_ours(args, world, rank, local):
                    "product": "FP64: complex128 operator, FP64 kernels (the paper's arithmetic)",
                    "levels": info["n_levels"], "l0": info["l0"], "q": info["q"][info["l0"]:],
                    "near_nnz": info["near_nnz"], "device_gb": info["device_bytes"] / 1e9,
-                   "build_s": info["build_seconds"],
+                   "build_s": info["build_seconds"], "build_split_s": info["build_split"],
                    "l2": "operator data %.1f GB (FP64) / %.1f GB (mixed) per product > 129 MB L2, no flush needed" % (
                        sum(v["bytes"] for v in prof64.values()) / args.steps / 1e9,
                        sum(v["bytes"] for v in prof_mx.values()) / args.steps / 1e9),
@@ -852,7 +857,8 @@ def main():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-model2d", action="store_true", help="skip the 2D model problem block")
-    ap.add_argument("--no-large", action="store_true", help="skip the r = 16 sphere block (about 90 s)")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the r = 16 sphere and 52-wavelength aircraft blocks (about 5 minutes)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-preconditioner block (aircraft body)")
     ap.add_argument("--fp64-solve", action="store_true", help="also time the unpreconditioned FP64 solve (about 2.5 minutes)")
     ap.add_argument("--workload", default=CONFIG, help="workload name (smaller ones are for profiling runs)")
