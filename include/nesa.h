@@ -90,7 +90,9 @@ typedef struct {
  * Octree and equivalent-source parameters (Sec. 2 and Sec. 3).
  *   leaf_size   side of a leaf box; the root cube has side leaf_size * 2^(n_levels-1)
  *               and is centred on the centre of the vertex bounding box
- *   n_levels    number of octree levels (root = level 0, leaves = level n_levels-1), 1..20
+ *   n_levels    number of octree levels (root = level 0, leaves = level n_levels-1), 1..20;
+ *               with leaf_size > 0, 0 selects the fewest levels whose root cube
+ *               (leaf_size * 2^(levels-1)) spans the largest side of the bounding box
  *   q_mode      NESA_Q_FIXED or NESA_Q_AUTO
  *   q_fixed     Q for NESA_Q_FIXED; lower bound of Q_l for NESA_Q_AUTO
  *   q_digits    d of the NESA_Q_AUTO rule
@@ -110,8 +112,6 @@ typedef struct {
  *               (same centre), and the leaf level is the deepest level l <= 19 whose
  *               occupied boxes hold on average at least P quadrature points (7 per
  *               triangle).  n_levels is then ignored.  0 when leaf_size > 0.
- *   n_levels    with leaf_size > 0, 0 selects the fewest levels whose root cube
- *               (leaf_size * 2^(levels-1)) spans the largest side of the bounding box
  *   singular_mode  NESA_SINGULAR_TOUCHING (default) or NESA_SINGULAR_SELF
  *   translation_tables  NESA_TABLES_AUTO (default), NESA_TABLES_STORED or
  *               NESA_TABLES_GENERATED: whether the translation matrices D_l(o) of Eq. 12
@@ -125,7 +125,7 @@ typedef struct {
  *               FP64 tables would exceed 6 GB (both products), and stores the others:
  *               generating a tile costs about twice streaming it from device memory.
  */
-#define NESA_TABLES_AUTO 0      /* translation matrices: generated where large or little reused */
+#define NESA_TABLES_AUTO 0      /* translation matrices: generated where the tables would not fit */
 #define NESA_TABLES_STORED 1    /* every translation matrix stored */
 #define NESA_TABLES_GENERATED 2 /* every translation matrix generated when used */
 #define NESA_SINGULAR_TOUCHING 0 /* singularity extraction for every triangle pair sharing a vertex */

@@ -658,58 +658,75 @@ static void ras_setup(nesa_ctx *c) {
   check_cuda(cudaMalloc(&d_pos, sizeof(int32_t) * gpos.size()), "ras pos");
   check_cuda(cudaMemcpy(d_pos, gpos.data(), sizeof(int32_t) * gpos.size(), cudaMemcpyHostToDevice), "ras pos");
   // per group: LU of the extended block (complex64, cuSOLVER), solve A^T X = unit columns
-  // of g's positions, keep R_g = X^T
-  cusolverDnHandle_t hs = nullptr;
-  if (cusolverDnCreate(&hs) != CUSOLVER_STATUS_SUCCESS) fail(NESA_ERR_CUDA, "cusolver create");
-  cusolverDnSetStream(hs, c->stream);
-  cplxf *A = nullptr, *X = nullptr, *work = nullptr;
-  int *ipiv = nullptr, *dinfo = nullptr;
+  // of g's positions, keep R_g = X^T.  The groups are independent: they go round-robin
+  // over NS streams, each with its own solver handle and buffers, started behind an
+  // event on the context's stream; the host waits for all of them before returning.
+  constexpr int NS = 8;
   const int emax = P->emax, smax = P->smax;
-  int lwork = 0;
+  struct Lane {
+    cudaStream_t st = nullptr;
+    cusolverDnHandle_t hs = nullptr;
+    cplxf *A = nullptr, *X = nullptr, *work = nullptr;
+    int *ipiv = nullptr;
+  } lane[NS];
+  int *dinfo = nullptr;
+  cudaEvent_t ev_start = nullptr;
+  auto release = [&]() {
+    for (Lane &q : lane) {
+      if (q.st) cudaStreamSynchronize(q.st);
+      cudaFree(q.A);
+      cudaFree(q.X);
+      cudaFree(q.work);
+      cudaFree(q.ipiv);
+      if (q.hs) cusolverDnDestroy(q.hs);
+      if (q.st) cudaStreamDestroy(q.st);
+    }
+    cudaFree(dinfo);
+    cudaFree(d_pos);
+    if (ev_start) cudaEventDestroy(ev_start);
+  };
   try {
-    check_cuda(cudaMalloc(&A, sizeof(cplxf) * (size_t)emax * emax), "ras A");
-    check_cuda(cudaMalloc(&X, sizeof(cplxf) * (size_t)emax * smax), "ras X");
-    check_cuda(cudaMalloc(&ipiv, sizeof(int) * emax), "ras piv");
-    check_cuda(cudaMalloc(&dinfo, sizeof(int) * (ng + 1)), "ras info");  // getrf per group; getrs last
-    if (cusolverDnCgetrf_bufferSize(hs, emax, emax, (cuComplex *)A, emax, &lwork) != CUSOLVER_STATUS_SUCCESS)
-      fail(NESA_ERR_CUDA, "cusolver getrf size");
-    check_cuda(cudaMalloc(&work, sizeof(cplxf) * (size_t)std::max(1, lwork)), "ras work");
+    check_cuda(cudaMalloc(&dinfo, sizeof(int) * (ng + NS)), "ras info");  // getrf per group; getrs per lane
+    check_cuda(cudaEventCreateWithFlags(&ev_start, cudaEventDisableTiming), "ras event");
+    check_cuda(cudaEventRecord(ev_start, c->stream), "ras event");
+    for (Lane &q : lane) {
+      check_cuda(cudaStreamCreateWithFlags(&q.st, cudaStreamNonBlocking), "ras stream");
+      check_cuda(cudaStreamWaitEvent(q.st, ev_start, 0), "ras wait");
+      if (cusolverDnCreate(&q.hs) != CUSOLVER_STATUS_SUCCESS) fail(NESA_ERR_CUDA, "cusolver create");
+      cusolverDnSetStream(q.hs, q.st);
+      int lwork = 0;
+      check_cuda(cudaMalloc(&q.A, sizeof(cplxf) * (size_t)emax * emax), "ras A");
+      check_cuda(cudaMalloc(&q.X, sizeof(cplxf) * (size_t)emax * smax), "ras X");
+      check_cuda(cudaMalloc(&q.ipiv, sizeof(int) * emax), "ras piv");
+      if (cusolverDnCgetrf_bufferSize(q.hs, emax, emax, (cuComplex *)q.A, emax, &lwork) != CUSOLVER_STATUS_SUCCESS)
+        fail(NESA_ERR_CUDA, "cusolver getrf size");
+      check_cuda(cudaMalloc(&q.work, sizeof(cplxf) * (size_t)std::max(1, lwork)), "ras work");
+    }
     for (int64_t g = 0; g < ng; ++g) {
+      Lane &q = lane[g % NS];
       const int ne = eptr[g + 1] - eptr[g], s = P->h_gptr[g + 1] - P->h_gptr[g];
-      k_ext_block<<<nblk((int64_t)ne * ne, 256), 256, 0, c->stream>>>(A, P->e_rwg + eptr[g], ne, c->d_nz_ptr,
-                                                                       c->d_nz_col, c->d_nz_val);
-      if (cusolverDnCgetrf(hs, ne, ne, (cuComplex *)A, ne, (cuComplex *)work, ipiv, dinfo + g) !=
+      k_ext_block<<<nblk((int64_t)ne * ne, 256), 256, 0, q.st>>>(q.A, P->e_rwg + eptr[g], ne, c->d_nz_ptr,
+                                                                  c->d_nz_col, c->d_nz_val);
+      if (cusolverDnCgetrf(q.hs, ne, ne, (cuComplex *)q.A, ne, (cuComplex *)q.work, q.ipiv, dinfo + g) !=
           CUSOLVER_STATUS_SUCCESS)
         fail(NESA_ERR_CUDA, "cusolver getrf");
-      k_unit_cols<<<nblk((int64_t)ne * s, 256), 256, 0, c->stream>>>(X, d_pos + P->h_gptr[g], ne, s);
-      if (cusolverDnCgetrs(hs, CUBLAS_OP_T, ne, s, (const cuComplex *)A, ne, ipiv, (cuComplex *)X, ne, dinfo + ng) !=
-          CUSOLVER_STATUS_SUCCESS)
+      k_unit_cols<<<nblk((int64_t)ne * s, 256), 256, 0, q.st>>>(q.X, d_pos + P->h_gptr[g], ne, s);
+      if (cusolverDnCgetrs(q.hs, CUBLAS_OP_T, ne, s, (const cuComplex *)q.A, ne, q.ipiv, (cuComplex *)q.X, ne,
+                           dinfo + ng + g % NS) != CUSOLVER_STATUS_SUCCESS)
         fail(NESA_ERR_CUDA, "cusolver getrs");
-      k_take_rows<<<nblk((int64_t)ne * s, 256), 256, 0, c->stream>>>(P->R + roff[g], X, ne, s);
+      k_take_rows<<<nblk((int64_t)ne * s, 256), 256, 0, q.st>>>(P->R + roff[g], q.X, ne, s);
     }
     check_cuda(cudaGetLastError(), "ras setup");
+    for (Lane &q : lane) check_cuda(cudaStreamSynchronize(q.st), "ras setup");
     std::vector<int> info(ng);
-    check_cuda(cudaMemcpyAsync(info.data(), dinfo, sizeof(int) * ng, cudaMemcpyDeviceToHost, c->stream), "info");
-    check_cuda(cudaStreamSynchronize(c->stream), "ras setup");
+    check_cuda(cudaMemcpy(info.data(), dinfo, sizeof(int) * ng, cudaMemcpyDeviceToHost), "info");
     for (int v : info)
       if (v != 0) fail(NESA_ERR_NUMERIC, "singular extended near-field block");
   } catch (...) {
-    cudaFree(A);
-    cudaFree(X);
-    cudaFree(work);
-    cudaFree(ipiv);
-    cudaFree(dinfo);
-    cudaFree(d_pos);
-    cusolverDnDestroy(hs);
+    release();
     throw;
   }
-  cudaFree(A);
-  cudaFree(X);
-  cudaFree(work);
-  cudaFree(ipiv);
-  cudaFree(dinfo);
-  cudaFree(d_pos);
-  cusolverDnDestroy(hs);
+  release();
   P->ras_ready = true;
 }
 
