@@ -51,8 +51,9 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # the r = 3 sphere (ncu, dram__bytes_read.sum + dram__bytes_write.sum); null elsewhere
 GEMM_DRAM_BYTES_C2 = 1.5083e9
 # DRAM traffic of the FP64 translation launches (k_translate<double2>) of one product of
-# the r = 3 sphere; None until measured on the current kernel
-K_TRANSLATE64_DRAM_BYTES_C2 = None
+# the r = 3 sphere (ncu: dram__bytes_read.sum + dram__bytes_write.sum of the 4 launches of one
+# product, captured on the current kernel with `--profile-run fp64_C2`)
+K_TRANSLATE64_DRAM_BYTES_C2 = 13.0865e9
 SPEC = ("PEC sphere r=3 wavelengths, icosphere subdiv 6 (81,920 triangles, 122,880 RWG), "
         "6-level octree, leaf 0.25 wavelength, 1 RHS")
 
@@ -847,6 +848,71 @@ def run_ours(args, world, rank, local):
     return 0
 
 
+def large_solve(name, max_iters, restart):
+    """Mixed solve with FP64 refinement to 1e-5 of a large workload, all its right-hand
+    sides (plane waves, seed 180103589) in lock step, overlapping block-Jacobi.  Prints
+    one JSON line (setup, solve time, iterations, refinements, true FP64 residuals)."""
+    import torch
+
+    import paper_1801_03589_gb300 as nesa
+    c = get_config(name)
+    nrhs = c["nrhs"]
+    t0 = time.perf_counter()
+    g = nesa.Nesa(c["vertices"], c["triangles"], c["k"], leaf_size=c["leaf_size"], n_levels=c["n_levels"],
+                  precision=nesa.MIXED, translate=nesa.TRANSLATE_TENSOR)
+    out = {"workload": "%s: %s" % (name, c["description"]), "n_unknowns": g.n, "nrhs": nrhs,
+           "build_s": time.perf_counter() - t0}
+    kh, pol = plane_wave_directions(nrhs, seed=180103589)
+    b = g.rhs_planewave(kh, pol)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g.precond_apply(b[:1].contiguous(), nesa.PRECOND_OVERLAP)
+    torch.cuda.synchronize()
+    out["overlap_setup_s"] = time.perf_counter() - t0
+    _, si = g.solve(b, tol=1e-5, restart=restart, max_iters=max_iters, check=False, mixed=True, inner_tol=3e-3,
+                    precond=nesa.PRECOND_OVERLAP, max_refine=6)
+    out["solve"] = {k: si[k] for k in ("status", "seconds", "iterations", "refinements", "fp64_matvecs", "matvecs")}
+    out["solve"]["restart"] = restart
+    out["solve"]["true_rel_residual"] = si["rel_residual"][:nrhs]
+    out["device_gb"] = g.info()["device_bytes"] / 1e9
+    print(json.dumps(out))
+    return 0
+
+
+PROFILE_RUNS = ("fp64_C2", "fp64_C3a", "tensor_C3a_generated", "tensor_C3a_stored", "model2d_N1e5_P300_Q100")
+
+
+def profile_run(name):
+    """A small fixed workload for profiler captures: build, two products, exit 0."""
+    import torch
+
+    import paper_1801_03589_gb300 as nesa
+    if name.startswith("fp64_"):
+        c = get_config(name.split("_")[1])
+        g = nesa.Nesa(c["vertices"], c["triangles"], c["k"], leaf_size=c["leaf_size"], n_levels=c["n_levels"])
+        x = torch.from_numpy(random_coefficients(g.n, 1, seed=5)).cuda()
+        for _ in range(2):
+            g.matvec(x)
+    elif name.startswith("tensor_"):
+        c = get_config("C3a")
+        tables = nesa.TABLES_GENERATED if name.endswith("generated") else nesa.TABLES_STORED
+        g = nesa.Nesa(c["vertices"], c["triangles"], c["k"], leaf_size=c["leaf_size"], n_levels=c["n_levels"],
+                      precision=nesa.MIXED, translate=nesa.TRANSLATE_TENSOR, tile_n=128, translation_tables=tables)
+        x = torch.from_numpy(random_coefficients(g.n, 1, seed=5)).cuda()
+        for _ in range(2):
+            g.matvec(x, parts=nesa.PART_ALL | nesa.PART_MIXED)
+    else:
+        from workloads.curve2d import charges, curve_points
+        n = 100_000
+        g = nesa.Model2D(curve_points(n, seed=1), 300, 100)
+        q = torch.from_numpy(charges(n, seed=1)).cuda()
+        for _ in range(2):
+            g.matvec(q)
+    torch.cuda.synchronize()
+    print("profile run %s: ok" % name)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -864,7 +930,16 @@ def main():
     ap.add_argument("--workload", default=CONFIG, help="workload name (smaller ones are for profiling runs)")
     ap.add_argument("--tile-n", type=int, default=0, choices=[0, 64, 128, 256],
                     help="fixed column-tile width of the tensor GEMMs (0: autotune); for runs under a profiler")
+    ap.add_argument("--profile-run", choices=PROFILE_RUNS,
+                    help="build one small fixed workload, run two products and exit (for ncu captures)")
+    ap.add_argument("--large-solve", choices=["C5", "C4L"],
+                    help="only a mixed solve to 1e-5 of a large workload (tens of minutes), one JSON line")
+    ap.add_argument("--large-solve-iters", type=int, default=2500)
     args = ap.parse_args()
+    if args.profile_run:
+        return profile_run(args.profile_run)
+    if args.large_solve:
+        return large_solve(args.large_solve, args.large_solve_iters, 50)
     world, rank, local = dist_setup()
     if args.impl == "reference":
         return run_reference(args, world, rank)
