@@ -53,7 +53,7 @@ struct Level {
   std::vector<int32_t> il_ptr, il_src, il_slot;
   std::vector<int32_t> offsets;             // [noff][2] target - source, sorted
   // device
-  double *D = nullptr, *C = nullptr, *s = nullptr, *o = nullptr;
+  double *D = nullptr, *C = nullptr, *Ct = nullptr, *s = nullptr, *o = nullptr;  // Ct: C transposed per quadrant
   int32_t *d_parent = nullptr, *d_quad = nullptr, *d_child_ptr = nullptr;
   int32_t *d_il_ptr = nullptr, *d_il_src = nullptr, *d_il_slot = nullptr;
 };
@@ -430,6 +430,11 @@ static void build(nesa2d_ctx *c, const double *x) {
         matmul(K[l - 1], Q, 2 * Q, G.data(), Q, &Cm[(size_t)qd * Q * Q]);
       }
       lv.C = upload(c, Cm);
+      std::vector<double> Ctm(Cm.size());  // B = C^T of every quadrant, column-major
+      for (int qd = 0; qd < 4; ++qd)
+        for (int j = 0; j < Q; ++j)
+          for (int i = 0; i < Q; ++i) Ctm[(size_t)qd * Q * Q + (size_t)j * Q + i] = Cm[(size_t)qd * Q * Q + (size_t)i * Q + j];
+      lv.Ct = upload(c, Ctm);
     }
     lv.d_parent = upload(c, lv.parent);
     lv.d_quad = upload(c, lv.quad);
@@ -522,72 +527,116 @@ __global__ void __launch_bounds__(32 * NEAR_WARPS) k2_near(double *__restrict__ 
   }
 }
 
-// Eq. 10: block b, thread = equivalent point k
-__global__ void k2_radiate(double *sL, const double *V, const double *qp, int64_t n, int nrhs,
-                           const int32_t *leaf_ptr, int q) {
+// Far-field kernels (Eqs. 10-14 in 2D).  Each output block of Q values (a group's
+// equivalent charges or potentials) is a sum of column-major matrix columns times
+// scalars: a CTA owns the block, its 8 warps split the columns of every matrix between
+// them, each lane accumulates the rows k0 + lane + 32 rr (FAR_KR rows, chunks of
+// FAR_TROWS rows for larger Q), and the 8 partial sums are added in warp order
+// (deterministic).  Every column is one coalesced load per row group.
+constexpr int FAR_WARPS = 8, FAR_KR = 4, FAR_TROWS = 32 * FAR_KR;
+
+__device__ __forceinline__ void far_col(double (&acc)[FAR_KR], const double *__restrict__ col, double xj, int k0,
+                                        int q, int lane) {
+#pragma unroll
+  for (int rr = 0; rr < FAR_KR; ++rr) {
+    const int k = k0 + lane + 32 * rr;
+    if (k < q) acc[rr] = fma(__ldg(col + k), xj, acc[rr]);
+  }
+}
+
+// columns [w len / 8, (w+1) len / 8) of a q x len panel M (column-major) times x
+__device__ __forceinline__ void far_panel(double (&acc)[FAR_KR], const double *__restrict__ M,
+                                          const double *__restrict__ x, int len, int k0, int q) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j0 = (int)((int64_t)warp * len / FAR_WARPS), j1 = (int)((int64_t)(warp + 1) * len / FAR_WARPS);
+#pragma unroll 2
+  for (int j = j0; j < j1; ++j) far_col(acc, M + (int64_t)j * q, __ldg(x + j), k0, q, lane);
+}
+
+__device__ __forceinline__ void far_store(double (&acc)[FAR_KR], double (*red)[FAR_TROWS], double *__restrict__ out,
+                                          int k0, int q) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int rr = 0; rr < FAR_KR; ++rr) red[warp][lane + 32 * rr] = acc[rr];
+  __syncthreads();
+  if (threadIdx.x < FAR_TROWS && k0 + (int)threadIdx.x < q) {
+    double sum = 0.0;
+#pragma unroll
+    for (int w = 0; w < FAR_WARPS; ++w) sum += red[w][threadIdx.x];
+    out[k0 + threadIdx.x] = sum;
+  }
+  __syncthreads();
+}
+
+// Eq. 10: CTA = leaf b; columns = the leaf's points (V_b is q x |b|, column j at point j)
+__global__ void __launch_bounds__(32 * FAR_WARPS) k2_radiate(double *sL, const double *V, const double *qp, int64_t n,
+                                                            int nrhs, const int32_t *leaf_ptr, int q) {
+  __shared__ double red[FAR_WARPS][FAR_TROWS];
   const int64_t b = blockIdx.x;
   const int32_t r0 = leaf_ptr[b], nb = leaf_ptr[b + 1] - r0;
   const double *Vb = V + (int64_t)q * r0;
-  for (int k = threadIdx.x; k < q; k += blockDim.x)
-    for (int r = 0; r < nrhs; ++r) {
-      double acc = 0.0;
-      const double *qb = qp + (int64_t)r * n + r0;
-      for (int32_t j = 0; j < nb; ++j) acc += Vb[(int64_t)j * q + k] * qb[j];
-      sL[(b * nrhs + r) * q + k] = acc;
+  for (int r = 0; r < nrhs; ++r)
+    for (int k0 = 0; k0 < q; k0 += FAR_TROWS) {
+      double acc[FAR_KR] = {};
+      far_panel(acc, Vb, qp + (int64_t)r * n + r0, nb, k0, q);
+      far_store(acc, red, sL + (b * nrhs + r) * q, k0, q);
     }
 }
 
-// Eq. 11: block = parent p at level l-1, children at level l in ascending order
-__global__ void k2_upward(double *sp, const double *sc, const double *C, const int32_t *child_ptr,
-                          const int32_t *quad, int nrhs, int q) {
+// Eq. 11: CTA = parent p at level l-1; columns = every child's q columns of C(quadrant)
+__global__ void __launch_bounds__(32 * FAR_WARPS) k2_upward(double *sp, const double *sc, const double *C,
+                                                           const int32_t *child_ptr, const int32_t *quad, int nrhs,
+                                                           int q) {
+  __shared__ double red[FAR_WARPS][FAR_TROWS];
   const int64_t p = blockIdx.x;
-  for (int k = threadIdx.x; k < q; k += blockDim.x)
-    for (int r = 0; r < nrhs; ++r) {
-      double acc = 0.0;
-      for (int32_t ch = child_ptr[p]; ch < child_ptr[p + 1]; ++ch) {
-        const double *Cq = C + (int64_t)quad[ch] * q * q;
-        const double *s = sc + ((int64_t)ch * nrhs + r) * q;
-        for (int j = 0; j < q; ++j) acc += Cq[(int64_t)j * q + k] * s[j];
-      }
-      sp[(p * nrhs + r) * q + k] = acc;
+  for (int r = 0; r < nrhs; ++r)
+    for (int k0 = 0; k0 < q; k0 += FAR_TROWS) {
+      double acc[FAR_KR] = {};
+      for (int32_t ch = child_ptr[p]; ch < child_ptr[p + 1]; ++ch)
+        far_panel(acc, C + (int64_t)quad[ch] * q * q, sc + ((int64_t)ch * nrhs + r) * q, q, k0, q);
+      far_store(acc, red, sp + (p * nrhs + r) * q, k0, q);
     }
 }
 
-// Eqs. 13 and 12: block = box a at level l
-__global__ void k2_translate(double *o, const double *s, const double *D, const int32_t *il_ptr,
-                             const int32_t *il_src, const int32_t *il_slot, const double *op, const double *C,
-                             const int32_t *parent, const int32_t *quad, int nrhs, int q) {
+// Eqs. 13 and 12: CTA = box a at level l; columns = B = C^T of its quadrant (stored
+// transposed, Ct) on the parent's potentials, then D(offset) on each source of the list
+__global__ void __launch_bounds__(32 * FAR_WARPS) k2_translate(double *o, const double *s, const double *D,
+                                                              const int32_t *il_ptr, const int32_t *il_src,
+                                                              const int32_t *il_slot, const double *op,
+                                                              const double *Ct, const int32_t *parent,
+                                                              const int32_t *quad, int nrhs, int q) {
+  __shared__ double red[FAR_WARPS][FAR_TROWS];
   const int64_t a = blockIdx.x;
-  for (int k = threadIdx.x; k < q; k += blockDim.x)
-    for (int r = 0; r < nrhs; ++r) {
-      double acc = 0.0;
-      if (op) {  // B = C^T: (k, j) of C^T is (j, k) of C
-        const double *Cq = C + (int64_t)quad[a] * q * q + (int64_t)k * q;
-        const double *opp = op + ((int64_t)parent[a] * nrhs + r) * q;
-        for (int j = 0; j < q; ++j) acc += Cq[j] * opp[j];
-      }
-      for (int32_t e = il_ptr[a]; e < il_ptr[a + 1]; ++e) {
-        const double *Ds = D + (int64_t)il_slot[e] * q * q;
-        const double *sb = s + ((int64_t)il_src[e] * nrhs + r) * q;
-        for (int j = 0; j < q; ++j) acc += Ds[(int64_t)j * q + k] * sb[j];
-      }
-      o[(a * nrhs + r) * q + k] = acc;
+  for (int r = 0; r < nrhs; ++r)
+    for (int k0 = 0; k0 < q; k0 += FAR_TROWS) {
+      double acc[FAR_KR] = {};
+      if (op) far_panel(acc, Ct + (int64_t)quad[a] * q * q, op + ((int64_t)parent[a] * nrhs + r) * q, q, k0, q);
+      for (int32_t e = il_ptr[a]; e < il_ptr[a + 1]; ++e)
+        far_panel(acc, D + (int64_t)il_slot[e] * q * q, s + ((int64_t)il_src[e] * nrhs + r) * q, q, k0, q);
+      far_store(acc, red, o + (a * nrhs + r) * q, k0, q);
     }
 }
 
-// Eq. 14: block = leaf a, thread = point i of a; U = V^T
-__global__ void k2_receive(double *yp, const double *oL, const double *V, int64_t n, int nrhs,
-                           const int32_t *leaf_ptr, int q) {
+// Eq. 14: CTA = leaf a; a warp per point i of a: y_i += V_a(:, i) . o_a (U = V^T), the
+// lanes over the q values (contiguous) and a shuffle reduction in fixed order
+__global__ void __launch_bounds__(32 * FAR_WARPS) k2_receive(double *yp, const double *oL, const double *V, int64_t n,
+                                                            int nrhs, const int32_t *leaf_ptr, int q) {
+  extern __shared__ double os[];  // [q]
   const int64_t a = blockIdx.x;
   const int32_t r0 = leaf_ptr[a], na = leaf_ptr[a + 1] - r0;
-  for (int i = threadIdx.x; i < na; i += blockDim.x) {
-    const double *Vi = V + (int64_t)q * (r0 + i);
-    for (int r = 0; r < nrhs; ++r) {
-      const double *o = oL + (a * nrhs + r) * q;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int r = 0; r < nrhs; ++r) {
+    for (int k = threadIdx.x; k < q; k += blockDim.x) os[k] = oL[(a * nrhs + r) * q + k];
+    __syncthreads();
+    for (int32_t i = warp; i < na; i += FAR_WARPS) {
+      const double *Vi = V + (int64_t)q * (r0 + i);
       double acc = 0.0;
-      for (int k = 0; k < q; ++k) acc += Vi[k] * o[k];
-      yp[(int64_t)r * n + r0 + i] += acc;
+      for (int k = lane; k < q; k += 32) acc = fma(__ldg(Vi + k), os[k], acc);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+      if (lane == 0) yp[(int64_t)r * n + r0 + i] += acc;
     }
+    __syncthreads();
   }
 }
 
@@ -624,23 +673,24 @@ static void matvec(nesa2d_ctx *c, const double *q, double *phi, int nrhs, int pa
   ensure_workspace(c, nrhs);
   cudaStream_t st = c->stream;
   const int Q = c->Q, L = c->L, l0 = c->l0;
-  const int tq = std::min(256, ((Q + 31) / 32) * 32);
   k2_perm_in<<<grid_of(c->n * nrhs), 256, 0, st>>>(c->d_qp, q, c->d_perm, c->n, nrhs);
   k2_near<<<(unsigned)c->ntile, 32 * NEAR_WARPS, 0, st>>>(c->d_yp, c->d_qp, c->n, nrhs, c->d_leaf_ptr, c->d_nptr,
                                                           c->d_nleaf, c->d_noff, c->d_Z, c->d_tiles,
                                                           (parts & NESA2D_PART_NEAR) ? 1 : 0);
   if (parts & NESA2D_PART_FAR) {
-    k2_radiate<<<(unsigned)c->nleaf, tq, 0, st>>>(c->lev[L].s, c->d_V, c->d_qp, c->n, nrhs, c->d_leaf_ptr, Q);
+    k2_radiate<<<(unsigned)c->nleaf, 32 * FAR_WARPS, 0, st>>>(c->lev[L].s, c->d_V, c->d_qp, c->n, nrhs,
+                                                              c->d_leaf_ptr, Q);
     for (int l = L; l > l0; --l)
-      k2_upward<<<(unsigned)c->lev[l - 1].nbox, tq, 0, st>>>(c->lev[l - 1].s, c->lev[l].s, c->lev[l].C,
+      k2_upward<<<(unsigned)c->lev[l - 1].nbox, 32 * FAR_WARPS, 0, st>>>(c->lev[l - 1].s, c->lev[l].s, c->lev[l].C,
                                                              c->lev[l - 1].d_child_ptr, c->lev[l].d_quad, nrhs, Q);
     for (int l = l0; l <= L; ++l) {
       const Level &lv = c->lev[l];
-      k2_translate<<<(unsigned)lv.nbox, tq, 0, st>>>(lv.o, lv.s, lv.D, lv.d_il_ptr, lv.d_il_src, lv.d_il_slot,
-                                                     l > l0 ? c->lev[l - 1].o : nullptr, lv.C, lv.d_parent,
-                                                     lv.d_quad, nrhs, Q);
+      k2_translate<<<(unsigned)lv.nbox, 32 * FAR_WARPS, 0, st>>>(lv.o, lv.s, lv.D, lv.d_il_ptr, lv.d_il_src,
+                                                                 lv.d_il_slot, l > l0 ? c->lev[l - 1].o : nullptr,
+                                                                 lv.Ct, lv.d_parent, lv.d_quad, nrhs, Q);
     }
-    k2_receive<<<(unsigned)c->nleaf, 256, 0, st>>>(c->d_yp, c->lev[L].o, c->d_V, c->n, nrhs, c->d_leaf_ptr, Q);
+    k2_receive<<<(unsigned)c->nleaf, 32 * FAR_WARPS, sizeof(double) * Q, st>>>(c->d_yp, c->lev[L].o, c->d_V, c->n,
+                                                                               nrhs, c->d_leaf_ptr, Q);
   }
   k2_perm_out<<<grid_of(c->n * nrhs), 256, 0, st>>>(phi, c->d_yp, c->d_perm, c->n, nrhs);
   check(cudaGetLastError(), "product launch");
