@@ -848,7 +848,7 @@ def run_ours(args, world, rank, local):
     return 0
 
 
-def large_solve(name, max_iters, restart):
+def large_solve(name, max_iters, restart, nrhs=0):
     """Mixed solve with FP64 refinement to 1e-5 of a large workload, all its right-hand
     sides (plane waves, seed 180103589) in lock step, overlapping block-Jacobi.  Prints
     one JSON line (setup, solve time, iterations, refinements, true FP64 residuals)."""
@@ -856,7 +856,7 @@ def large_solve(name, max_iters, restart):
 
     import paper_1801_03589_gb300 as nesa
     c = get_config(name)
-    nrhs = c["nrhs"]
+    nrhs = nrhs or c["nrhs"]
     t0 = time.perf_counter()
     g = nesa.Nesa(c["vertices"], c["triangles"], c["k"], leaf_size=c["leaf_size"], n_levels=c["n_levels"],
                   precision=nesa.MIXED, translate=nesa.TRANSLATE_TENSOR)
@@ -935,11 +935,13 @@ def main():
     ap.add_argument("--large-solve", choices=["C5", "C4L"],
                     help="only a mixed solve to 1e-5 of a large workload (tens of minutes), one JSON line")
     ap.add_argument("--large-solve-iters", type=int, default=2500)
+    ap.add_argument("--large-solve-restart", type=int, default=50)
+    ap.add_argument("--large-solve-nrhs", type=int, default=0, help="right-hand sides (0: the workload's)")
     args = ap.parse_args()
     if args.profile_run:
         return profile_run(args.profile_run)
     if args.large_solve:
-        return large_solve(args.large_solve, args.large_solve_iters, 50)
+        return large_solve(args.large_solve, args.large_solve_iters, args.large_solve_restart, args.large_solve_nrhs)
     world, rank, local = dist_setup()
     if args.impl == "reference":
         return run_reference(args, world, rank)
