@@ -617,8 +617,9 @@ __global__ void __launch_bounds__(32 * FAR_WARPS) k2_translate(double *o, const 
     }
 }
 
-// Eq. 14: CTA = leaf a; a warp per point i of a: y_i += V_a(:, i) . o_a (U = V^T), the
-// lanes over the q values (contiguous) and a shuffle reduction in fixed order
+// Eq. 14: CTA = leaf a; 8 lanes per point i of a: y_i += V_a(:, i) . o_a (U = V^T), the
+// 8 lanes over the point's q values (contiguous, k = sub + 8 t) and a shuffle reduction
+// in fixed order; a warp serves 4 points at a time
 __global__ void __launch_bounds__(32 * FAR_WARPS) k2_receive(double *yp, const double *oL, const double *V, int64_t n,
                                                             int nrhs, const int32_t *leaf_ptr, int q) {
   extern __shared__ double os[];  // [q]
@@ -628,13 +629,17 @@ __global__ void __launch_bounds__(32 * FAR_WARPS) k2_receive(double *yp, const d
   for (int r = 0; r < nrhs; ++r) {
     for (int k = threadIdx.x; k < q; k += blockDim.x) os[k] = oL[(a * nrhs + r) * q + k];
     __syncthreads();
-    for (int32_t i = warp; i < na; i += FAR_WARPS) {
-      const double *Vi = V + (int64_t)q * (r0 + i);
+    const int sub = lane & 7;
+    for (int32_t i0 = 4 * warp; i0 < na; i0 += 4 * FAR_WARPS) {
+      const int32_t i = i0 + (lane >> 3);
       double acc = 0.0;
-      for (int k = lane; k < q; k += 32) acc = fma(__ldg(Vi + k), os[k], acc);
+      if (i < na) {
+        const double *Vi = V + (int64_t)q * (r0 + i);
+        for (int k = sub; k < q; k += 8) acc = fma(__ldg(Vi + k), os[k], acc);
+      }
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-      if (lane == 0) yp[(int64_t)r * n + r0 + i] += acc;
+      for (int off = 4; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off, 8);
+      if (sub == 0 && i < na) yp[(int64_t)r * n + r0 + i] += acc;
     }
     __syncthreads();
   }
