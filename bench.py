@@ -698,10 +698,21 @@ def run_ours(args, world, rank, local):
         e1.record(stream)
         stream.synchronize()
         pass_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+        # per-stage device times of one eager 64-RHS product per member (outside the
+        # timed region; the graph's branches overlap, so these add up to more than a pass)
+        stages_ms = {}
+        for m, v, w in zip(members, bx, by):
+            m.profile_enable(True)
+            m.matvec(v, w, parts=mixed)
+            torch.cuda.synchronize()
+            for k_, d_ in m.profile_read().items():
+                stages_ms[k_] = stages_ms.get(k_, 0.0) + d_["ms"]
+            m.profile_enable(False)
         batch = {"workload": "sphere r=2 (30,720 RWG), 3:1 spheroid (60,750 RWG), 4x4 plate (42,960 RWG); "
                              "64 right-hand sides each; mixed product",
                  "pass_ms": pass_ms, "matvec_per_s": job_throughput(world, 3 * 64, pass_ms),
                  "graph_kernel_nodes": bt.kernel_nodes, "launches_per_pass": 1, "build_and_capture_s": build_s,
+                 "stages_ms_eager": {k_: round(v_, 4) for k_, v_ in stages_ms.items()},
                  "tile_n": [{l: t["tile_n"] for l, t in m.tuning().items()} for m in members]}
         bt.close()
 
@@ -879,7 +890,8 @@ def large_solve(name, max_iters, restart, nrhs=0):
     return 0
 
 
-PROFILE_RUNS = ("fp64_C2", "fp64_C3a", "tensor_C3a_generated", "tensor_C3a_stored", "model2d_N1e5_P300_Q100")
+PROFILE_RUNS = ("fp64_C2", "fp64_C3a", "tensor_C3a_generated", "tensor_C3a_stored", "tensor_C3a_64rhs",
+                "model2d_N1e5_P300_Q100")
 
 
 def profile_run(name):
@@ -898,7 +910,7 @@ def profile_run(name):
         tables = nesa.TABLES_GENERATED if name.endswith("generated") else nesa.TABLES_STORED
         g = nesa.Nesa(c["vertices"], c["triangles"], c["k"], leaf_size=c["leaf_size"], n_levels=c["n_levels"],
                       precision=nesa.MIXED, translate=nesa.TRANSLATE_TENSOR, tile_n=128, translation_tables=tables)
-        x = torch.from_numpy(random_coefficients(g.n, 1, seed=5)).cuda()
+        x = torch.from_numpy(random_coefficients(g.n, 64 if name.endswith("64rhs") else 1, seed=5)).cuda()
         for _ in range(2):
             g.matvec(x, parts=nesa.PART_ALL | nesa.PART_MIXED)
     else:

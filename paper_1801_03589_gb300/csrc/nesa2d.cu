@@ -73,6 +73,7 @@ struct nesa2d_ctx {
   int64_t nleaf = 0, near_entries = 0;
   // device
   int32_t *d_perm = nullptr, *d_leaf_ptr = nullptr, *d_nptr = nullptr, *d_nleaf = nullptr;
+  int32_t *d_pt_leaf = nullptr;  // [n] leaf of each internal point
   int64_t *d_noff = nullptr;
   int2 *d_tiles = nullptr;  // near-field row tiles (leaf, first row)
   int64_t ntile = 0;
@@ -445,6 +446,12 @@ static void build(nesa2d_ctx *c, const double *x) {
   }
   c->d_perm = upload(c, c->perm);
   c->d_leaf_ptr = upload(c, c->leaf_ptr);
+  {
+    std::vector<int32_t> pt_leaf(std::max<int64_t>(c->n, 1), 0);
+    for (int64_t a = 0; a < c->nleaf; ++a)
+      for (int32_t i = c->leaf_ptr[a]; i < c->leaf_ptr[a + 1]; ++i) pt_leaf[i] = (int32_t)a;
+    c->d_pt_leaf = upload(c, pt_leaf);
+  }
   c->d_nptr = upload(c, nptr);
   c->d_nleaf = upload(c, nlist);
   c->d_noff = upload(c, noff);
@@ -549,7 +556,7 @@ __device__ __forceinline__ void far_panel(double (&acc)[FAR_KR], const double *_
                                           const double *__restrict__ x, int len, int k0, int q) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int j0 = (int)((int64_t)warp * len / FAR_WARPS), j1 = (int)((int64_t)(warp + 1) * len / FAR_WARPS);
-#pragma unroll 2
+#pragma unroll 4
   for (int j = j0; j < j1; ++j) far_col(acc, M + (int64_t)j * q, __ldg(x + j), k0, q, lane);
 }
 
@@ -617,31 +624,27 @@ __global__ void __launch_bounds__(32 * FAR_WARPS) k2_translate(double *o, const 
     }
 }
 
-// Eq. 14: CTA = leaf a; 8 lanes per point i of a: y_i += V_a(:, i) . o_a (U = V^T), the
-// 8 lanes over the point's q values (contiguous, k = sub + 8 t) and a shuffle reduction
-// in fixed order; a warp serves 4 points at a time
-__global__ void __launch_bounds__(32 * FAR_WARPS) k2_receive(double *yp, const double *oL, const double *V, int64_t n,
-                                                            int nrhs, const int32_t *leaf_ptr, int q) {
-  extern __shared__ double os[];  // [q]
-  const int64_t a = blockIdx.x;
-  const int32_t r0 = leaf_ptr[a], na = leaf_ptr[a + 1] - r0;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+// Eq. 14: 8 lanes per point i: y_i += V(:, i) . o_a (U = V^T, a the leaf of i), the 8
+// lanes over the point's q values (contiguous, k = sub + 8 t) and a shuffle reduction in
+// fixed order.  The grid runs over all points (32 per CTA), not one CTA per leaf, so
+// that enough loads are in flight on every SM; o_a (q values) comes through L1.
+__global__ void __launch_bounds__(256) k2_receive(double *__restrict__ yp, const double *__restrict__ oL,
+                                                 const double *__restrict__ V, int64_t n, int nrhs,
+                                                 const int32_t *__restrict__ pt_leaf, int q) {
+  const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 3;
+  const int sub = threadIdx.x & 7;
+  const bool on = i < n;
+  const int64_t ic = on ? i : 0;
+  const double *Vi = V + (int64_t)q * ic;
+  const int64_t a = pt_leaf[ic];
   for (int r = 0; r < nrhs; ++r) {
-    for (int k = threadIdx.x; k < q; k += blockDim.x) os[k] = oL[(a * nrhs + r) * q + k];
-    __syncthreads();
-    const int sub = lane & 7;
-    for (int32_t i0 = 4 * warp; i0 < na; i0 += 4 * FAR_WARPS) {
-      const int32_t i = i0 + (lane >> 3);
-      double acc = 0.0;
-      if (i < na) {
-        const double *Vi = V + (int64_t)q * (r0 + i);
-        for (int k = sub; k < q; k += 8) acc = fma(__ldg(Vi + k), os[k], acc);
-      }
+    const double *o = oL + (a * nrhs + r) * q;
+    double acc = 0.0;
+#pragma unroll 4
+    for (int k = sub; k < q; k += 8) acc = fma(__ldg(Vi + k), __ldg(o + k), acc);
 #pragma unroll
-      for (int off = 4; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off, 8);
-      if (sub == 0 && i < na) yp[(int64_t)r * n + r0 + i] += acc;
-    }
-    __syncthreads();
+    for (int off = 4; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off, 8);
+    if (sub == 0 && on) yp[(int64_t)r * n + i] += acc;
   }
 }
 
@@ -694,8 +697,8 @@ static void matvec(nesa2d_ctx *c, const double *q, double *phi, int nrhs, int pa
                                                                  lv.d_il_slot, l > l0 ? c->lev[l - 1].o : nullptr,
                                                                  lv.Ct, lv.d_parent, lv.d_quad, nrhs, Q);
     }
-    k2_receive<<<(unsigned)c->nleaf, 32 * FAR_WARPS, sizeof(double) * Q, st>>>(c->d_yp, c->lev[L].o, c->d_V, c->n,
-                                                                               nrhs, c->d_leaf_ptr, Q);
+    k2_receive<<<(unsigned)((c->n * 8 + 255) / 256), 256, 0, st>>>(c->d_yp, c->lev[L].o, c->d_V, c->n, nrhs,
+                                                                    c->d_pt_leaf, Q);
   }
   k2_perm_out<<<grid_of(c->n * nrhs), 256, 0, st>>>(phi, c->d_yp, c->d_perm, c->n, nrhs);
   check(cudaGetLastError(), "product launch");

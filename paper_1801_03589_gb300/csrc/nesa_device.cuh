@@ -116,8 +116,17 @@ struct nesa_ctx {
   int64_t *d_nz_ptr4 = nullptr;
   int32_t *d_nz_col4 = nullptr;
   int32_t *d_perm = nullptr;           // internal index -> ABI index
-  nesa::cplxf *d_xp = nullptr;         // x in the internal order, complex64 [nrhs][n]
+  nesa::cplxf *d_xp = nullptr;         // x in the internal order, complex64 [nrhs][n], or
+                                       // [n][ldx] with nrhs >= 32 (ldx = nrhs rounded up to even)
   nesa::cplxf *d_rcv = nullptr;        // reception per V column, [ncol][nrhs] (nrhs >= 32)
+  // the same near field for 32 or more right-hand sides (built by the first such
+  // product): internal rows in groups of four, a group's columns the union of its
+  // rows' columns, a row's value 0 at the columns it lacks
+  int64_t n_group = 0;
+  int64_t *d_ng_ptr = nullptr;         // [n_group + 1] first column slot of each group (even)
+  int32_t *d_ng_col = nullptr;         // [slot] internal column (a group's last may repeat, value 0)
+  nesa::cplxf *d_ng_val = nullptr;     // [slot][4] the four rows' values at that column
+  int32_t *d_ng_row = nullptr;         // [n_group][4] ABI row of each group member, -1 past the end
   nesa::cplxf *d_V32 = nullptr;
   int nrhs_cap32 = 0;
   // levels

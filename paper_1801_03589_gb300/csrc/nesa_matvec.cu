@@ -8,8 +8,9 @@
 //   k_near_receive y_m    = sum_n Z^near_mn x_n                (Eq. 9)
 //                         + (-i eta k) sum_ch gamma_ch V^T o   (Eq. 14; U = V^T)
 // The mixed product with 32 or more right-hand sides splits the last stage in two:
-// k_receive_leaf (Eq. 14 per leaf and V column, for 32 right-hand sides at a time) and
-// k_near_wide (Eq. 9, one lane per right-hand side, plus the row's reception values).
+// k_receive_leaf (Eq. 14 per leaf and V column, for 64 right-hand sides at a time) and
+// k_near_group (Eq. 9 for four rows at a time, two right-hand sides per lane, plus the
+// rows' reception values).
 // Every output element is owned by one thread or one warp (no atomics), so the
 // product is deterministic.  The kernels are templated on the complex type of the
 // operator: complex128 (the FP64 product, bound by the FP64 pipe: a complex
@@ -64,12 +65,16 @@ int ensure_workspace(nesa_ctx *c, int nrhs) {
   return NESA_OK;
 }
 
+static void build_near_groups(nesa_ctx *c);
+
 static void ensure_workspace32(nesa_ctx *c, int nrhs) {
+  if (nrhs >= 32 && !c->d_ng_ptr) build_near_groups(c);
   if (nrhs <= c->nrhs_cap32) return;
   dfree(c, c->d_xp);
   dfree(c, c->d_rcv);
   c->d_rcv = nullptr;
-  c->d_xp = (cplxf *)dalloc(c, sizeof(cplxf) * (size_t)std::max<int64_t>(1, c->n * nrhs));
+  // (nrhs + 1) & ~1: the row stride of the wide layout
+  c->d_xp = (cplxf *)dalloc(c, sizeof(cplxf) * (size_t)std::max<int64_t>(1, c->n * ((nrhs + 1) & ~1)));
   if (nrhs >= 32) c->d_rcv = (cplxf *)dalloc(c, sizeof(cplxf) * (size_t)c->info.v_columns * nrhs);
   for (int l = c->l0; l <= c->L; ++l) {
     DevLevel &d = c->lev[l];
@@ -209,6 +214,70 @@ __global__ void __launch_bounds__(512) k_radiate2(cplxf *__restrict__ s, const c
     }
     if (active)
       *(float4 *)(s + ((int64_t)b * 4 * nrhs + 4 * r + ch) * q + i) = make_float4(a0.x, a0.y, a1.x, a1.y);
+  }
+}
+
+// Radiation of the mixed product with Q even and 8 or more right-hand sides: every
+// thread owns two consecutive rows i, i+1 of one channel and RB right-hand sides, so a
+// 16-byte V load serves 2 RB complex FMAs and the x values of a column come from shared
+// memory as RB/2 16-byte broadcasts (one row per thread took one 8-byte V load per RB
+// FMAs).  Per right-hand side the summation order over the columns is that of one at a
+// time.
+template <int RB>
+__global__ void __launch_bounds__(512) k_radiate2w(cplxf *__restrict__ s, const cplxf *__restrict__ V,
+                                                   const int32_t *__restrict__ vc_ptr,
+                                                   const int32_t *__restrict__ vc_rwg, const cplx *__restrict__ x,
+                                                   int64_t n, int nrhs, int q, int tr2, int jc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplxf *xs = (cplxf *)smem_raw;  // [jc][RB]
+  const int32_t b = blockIdx.x;
+  const int ch = threadIdx.x / tr2;
+  const int i = 2 * (blockIdx.y * tr2 + threadIdx.x % tr2);
+  const bool active = ch < 4 && i < q;
+  const int32_t g0 = vc_ptr[b], ns = vc_ptr[b + 1] - g0;
+  const cplxf *Vb = V + (int64_t)4 * g0 * q;
+  for (int r0 = 0; r0 < nrhs; r0 += RB) {
+    const int rb = min(RB, nrhs - r0);
+    cplxf a0[RB], a1[RB];
+#pragma unroll
+    for (int rr = 0; rr < RB; ++rr) a0[rr] = a1[rr] = make_float2(0.0f, 0.0f);
+    for (int j0 = 0; j0 < ns; j0 += jc) {
+      const int len = min(jc, ns - j0);
+      __syncthreads();
+      for (int t = threadIdx.x; t < len * RB; t += blockDim.x) {
+        const int j = t / RB, rr = t % RB;
+        cplxf v = make_float2(0.0f, 0.0f);
+        if (rr < rb) {
+          const cplx xv = x[(int64_t)(r0 + rr) * n + vc_rwg[g0 + j0 + j]];
+          v = make_float2((float)xv.x, (float)xv.y);
+        }
+        xs[t] = v;
+      }
+      __syncthreads();
+      if (!active) continue;
+      const cplxf *vp = Vb + (int64_t)4 * j0 * q + (int64_t)ch * q + i;
+#pragma unroll 2
+      for (int j = 0; j < len; ++j) {
+        const float4 v2 = *(const float4 *)(vp + (int64_t)4 * j * q);
+        const cplxf va = make_float2(v2.x, v2.y), vb = make_float2(v2.z, v2.w);
+        const float4 *xj = (const float4 *)(xs + j * RB);
+#pragma unroll
+        for (int h = 0; h < RB / 2; ++h) {
+          const float4 x2 = xj[h];
+          const cplxf xa = make_float2(x2.x, x2.y), xb = make_float2(x2.z, x2.w);
+          cfma(a0[2 * h], va, xa);
+          cfma(a1[2 * h], vb, xa);
+          cfma(a0[2 * h + 1], va, xb);
+          cfma(a1[2 * h + 1], vb, xb);
+        }
+      }
+    }
+    if (active)
+#pragma unroll
+      for (int rr = 0; rr < RB; ++rr)
+        if (rr < rb)
+          *(float4 *)(s + ((int64_t)b * 4 * nrhs + 4 * (r0 + rr) + ch) * q + i) =
+              make_float4(a0[rr].x, a0[rr].y, a1[rr].x, a1[rr].y);
   }
 }
 
@@ -438,32 +507,36 @@ __global__ void __launch_bounds__(256) k_near_receive_v(cplx *__restrict__ y, co
 }
 
 // Reception of the mixed product for many right-hand sides (nrhs >= 32), one leaf b and
-// one group of 32 right-hand sides per block, as a small complex product per leaf:
+// one group of 64 right-hand sides per block, as a small complex product per leaf:
 //   R[g][r] = sum_{ch,i} gamma_ch V[g][ch][i] o_b[r][ch][i]       (Eq. 14, U = V^T)
 // for the leaf's V columns g (an RWG function has one column per leaf that holds one of
-// its triangles; k_near_wide adds its columns up).  V and o go through shared memory in
+// its triangles; k_near_group adds its columns up).  V and o go through shared memory in
 // chunks of RC_KC of the 4Q values: V as [column][k] (every lane of a warp reads the
-// same two values with one 16-byte load), o as [right-hand side][k] with rows padded to
-// RC_KC + 2 values (lane r reads its two values with one 16-byte load, eight lanes per
-// bank cycle).  Thread (warp w, lane) owns right-hand side r0 + lane and the columns
-// w, w + 8, ... of a block of RC_COLS (only those the leaf has); FP32 sums in the order
-// k = 0 .. 4Q-1.
-constexpr int RC_KC = 32, RC_COLS = 64, RC_OPAD = RC_KC + 2;
+// same two values with one 16-byte load), o as [k][right-hand side] with rows padded to
+// 64 + 2 values (lane l reads right-hand sides 2l and 2l + 1 with one 16-byte load).
+// Thread (warp w, lane l) owns right-hand sides r0 + 2l, r0 + 2l + 1 and the columns
+// w, w + 8, ... of a block of RC_COLS (only those the leaf has): per pair of k values,
+// two o loads and one V load per column feed 16 FMAs per column.  FP32 sums in the
+// order k = 0 .. 4Q-1.
+constexpr int RC_KC = 32, RC_COLS = 64, RC_RHS = 64, RC_OPAD = RC_RHS + 2;
 __global__ void __launch_bounds__(256) k_receive_leaf(cplxf *__restrict__ R, const cplxf *__restrict__ V,
                                                       const cplxf *__restrict__ oL, const int32_t *__restrict__ vc_ptr,
                                                       int nrhs, int q, float mk2) {
   __shared__ __align__(16) cplxf Vs[RC_COLS][RC_KC];
-  __shared__ __align__(16) cplxf Os[32][RC_OPAD];
+  __shared__ __align__(16) cplxf Os[RC_KC][RC_OPAD];
   const int64_t b = blockIdx.x;
-  const int r0 = blockIdx.y * 32;
+  const int r0 = blockIdx.y * RC_RHS;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int32_t g0 = vc_ptr[b], ns = vc_ptr[b + 1] - g0;
   const int q4 = 4 * q, q3 = 3 * q;
   const cplxf *ob = oL + b * nrhs * (int64_t)q4;  // o_b[r][ch][i] at ob + r * 4Q + ch * Q + i
+  const int ra = r0 + 2 * lane;                   // this lane's right-hand sides ra, ra + 1
   for (int c0 = 0; c0 < ns; c0 += RC_COLS) {
     const int nc = min(RC_COLS, ns - c0);
     const int jn = nc > warp ? (nc - warp + 7) / 8 : 0;  // this warp's columns in the block
-    cplxf acc[RC_COLS / 8] = {};
+    cplxf acc[RC_COLS / 8][2];
+#pragma unroll
+    for (int j = 0; j < RC_COLS / 8; ++j) acc[j][0] = acc[j][1] = make_float2(0.0f, 0.0f);
     for (int k0 = 0; k0 < q4; k0 += RC_KC) {
       const int kn = min(RC_KC, q4 - k0);
       __syncthreads();
@@ -477,93 +550,135 @@ __global__ void __launch_bounds__(256) k_receive_leaf(cplxf *__restrict__ R, con
         }
         Vs[cc][kk] = v;
       }
-      for (int t = threadIdx.x; t < 32 * RC_KC; t += blockDim.x) {
+      for (int t = threadIdx.x; t < RC_RHS * RC_KC; t += blockDim.x) {  // coalesced along k
         const int rr = t / RC_KC, kk = t % RC_KC;
-        Os[rr][kk] = r0 + rr < nrhs && kk < kn ? ob[(int64_t)(r0 + rr) * q4 + k0 + kk] : make_float2(0.0f, 0.0f);
+        Os[kk][rr] = r0 + rr < nrhs && kk < kn ? ob[(int64_t)(r0 + rr) * q4 + k0 + kk] : make_float2(0.0f, 0.0f);
       }
       __syncthreads();
 #pragma unroll 2
       for (int kk = 0; kk < RC_KC; kk += 2) {  // zeros past kn
-        const float4 o2 = *(const float4 *)&Os[lane][kk];
-        const cplxf oa = make_float2(o2.x, o2.y), obv = make_float2(o2.z, o2.w);
+        const float4 oa = *(const float4 *)&Os[kk][2 * lane];
+        const float4 obk = *(const float4 *)&Os[kk + 1][2 * lane];
+        const cplxf oa0 = make_float2(oa.x, oa.y), oa1 = make_float2(oa.z, oa.w);
+        const cplxf ob0 = make_float2(obk.x, obk.y), ob1 = make_float2(obk.z, obk.w);
 #pragma unroll
         for (int j = 0; j < RC_COLS / 8; ++j)
           if (j < jn) {
             const float4 v2 = *(const float4 *)&Vs[warp + 8 * j][kk];
-            cfma(acc[j], make_float2(v2.x, v2.y), oa);
-            cfma(acc[j], make_float2(v2.z, v2.w), obv);
+            const cplxf va = make_float2(v2.x, v2.y), vb = make_float2(v2.z, v2.w);
+            cfma(acc[j][0], va, oa0);
+            cfma(acc[j][1], va, oa1);
+            cfma(acc[j][0], vb, ob0);
+            cfma(acc[j][1], vb, ob1);
           }
       }
     }
-    if (r0 + lane < nrhs)
 #pragma unroll
-      for (int j = 0; j < RC_COLS / 8; ++j)
-        if (j < jn) R[(int64_t)(g0 + c0 + warp + 8 * j) * nrhs + r0 + lane] = acc[j];
+    for (int j = 0; j < RC_COLS / 8; ++j)
+      if (j < jn) {
+        cplxf *Rg = R + (int64_t)(g0 + c0 + warp + 8 * j) * nrhs;
+        if (ra < nrhs) Rg[ra] = acc[j][0];
+        if (ra + 1 < nrhs) Rg[ra + 1] = acc[j][1];
+      }
   }
 }
 
 // Near field and reception sum of the mixed product for many right-hand sides
-// (nrhs >= 32): one warp per (internal row, group of 32 right-hand sides), lane = right-
-// hand side.  Every entry's value and column are read once per group (the lanes load
-// the same address), and the x values of a column for the group are one coalesced
-// 256-byte load (xw is [n][nrhs]).  Four FP32 partial sums per lane (one per entry of a
-// group of four), added in FP64.  The far part adds the reception values R of the row's
-// V columns (k_receive_leaf) times -i eta k.
-__global__ void __launch_bounds__(256) k_near_wide(cplx *__restrict__ y, const cplxf *__restrict__ xw, int64_t n,
-                                                   int nrhs, const int32_t *__restrict__ perm,
-                                                   const int64_t *__restrict__ nz_ptr,
-                                                   const int32_t *__restrict__ nz_col,
-                                                   const cplxf *__restrict__ nz_val,
-                                                   const int32_t *__restrict__ rx_ptr,
-                                                   const int32_t *__restrict__ rx_col, const cplxf *__restrict__ R,
-                                                   double eta_k, int parts) {
+// (nrhs >= 32).  The internal rows come in groups of four whose columns are the union
+// of the four rows' columns (a row's value is 0 at a column it lacks).  One warp per
+// (group, 64 right-hand sides); lane l owns right-hand sides 2l and 2l + 1.  Per column
+// a lane loads its two x values once (16 bytes; the warp reads 512 contiguous bytes of
+// xw) and uses them for all four rows: 32 FP32 FMAs per x load, against 8 with one row
+// per warp.  The column index and the four values are the same for every lane (one
+// broadcast load each).  The eight warps of a block take consecutive groups, which
+// share most of their columns, so their x loads meet in L1.  Two FP32 partial sums per
+// output (even and odd column slots), added in FP64.  The far part adds the reception
+// values R of the row's V columns (k_receive_leaf) times -i eta k.
+constexpr int NG_ROWS = 4;
+__global__ void __launch_bounds__(256) k_near_group(cplx *__restrict__ y, const cplxf *__restrict__ xw, int ldx,
+                                                    int64_t n, int nrhs, int64_t n_group,
+                                                    const int64_t *__restrict__ g_ptr,
+                                                    const int32_t *__restrict__ g_col,
+                                                    const float4 *__restrict__ g_val,
+                                                    const int32_t *__restrict__ g_row,
+                                                    const int32_t *__restrict__ rx_ptr,
+                                                    const int32_t *__restrict__ rx_col, const cplxf *__restrict__ R,
+                                                    double eta_k, int parts) {
   const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  const int ngrp = (nrhs + 31) >> 5;
-  const int64_t r = wid / ngrp;
-  if (r >= n) return;
-  const int rr = (int)(wid % ngrp) * 32 + lane;
-  const bool on = rr < nrhs;
-  const int rc = on ? rr : 0;
-  cplxf a0 = {0.0f, 0.0f}, a1 = a0, a2 = a0, a3 = a0;
+  const int nblk = (nrhs + 63) >> 6;
+  const int64_t g = wid / nblk;
+  if (g >= n_group) return;
+  const int r0 = (int)(wid % nblk) * 64 + 2 * lane;  // this lane's right-hand sides r0, r0 + 1
+  const bool on0 = r0 < nrhs, on1 = r0 + 1 < nrhs;
+  // acc[p][i][j]: column-slot parity p, group row i, right-hand side r0 + j
+  cplxf acc[2][NG_ROWS][2];
+#pragma unroll
+  for (int p = 0; p < 2; ++p)
+#pragma unroll
+    for (int i = 0; i < NG_ROWS; ++i) acc[p][i][0] = acc[p][i][1] = make_float2(0.0f, 0.0f);
   if (parts & NESA_PART_NEAR) {
-    const cplxf *xc = xw + rc;
-    const int64_t z0 = nz_ptr[r], z1 = nz_ptr[r + 1];
+    const float4 *xc = (const float4 *)xw + (on0 ? r0 >> 1 : 0);  // ldx and r0 even: 16-byte aligned
+    const int64_t lq = ldx >> 1;
+    const int64_t z0 = g_ptr[g], z1 = g_ptr[g + 1];  // even
 #pragma unroll 2
-    for (int64_t e = z0; e < z1; e += 4) {  // rows are padded to multiples of four
-      const int4 k = *(const int4 *)(nz_col + e);
-      const float4 va = *(const float4 *)(nz_val + e);
-      const float4 vb = *(const float4 *)(nz_val + e + 2);
-      cfma(a0, make_float2(va.x, va.y), xc[(int64_t)k.x * nrhs]);
-      cfma(a1, make_float2(va.z, va.w), xc[(int64_t)k.y * nrhs]);
-      cfma(a2, make_float2(vb.x, vb.y), xc[(int64_t)k.z * nrhs]);
-      cfma(a3, make_float2(vb.z, vb.w), xc[(int64_t)k.w * nrhs]);
+    for (int64_t e = z0; e < z1; e += 2) {
+      const int2 k = *(const int2 *)(g_col + e);
+      const float4 xa = xc[(int64_t)k.x * lq], xb = xc[(int64_t)k.y * lq];
+      const float4 v0 = g_val[2 * e], v1 = g_val[2 * e + 1], v2 = g_val[2 * e + 2], v3 = g_val[2 * e + 3];
+      const cplxf va[NG_ROWS] = {make_float2(v0.x, v0.y), make_float2(v0.z, v0.w), make_float2(v1.x, v1.y),
+                                 make_float2(v1.z, v1.w)};
+      const cplxf vb[NG_ROWS] = {make_float2(v2.x, v2.y), make_float2(v2.z, v2.w), make_float2(v3.x, v3.y),
+                                 make_float2(v3.z, v3.w)};
+      const cplxf xa0 = make_float2(xa.x, xa.y), xa1 = make_float2(xa.z, xa.w);
+      const cplxf xb0 = make_float2(xb.x, xb.y), xb1 = make_float2(xb.z, xb.w);
+#pragma unroll
+      for (int i = 0; i < NG_ROWS; ++i) {
+        cfma(acc[0][i][0], va[i], xa0);
+        cfma(acc[0][i][1], va[i], xa1);
+        cfma(acc[1][i][0], vb[i], xb0);
+        cfma(acc[1][i][1], vb[i], xb1);
+      }
     }
   }
-  const int32_t m = perm[r];
-  double2 v = make_double2(((double)a0.x + (double)a1.x) + ((double)a2.x + (double)a3.x),
-                           ((double)a0.y + (double)a1.y) + ((double)a2.y + (double)a3.y));
-  if (parts & NESA_PART_FAR) {
-    double fx = 0.0, fy = 0.0;
-    for (int32_t e = rx_ptr[m]; e < rx_ptr[m + 1]; ++e) {
-      const cplxf f = R[(int64_t)rx_col[e] * nrhs + rc];
-      fx += f.x;
-      fy += f.y;
+#pragma unroll
+  for (int i = 0; i < NG_ROWS; ++i) {
+    const int32_t m = g_row[NG_ROWS * g + i];
+    if (m < 0) continue;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int rr = r0 + j;
+      const int rc = rr < nrhs ? rr : 0;
+      double2 v = make_double2((double)acc[0][i][j].x + (double)acc[1][i][j].x,
+                               (double)acc[0][i][j].y + (double)acc[1][i][j].y);
+      if (parts & NESA_PART_FAR) {
+        double fx = 0.0, fy = 0.0;
+        for (int32_t e = rx_ptr[m]; e < rx_ptr[m + 1]; ++e) {
+          const cplxf f = R[(int64_t)rx_col[e] * nrhs + rc];
+          fx += f.x;
+          fy += f.y;
+        }
+        v.x += eta_k * fy;
+        v.y -= eta_k * fx;
+      }
+      if (j == 0 ? on0 : on1) y[(int64_t)rr * n + m] = v;
     }
-    v.x += eta_k * fy;
-    v.y -= eta_k * fx;
   }
-  if (on) y[(int64_t)rr * n + m] = v;
 }
 
-// xw[i][r] = complex64(x[r][perm[i]])   (right-hand sides innermost, for k_near_wide)
+// xw[i][r] = complex64(x[r][perm[i]]) for r < nrhs, 0 for nrhs <= r < ldx   (right-hand
+// sides innermost, rows ldx apart, for k_near_group)
 __global__ void k_perm_x_wide(cplxf *__restrict__ xw, const cplx *__restrict__ x, const int32_t *__restrict__ perm,
-                              int64_t n, int nrhs) {
-  const int64_t total = n * nrhs;
+                              int64_t n, int nrhs, int ldx) {
+  const int64_t total = n * ldx;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = t / nrhs, r = t % nrhs;  // consecutive threads write consecutive xw
-    const cplx v = x[r * n + perm[i]];
-    xw[t] = make_float2((float)v.x, (float)v.y);
+    const int64_t i = t / ldx, r = t % ldx;  // consecutive threads write consecutive xw
+    if (r < nrhs) {
+      const cplx v = x[r * n + perm[i]];
+      xw[t] = make_float2((float)v.x, (float)v.y);
+    } else {
+      xw[t] = make_float2(0.0f, 0.0f);
+    }
   }
 }
 
@@ -677,10 +792,14 @@ static void run_product(nesa_ctx *c, const OpView<CT> &op, const cplx *x, cplx *
                     B * (4.0 * ncol * d.q + 4.0 * nrhs * d.nbox * d.q) + 16.0 * nrhs * c->n);
       bool done = false;
       if constexpr (std::is_same<CT, cplxf>::value) {
-        if (rbk == 1 && d.q % 2 == 0) {  // two rows per thread, 16-byte V loads
+        if (d.q % 2 == 0) {  // two rows per thread, 16-byte V loads
           Tiling t2 = tiling(d.q / 2);
-          k_radiate2<<<dim3((unsigned)d.nbox, t2.ntile), t2.threads, smem, st>>>(
-              op.s[L], op.V, c->d_vc_ptr, c->d_vc_rwg, x, c->n, nrhs, d.q, t2.tr, jc);
+          if (rbk == 1)
+            k_radiate2<<<dim3((unsigned)d.nbox, t2.ntile), t2.threads, smem, st>>>(
+                op.s[L], op.V, c->d_vc_ptr, c->d_vc_rwg, x, c->n, nrhs, d.q, t2.tr, jc);
+          else
+            k_radiate2w<8><<<dim3((unsigned)d.nbox, t2.ntile), t2.threads, smem, st>>>(
+                op.s[L], op.V, c->d_vc_ptr, c->d_vc_rwg, x, c->n, nrhs, d.q, t2.tr, jc);
           done = true;
         }
       }
@@ -754,14 +873,18 @@ static void run_product(nesa_ctx *c, const OpView<CT> &op, const cplx *x, cplx *
   StageScope sc(c, 3, fl, by);
   if constexpr (std::is_same<CT, cplxf>::value) {
     const unsigned pgrid = (unsigned)std::min<int64_t>((c->n * nrhs + 255) / 256, 1 << 16);
-    if (nrhs >= 32) {  // many right-hand sides: lane per right-hand side
-      if (parts & NESA_PART_NEAR) k_perm_x_wide<<<pgrid, 256, 0, st>>>(c->d_xp, x, c->d_perm, c->n, nrhs);
+    if (nrhs >= 32) {  // many right-hand sides: groups of four rows, two right-hand sides per lane
+      const int ldx = (nrhs + 1) & ~1;
+      if (parts & NESA_PART_NEAR)
+        k_perm_x_wide<<<(unsigned)std::min<int64_t>((c->n * ldx + 255) / 256, 1 << 16), 256, 0, st>>>(
+            c->d_xp, x, c->d_perm, c->n, nrhs, ldx);
       if (parts & NESA_PART_FAR)
-        k_receive_leaf<<<dim3((unsigned)c->nleaf, (unsigned)((nrhs + 31) / 32)), 256, 0, st>>>(
+        k_receive_leaf<<<dim3((unsigned)c->nleaf, (unsigned)((nrhs + RC_RHS - 1) / RC_RHS)), 256, 0, st>>>(
             c->d_rcv, op.V, op.o[L], c->d_vc_ptr, nrhs, dL.q, (float)(-1.0 / (c->k * c->k)));
-      k_near_wide<<<grid_for(c->n * ((nrhs + 31) / 32) * 32, 256), 256, 0, st>>>(
-          y, c->d_xp, c->n, nrhs, c->d_perm, c->d_nz_ptr4, c->d_nz_col4, op.nz_val, c->d_rx_ptr, c->d_rx_col,
-          c->d_rcv, c->eta * c->k, parts);
+      if (c->n_group > 0)
+        k_near_group<<<grid_for(c->n_group * ((nrhs + 63) / 64) * 32, 256), 256, 0, st>>>(
+            y, c->d_xp, ldx, c->n, nrhs, c->n_group, c->d_ng_ptr, c->d_ng_col, (const float4 *)c->d_ng_val,
+            c->d_ng_row, c->d_rx_ptr, c->d_rx_col, c->d_rcv, c->eta * c->k, parts);
     } else {
       if (parts & NESA_PART_NEAR) k_perm_x<<<pgrid, 256, 0, st>>>(c->d_xp, x, c->d_perm, c->n, nrhs);
       auto near = nrhs == 1 ? k_near_receive_v<1> : k_near_receive_v<4>;
@@ -882,6 +1005,130 @@ static void build_near_internal(nesa_ctx *c) {
       c->d_nz_val32, d_src, c->d_nz_val, nnz4);
   check_cuda(cudaStreamSynchronize(c->stream), "near order");
   dfree(c, d_src);
+}
+
+// dst[e] = src[idx[e]], 0 where idx[e] < 0
+__global__ void k_gather_c64(cplxf *__restrict__ dst, const int64_t *__restrict__ idx, const cplxf *__restrict__ src,
+                             int64_t count) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = idx[e];
+    dst[e] = s >= 0 ? src[s] : make_float2(0.0f, 0.0f);
+  }
+}
+
+// The near field of the mixed product regrouped for many right-hand sides (k_near_group).
+// Within the internal rows of one leaf (rows whose first quadrature point lies in it),
+// rows are ordered by their column lists, so that rows with the same list (RWG functions
+// whose quadrature points lie in the same leaves) sit next to each other; then every
+// four consecutive rows form a group over the union of their columns.  The values are
+// the complex64 values of the padded CSR, gathered on the device; the zeros a row gets
+// at columns it lacks change none of its sums.
+static void build_near_groups(nesa_ctx *c) {
+  const HostModel &h = c->h;
+  const int64_t n = c->n;
+  std::vector<int64_t> ptr4(n + 1);
+  std::vector<int32_t> perm(std::max<int64_t>(n, 1));
+  check_cuda(cudaMemcpy(ptr4.data(), c->d_nz_ptr4, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost), "near groups");
+  check_cuda(cudaMemcpy(perm.data(), c->d_perm, sizeof(int32_t) * n, cudaMemcpyDeviceToHost), "near groups");
+  const int64_t nnz4 = ptr4[n];
+  std::vector<int32_t> col4(std::max<int64_t>(nnz4, 1));
+  if (nnz4 > 0)
+    check_cuda(cudaMemcpy(col4.data(), c->d_nz_col4, sizeof(int32_t) * nnz4, cudaMemcpyDeviceToHost), "near groups");
+  // a row's true length: its padded tail repeats the last column
+  auto row_len = [&](int64_t r) {
+    int64_t e = ptr4[r + 1];
+    while (e - 1 > ptr4[r] && col4[e - 1] == col4[e - 2]) --e;
+    return e - ptr4[r];
+  };
+  // order the rows of each leaf by their column lists
+  std::vector<int64_t> order(n);
+  for (int64_t r = 0; r < n; ++r) order[r] = r;
+  auto leaf_of = [&](int64_t r) { return h.pt_leaf[7 * (int64_t)h.rwg_tri[2 * (int64_t)perm[r]]]; };
+  for (int64_t r0 = 0; r0 < n;) {
+    int64_t r1 = r0 + 1;
+    while (r1 < n && leaf_of(r1) == leaf_of(r0)) ++r1;
+    std::stable_sort(order.begin() + r0, order.begin() + r1, [&](int64_t a, int64_t b) {
+      const int32_t *pa = col4.data() + ptr4[a], *pb = col4.data() + ptr4[b];
+      return std::lexicographical_compare(pa, pa + row_len(a), pb, pb + row_len(b));
+    });
+    r0 = r1;
+  }
+  const int64_t ng = (n + NG_ROWS - 1) / NG_ROWS;
+  // union of each group's columns (ascending), padded to an even count
+  std::vector<std::vector<int32_t>> ucol(ng);
+  auto unions = [&](int64_t g0, int64_t g1) {
+    for (int64_t g = g0; g < g1; ++g) {
+      std::vector<int32_t> &u = ucol[g];
+      for (int i = 0; i < NG_ROWS && g * NG_ROWS + i < n; ++i) {
+        const int64_t r = order[g * NG_ROWS + i];
+        u.insert(u.end(), col4.begin() + ptr4[r], col4.begin() + ptr4[r] + row_len(r));
+      }
+      std::sort(u.begin(), u.end());
+      u.erase(std::unique(u.begin(), u.end()), u.end());
+      if (u.empty()) u.push_back(0);
+      if (u.size() & 1) u.push_back(u.back());
+    }
+  };
+  const int nth = (int)std::max<unsigned>(1, std::min<unsigned>(16, std::thread::hardware_concurrency()));
+  auto run_threads = [&](auto &&fn, int64_t count) {
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nth; ++t) pool.emplace_back(fn, count * t / nth, count * (t + 1) / nth);
+    for (auto &th : pool) th.join();
+  };
+  run_threads(unions, ng);
+  std::vector<int64_t> gptr(ng + 1, 0);
+  for (int64_t g = 0; g < ng; ++g) gptr[g + 1] = gptr[g] + (int64_t)ucol[g].size();
+  const int64_t nslot = gptr[ng];
+  std::vector<int32_t> gcol(std::max<int64_t>(nslot, 1)), grow(std::max<int64_t>(ng * NG_ROWS, 1), -1);
+  for (int64_t g = 0; g < ng; ++g) {
+    std::copy(ucol[g].begin(), ucol[g].end(), gcol.begin() + gptr[g]);
+    for (int i = 0; i < NG_ROWS && g * NG_ROWS + i < n; ++i) grow[g * NG_ROWS + i] = perm[order[g * NG_ROWS + i]];
+  }
+  std::vector<std::vector<int32_t>>().swap(ucol);
+  c->d_ng_ptr = (int64_t *)dalloc(c, sizeof(int64_t) * (ng + 1));
+  c->d_ng_col = (int32_t *)dalloc(c, sizeof(int32_t) * std::max<int64_t>(nslot, 1));
+  c->d_ng_row = (int32_t *)dalloc(c, sizeof(int32_t) * std::max<int64_t>(ng * NG_ROWS, 1));
+  c->d_ng_val = (cplxf *)dalloc(c, sizeof(cplxf) * std::max<int64_t>(nslot * NG_ROWS, 1));
+  check_cuda(cudaMemcpy(c->d_ng_ptr, gptr.data(), sizeof(int64_t) * (ng + 1), cudaMemcpyHostToDevice), "near groups");
+  if (nslot > 0)
+    check_cuda(cudaMemcpy(c->d_ng_col, gcol.data(), sizeof(int32_t) * nslot, cudaMemcpyHostToDevice), "near groups");
+  if (ng > 0)
+    check_cuda(cudaMemcpy(c->d_ng_row, grow.data(), sizeof(int32_t) * ng * NG_ROWS, cudaMemcpyHostToDevice),
+               "near groups");
+  // source index in the padded CSR of every (slot, row) value, -1 for the zeros; built
+  // and gathered in chunks of groups to bound the host index array (a single group has
+  // at most n + 1 slots)
+  const int64_t chunk_slots = (int64_t)1 << 24;
+  std::vector<int64_t> src;
+  int64_t *d_src = (int64_t *)dalloc(
+      c, sizeof(int64_t) * (size_t)std::min<int64_t>(std::max<int64_t>(nslot, 1) * NG_ROWS,
+                                                     (chunk_slots + 2 * (int64_t)n + 2) * NG_ROWS));
+  for (int64_t g0 = 0; g0 < ng;) {
+    int64_t g1 = g0 + 1;
+    while (g1 < ng && gptr[g1 + 1] - gptr[g0] <= chunk_slots) ++g1;
+    const int64_t s0 = gptr[g0], cnt = (gptr[g1] - s0) * NG_ROWS;
+    src.assign(cnt, -1);
+    auto fill = [&](int64_t a, int64_t b) {
+      for (int64_t g = g0 + a; g < g0 + b; ++g)
+        for (int i = 0; i < NG_ROWS && g * NG_ROWS + i < n; ++i) {
+          const int64_t r = order[g * NG_ROWS + i], e0 = ptr4[r], len = row_len(r);
+          int64_t e = e0;  // both lists ascending: walk them together
+          for (int64_t sl = gptr[g]; sl < gptr[g + 1] && e < e0 + len; ++sl)
+            if (gcol[sl] == col4[e]) {  // a repeated last slot stays 0: e has moved on
+              src[(sl - s0) * NG_ROWS + i] = e;
+              ++e;
+            }
+        }
+    };
+    run_threads(fill, g1 - g0);
+    check_cuda(cudaMemcpy(d_src, src.data(), sizeof(int64_t) * cnt, cudaMemcpyHostToDevice), "near groups");
+    k_gather_c64<<<(unsigned)std::min<int64_t>((cnt + 255) / 256, 1 << 16), 256, 0, c->stream>>>(
+        c->d_ng_val + s0 * NG_ROWS, d_src, c->d_nz_val32, cnt);
+    check_cuda(cudaStreamSynchronize(c->stream), "near groups");
+    g0 = g1;
+  }
+  dfree(c, d_src);
+  c->n_group = ng;
 }
 
 void build_mixed(nesa_ctx *c) {

@@ -81,9 +81,9 @@ def test_refined_solve_with_tensor_product():
 
 
 def test_many_rhs_near_field_partial_group():
-    # 40 right-hand sides: the near field runs one lane per right-hand side in groups of
-    # 32 (the second group partly idle), and so does the per-leaf reception product; every
-    # column must match its own single product
+    # 40 right-hand sides: the near field runs four rows at a time and the per-leaf
+    # reception product a leaf's columns at a time, both with two right-hand sides per
+    # lane (lanes 20-31 idle); every column must match its own single product
     # (different summation order in FP32: bounded by the mixed tolerance)
     import paper_1801_03589_gb300 as nesa
     c, g = build("C1b")
@@ -122,6 +122,35 @@ def test_many_rhs_reception_large_leaves():
     e = rel(Y[39, rows], o.matvec_rows(xh[39], rows))
     print("C1b at 3 levels (max %d V columns per leaf), 40 RHS: rel err vs oracle (12 rows) %.2e" % (mc, e))
     assert e < TOL_TC
+
+
+@pytest.mark.parametrize("nrhs", [33, 64])
+def test_many_rhs_grouped_near_field(nrhs):
+    # 32 or more right-hand sides: the near field runs four rows at a time over the union
+    # of their columns (a row's value 0 where it lacks a column), two right-hand sides
+    # per lane; an odd count pads the x rows to an even stride with zeros.  Every column
+    # of the near part against the FP64 near part (complex64 values and x, FP32 sums:
+    # 1e-5 as for one right-hand side), every column of the whole product against the
+    # FP64 product (the mixed tolerance), and sampled rows of the last column against the
+    # oracle's near rows (Eq. 9).
+    import paper_1801_03589_gb300 as nesa
+    c, g = build("C3a")
+    X = torch.from_numpy(random_coefficients(g.n, nrhs, seed=60 + nrhs)).cuda()
+    Yn = g.matvec(X, parts=nesa.PART_NEAR | nesa.PART_MIXED).cpu().numpy()
+    Yn64 = g.matvec(X, parts=nesa.PART_NEAR).cpu().numpy()
+    assert nesa.lib().nesa_device_status(g._h) == nesa.OK
+    en = [rel(Yn[r], Yn64[r]) for r in range(nrhs)]
+    Y = g.matvec(X, parts=nesa.PART_ALL | nesa.PART_MIXED).cpu().numpy()
+    Y64 = g.matvec(X, parts=nesa.PART_ALL).cpu().numpy()
+    ea = [rel(Y[r], Y64[r]) for r in range(nrhs)]
+    o = NesaOracle(c["vertices"], c["triangles"], c["k"], c["leaf_size"], c["n_levels"])
+    rows = np.unique(np.linspace(0, g.n - 1, 9).astype(np.int64))
+    xh = X[nrhs - 1].cpu().numpy()
+    eo = rel(Yn[nrhs - 1, rows], o.near_rows(rows) @ xh)
+    print("C3a grouped near field, %d RHS: max rel err vs FP64 near %.2e, whole product %.2e, "
+          "near rows vs oracle %.2e" % (nrhs, max(en), max(ea), eo))
+    assert max(en) < 1e-5 and eo < 1e-5
+    assert max(ea) < TOL_TC
 
 
 @pytest.mark.parametrize("name", ["C1b", "C3a"])
