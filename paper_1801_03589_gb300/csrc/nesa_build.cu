@@ -557,6 +557,8 @@ static void build_device(nesa_ctx *c, const nesa_params &p) {
         k_translation_fill<<<grid_for(dl.noff * q * (int64_t)q, 256), 256, 0, st>>>(dl.D, d_E, q, d_off, dl.noff,
                                                                                      hl.width, c->k);
         check_cuda(cudaGetLastError(), "translation fill");
+        dl.Ds = (double *)dalloc(c, sizeof(double) * (size_t)dl.noff * q * q);
+        plane_sum(c, dl.Ds, dl.D, dl.noff * q * (int64_t)q);
       } else {
         dl.E = d_E;
         dl.offs = d_off;
@@ -586,6 +588,7 @@ static void build_device(nesa_ctx *c, const nesa_params &p) {
         dl.cil_src = upload(c, csrc);
         dl.cil_slot = upload(c, cslot);
         dl.Dw = (cplx *)dalloc(c, sizeof(cplx) * (size_t)dl.chunk_slots * q * q);
+        dl.Dws = (double *)dalloc(c, sizeof(double) * (size_t)dl.chunk_slots * q * q);
       }
       // C_l (l > l0): K_{l-1} G(T_{l-1}, E_l + delta)
       if (l > h.l0) {

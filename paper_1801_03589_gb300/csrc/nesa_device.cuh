@@ -59,6 +59,7 @@ struct DevLevel {
   int32_t *parent = nullptr, *octant = nullptr, *child_ptr = nullptr;
   int32_t *il_ptr = nullptr, *il_src = nullptr, *il_slot = nullptr;
   cplx *D = nullptr;   // [noff][q][q] column-major per offset
+  double *Ds = nullptr;  // [noff][q][q] Re + Im of D (the FP64 product's 3M sums)
   cplx *C = nullptr;   // [8][q_{l-1}][q] column-major (rows: parent's sources)
   cplx *Ct = nullptr;  // [8][q][q_{l-1}] column-major (transpose of C)
   cplx *K = nullptr;   // [q][2q] column-major
@@ -72,6 +73,7 @@ struct DevLevel {
   int chunk_slots = 0, nchunk = 0;
   int32_t *cil_ptr = nullptr, *cil_src = nullptr, *cil_slot = nullptr;
   cplx *Dw = nullptr;
+  double *Dws = nullptr;  // Re + Im of Dw
   cplxf *Dw32 = nullptr;
   cplx *s = nullptr;   // workspace [nbox][4*nrhs][q] outgoing equivalent sources
   cplx *o = nullptr;   // workspace [nbox][4*nrhs][q] incoming field at the equivalent points
@@ -121,12 +123,16 @@ struct nesa_ctx {
   nesa::cplxf *d_rcv = nullptr;        // reception per V column, [ncol][nrhs] (nrhs >= 32)
   // the same near field for 32 or more right-hand sides (built by the first such
   // product): internal rows in groups of four, a group's columns the union of its
-  // rows' columns, a row's value 0 at the columns it lacks
+  // rows' columns, a row's value 0 at the columns it lacks; groups in blocks of eight
+  // whose x columns are the union of the eight groups' columns
   int64_t n_group = 0;
-  int64_t *d_ng_ptr = nullptr;         // [n_group + 1] first column slot of each group (even)
-  int32_t *d_ng_col = nullptr;         // [slot] internal column (a group's last may repeat, value 0)
+  int64_t *d_ng_ptr = nullptr;         // [n_group + 1] first column slot of each group
+  int32_t *d_ng_loc = nullptr;         // [slot] position of the slot's column in its block's union
   nesa::cplxf *d_ng_val = nullptr;     // [slot][4] the four rows' values at that column
   int32_t *d_ng_row = nullptr;         // [n_group][4] ABI row of each group member, -1 past the end
+  int64_t *d_nb_ptr = nullptr;         // [n_block + 1] start of each block's union in d_nb_col
+  int32_t *d_nb_col = nullptr;         // internal columns of the blocks' unions, ascending per block
+  int32_t *d_vc_int = nullptr;         // [ncol] internal index of each V column's RWG function
   nesa::cplxf *d_V32 = nullptr;
   int nrhs_cap32 = 0;
   // levels
@@ -179,6 +185,8 @@ void device_tree(nesa_ctx *c, const nesa_params &p, HostModel &m);
 // ([ns][q][q] column-major, complex128 or complex64), on the context's stream
 void fill_translations(nesa_ctx *c, int level, int64_t slot0, int64_t ns, cplx *D);
 void fill_translations(nesa_ctx *c, int level, int64_t slot0, int64_t ns, cplxf *D);
+// S[e] = D[e].x + D[e].y for e < count, on the context's stream (FP64 translations' 3M sums)
+void plane_sum(nesa_ctx *c, double *S, const cplx *D, int64_t count);
 // an event from the context's pool (stage timing)
 cudaEvent_t take_event(nesa_ctx *c);
 // tensor-core translations of the mixed product (nesa_tc.cu)

@@ -281,6 +281,75 @@ __global__ void __launch_bounds__(512) k_radiate2w(cplxf *__restrict__ s, const 
   }
 }
 
+// Radiation of the mixed product for many right-hand sides (nrhs >= 32) as a small
+// complex product per leaf, s_b = V_b X_b (Eq. 10): a CTA owns 64 of the leaf's 4Q
+// rows (ch Q + i) and 64 right-hand sides; thread (warp w, lane l) owns rows 8w .. 8w+7
+// of the tile and right-hand sides 2l, 2l + 1.  The leaf's columns pass through shared
+// memory RL_KC at a time: V as [column][64 rows] (512 contiguous bytes per column, every
+// V value read once per 64 right-hand sides) and x as [column][64 right-hand sides]
+// from the permuted complex64 copy xw (512 contiguous bytes per column).  Per column a
+// lane reads its x pair with one 16-byte load and its eight V values with four
+// broadcast loads, and does 64 FP32 FMAs.  Per output the summation order over the
+// columns is that of one column at a time.
+constexpr int RL_KC = 32, RL_ROWS = 64;
+__global__ void __launch_bounds__(256) k_radiate_leaf(cplxf *__restrict__ s, const cplxf *__restrict__ V,
+                                                      const int32_t *__restrict__ vc_ptr,
+                                                      const int32_t *__restrict__ vc_int,
+                                                      const cplxf *__restrict__ xw, int ldx, int nrhs, int q) {
+  __shared__ __align__(16) cplxf Vs[RL_KC][RL_ROWS];
+  __shared__ __align__(16) float4 Xs[RL_KC][32];
+  const int32_t b = blockIdx.x;
+  const int k0 = blockIdx.y * RL_ROWS;  // first row (ch Q + i) of the tile
+  const int rb = blockIdx.z * 64;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q4 = 4 * q;
+  const int32_t g0 = vc_ptr[b], ns = vc_ptr[b + 1] - g0;
+  cplxf acc[8][2];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) acc[m][0] = acc[m][1] = make_float2(0.0f, 0.0f);
+  for (int j0 = 0; j0 < ns; j0 += RL_KC) {
+    const int len = min(RL_KC, ns - j0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < RL_KC * RL_ROWS; t += blockDim.x) {
+      const int j = t / RL_ROWS, rr = t % RL_ROWS;
+      Vs[j][rr] = j < len && k0 + rr < q4 ? V[(int64_t)(g0 + j0 + j) * q4 + k0 + rr] : make_float2(0.0f, 0.0f);
+    }
+    for (int t = threadIdx.x; t < RL_KC * 32; t += blockDim.x) {
+      const int j = t >> 5, pc = t & 31;
+      Xs[j][pc] = j < len && rb + 2 * pc < ldx
+                      ? *(const float4 *)(xw + (int64_t)vc_int[g0 + j0 + j] * ldx + rb + 2 * pc)
+                      : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+    __syncthreads();
+#pragma unroll 2
+    for (int j = 0; j < len; ++j) {
+      const float4 x2 = Xs[j][lane];
+      const cplxf xa = make_float2(x2.x, x2.y), xb = make_float2(x2.z, x2.w);
+      const float4 *vr = (const float4 *)&Vs[j][8 * warp];
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const float4 v2 = vr[h];
+        const cplxf va = make_float2(v2.x, v2.y), vb = make_float2(v2.z, v2.w);
+        cfma(acc[2 * h][0], va, xa);
+        cfma(acc[2 * h][1], va, xb);
+        cfma(acc[2 * h + 1][0], vb, xa);
+        cfma(acc[2 * h + 1][1], vb, xb);
+      }
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int k = k0 + 8 * warp + m;
+    if (k >= q4) break;
+    const int ch = k / q, i = k % q;
+#pragma unroll
+    for (int jj = 0; jj < 2; ++jj) {
+      const int r = rb + 2 * lane + jj;
+      if (r < nrhs) s[((int64_t)b * 4 * nrhs + 4 * r + ch) * q + i] = acc[m][jj];
+    }
+  }
+}
+
 // acc += M[i + j*ld] * col(ch)[j] over j < kdim, with the column (4 channels of kdim
 // values at src, channel stride kdim) staged through shared memory in chunks of JC
 template <typename CT>
@@ -351,6 +420,93 @@ __global__ void __launch_bounds__(512) k_translate(CT *__restrict__ o, const CT 
                      q, q, ch, active);
     if (active) o[((int64_t)a * 4 * nrhs + 4 * r + ch) * q + i] = acc;
   }
+}
+
+// FP64 translation and potential transfer, the translations in the 3M (Gauss) form.
+// For D = A + iB and a source column u + iv,
+//   Re(D x) = A u - B v,   Im(D x) = (A + B)(u + v) - A u - B v,
+// so with the sums S = A + B stored beside D (one FP64 plane per offset) an entry costs
+// three FMAs per channel instead of the four of the direct form, on a kernel bound by
+// the FP64 pipe.  Thread (channel ch, row i) as in k_translate (4Q threads per box, so
+// nearly every lane works at Q = 100); the source columns pass through shared memory as
+// (u, v) and u + v per channel, JC3 columns at a time.  The potential transfer C^T o_P
+// (Eq. 13) keeps the direct form in its own sum.  The three sums run over the columns in
+// order and are combined once at the end; a later chunk of generated offsets adds its
+// result to o.
+constexpr int JC3 = 256;
+__global__ void __launch_bounds__(512) k_translate64(double2 *__restrict__ o, const double2 *__restrict__ s,
+                                                     const double2 *__restrict__ D, const double *__restrict__ DS,
+                                                     const int32_t *__restrict__ il_ptr,
+                                                     const int32_t *__restrict__ il_src,
+                                                     const int32_t *__restrict__ il_slot, const double2 *__restrict__ op,
+                                                     const double2 *__restrict__ Ct, const int32_t *__restrict__ parent,
+                                                     const int32_t *__restrict__ octant, int nrhs, int q, int qp, int tr,
+                                                     int accum) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2 *col = (double2 *)smem_raw;                 // [4][JC3] (u, v)
+  double *colw = (double *)(smem_raw + sizeof(double2) * 4 * JC3);  // [4][JC3] u + v
+  const int32_t a = blockIdx.x;
+  const int ch = threadIdx.x / tr;
+  const int i = blockIdx.y * tr + threadIdx.x % tr;
+  const bool active = ch < 4 && i < q;
+  const int32_t e0 = il_ptr[a], e1 = il_ptr[a + 1];
+  if (accum && e0 == e1) return;  // a later chunk of offsets without pairs of this box
+  for (int r = 0; r < nrhs; ++r) {
+    double2 acc = make_double2(0.0, 0.0);
+    if (op)  // potential transfer from the parent (Eq. 13): o_a += C^T o_P
+      matvec_chunked(acc, col, op + ((int64_t)parent[a] * 4 * nrhs + 4 * r) * qp,
+                     Ct + (int64_t)octant[a] * q * qp + i, q, qp, ch, active);
+    double p0 = 0.0, p1 = 0.0, p2 = 0.0;  // A u, B v, S (u + v)
+    for (int32_t e = e0; e < e1; ++e) {  // translations (Eq. 12)
+      const double2 *src = s + ((int64_t)il_src[e] * 4 * nrhs + 4 * r) * q;
+      const double2 *M = D + (int64_t)il_slot[e] * q * q + i;
+      const double *MS = DS + (int64_t)il_slot[e] * q * q + i;
+      for (int j0 = 0; j0 < q; j0 += JC3) {
+        const int len = min(JC3, q - j0);
+        __syncthreads();
+        for (int t = threadIdx.x; t < 4 * len; t += blockDim.x) {
+          const double2 v = src[(int64_t)(t / len) * q + j0 + t % len];
+          col[t] = v;
+          colw[t] = v.x + v.y;
+        }
+        __syncthreads();
+        if (!active) continue;
+        const double2 *cs = col + ch * len;
+        const double *cw = colw + ch * len;
+        const double2 *Mj = M + (int64_t)j0 * q;
+        const double *Sj = MS + (int64_t)j0 * q;
+#pragma unroll 4
+        for (int j = 0; j < len; ++j) {
+          const double2 m = Mj[(int64_t)j * q];
+          const double sm = Sj[(int64_t)j * q];
+          const double2 x = cs[j];
+          p0 = fma(m.x, x.x, p0);
+          p1 = fma(m.y, x.y, p1);
+          p2 = fma(sm, cw[j], p2);
+        }
+      }
+    }
+    if (active) {
+      double2 *dst = o + ((int64_t)a * 4 * nrhs + 4 * r + ch) * q + i;
+      double2 v = make_double2(acc.x + (p0 - p1), acc.y + (p2 - p0 - p1));
+      if (accum) {  // earlier chunks
+        const double2 w = *dst;
+        v = make_double2(w.x + v.x, w.y + v.y);
+      }
+      *dst = v;
+    }
+  }
+}
+
+// S = Re + Im of every entry (the 3M sums of the FP64 translations)
+__global__ void k_plane_sum(double *__restrict__ S, const double2 *__restrict__ D, int64_t count) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x)
+    S[e] = D[e].x + D[e].y;
+}
+void plane_sum(nesa_ctx *c, double *S, const cplx *D, int64_t count) {
+  if (count <= 0) return;
+  k_plane_sum<<<(unsigned)std::min<int64_t>((count + 255) / 256, 1 << 16), 256, 0, c->stream>>>(S, D, count);
+  check_cuda(cudaGetLastError(), "plane sum");
 }
 
 // ------------------------------------------------------------------ near field + reception
@@ -585,62 +741,105 @@ __global__ void __launch_bounds__(256) k_receive_leaf(cplxf *__restrict__ R, con
 
 // Near field and reception sum of the mixed product for many right-hand sides
 // (nrhs >= 32).  The internal rows come in groups of four whose columns are the union
-// of the four rows' columns (a row's value is 0 at a column it lacks).  One warp per
-// (group, 64 right-hand sides); lane l owns right-hand sides 2l and 2l + 1.  Per column
-// a lane loads its two x values once (16 bytes; the warp reads 512 contiguous bytes of
-// xw) and uses them for all four rows: 32 FP32 FMAs per x load, against 8 with one row
-// per warp.  The column index and the four values are the same for every lane (one
-// broadcast load each).  The eight warps of a block take consecutive groups, which
-// share most of their columns, so their x loads meet in L1.  Two FP32 partial sums per
-// output (even and odd column slots), added in FP64.  The far part adds the reception
-// values R of the row's V columns (k_receive_leaf) times -i eta k.
-constexpr int NG_ROWS = 4;
+// of the four rows' columns (a row's value is 0 at a column it lacks), and the groups in
+// blocks of eight (one CTA, one warp per group) whose x columns are the union of the
+// eight groups' columns.  Lane l of a warp owns right-hand sides r0 + 2l and r0 + 2l + 1
+// of the CTA's 64.  The CTA copies the x rows of its column union into shared memory
+// NS_CH columns at a time (512 contiguous bytes per column, 16-byte asynchronous
+// copies, the next chunk in flight while this one is used), so every x value crosses
+// from L2 once per CTA instead of once per warp, and a warp never waits on a
+// column-then-x chain of global loads.  For each of its slots in the chunk a lane reads
+// its two x values with one conflict-free 16-byte shared load and the four values with
+// two broadcast loads, and does 32 FP32 FMAs.  A group stores its slots' positions in
+// the CTA's union (ascending), so the slots of a chunk are a prefix of the remaining
+// ones: 32 positions are read at a time and a ballot counts those in the chunk.  FP32
+// sums in slot order, converted to FP64; the far part adds the reception values R of
+// the row's V columns (k_receive_leaf) times -i eta k.
+constexpr int NG_ROWS = 4, NS_GROUPS = 8, NS_CH = 64;
+constexpr int NS_SMEM = 2 * NS_CH * 32 * 16;  // two chunks of NS_CH columns x 64 right-hand sides
+__device__ __forceinline__ void ns_cp16(uint32_t dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void ns_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void ns_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 __global__ void __launch_bounds__(256) k_near_group(cplx *__restrict__ y, const cplxf *__restrict__ xw, int ldx,
                                                     int64_t n, int nrhs, int64_t n_group,
                                                     const int64_t *__restrict__ g_ptr,
-                                                    const int32_t *__restrict__ g_col,
+                                                    const int32_t *__restrict__ g_loc,
                                                     const float4 *__restrict__ g_val,
                                                     const int32_t *__restrict__ g_row,
+                                                    const int64_t *__restrict__ b_ptr,
+                                                    const int32_t *__restrict__ b_col,
                                                     const int32_t *__restrict__ rx_ptr,
                                                     const int32_t *__restrict__ rx_col, const cplxf *__restrict__ R,
                                                     double eta_k, int parts) {
-  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  const int nblk = (nrhs + 63) >> 6;
-  const int64_t g = wid / nblk;
-  if (g >= n_group) return;
-  const int r0 = (int)(wid % nblk) * 64 + 2 * lane;  // this lane's right-hand sides r0, r0 + 1
-  const bool on0 = r0 < nrhs, on1 = r0 + 1 < nrhs;
-  // acc[p][i][j]: column-slot parity p, group row i, right-hand side r0 + j
-  cplxf acc[2][NG_ROWS][2];
+  extern __shared__ __align__(16) float4 xs4[];  // [2][NS_CH][32]: x of 64 right-hand sides per column
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t blk = blockIdx.x;
+  const int64_t g = blk * NS_GROUPS + warp;
+  const bool gon = g < n_group;
+  const int rb = blockIdx.y * 64;
+  const int r0 = rb + 2 * lane;  // this lane's right-hand sides r0, r0 + 1
+  cplxf acc[NG_ROWS][2];
 #pragma unroll
-  for (int p = 0; p < 2; ++p)
-#pragma unroll
-    for (int i = 0; i < NG_ROWS; ++i) acc[p][i][0] = acc[p][i][1] = make_float2(0.0f, 0.0f);
+  for (int i = 0; i < NG_ROWS; ++i) acc[i][0] = acc[i][1] = make_float2(0.0f, 0.0f);
   if (parts & NESA_PART_NEAR) {
-    const float4 *xc = (const float4 *)xw + (on0 ? r0 >> 1 : 0);  // ldx and r0 even: 16-byte aligned
-    const int64_t lq = ldx >> 1;
-    const int64_t z0 = g_ptr[g], z1 = g_ptr[g + 1];  // even
-#pragma unroll 2
-    for (int64_t e = z0; e < z1; e += 2) {
-      const int2 k = *(const int2 *)(g_col + e);
-      const float4 xa = xc[(int64_t)k.x * lq], xb = xc[(int64_t)k.y * lq];
-      const float4 v0 = g_val[2 * e], v1 = g_val[2 * e + 1], v2 = g_val[2 * e + 2], v3 = g_val[2 * e + 3];
-      const cplxf va[NG_ROWS] = {make_float2(v0.x, v0.y), make_float2(v0.z, v0.w), make_float2(v1.x, v1.y),
-                                 make_float2(v1.z, v1.w)};
-      const cplxf vb[NG_ROWS] = {make_float2(v2.x, v2.y), make_float2(v2.z, v2.w), make_float2(v3.x, v3.y),
-                                 make_float2(v3.z, v3.w)};
-      const cplxf xa0 = make_float2(xa.x, xa.y), xa1 = make_float2(xa.z, xa.w);
-      const cplxf xb0 = make_float2(xb.x, xb.y), xb1 = make_float2(xb.z, xb.w);
-#pragma unroll
-      for (int i = 0; i < NG_ROWS; ++i) {
-        cfma(acc[0][i][0], va[i], xa0);
-        cfma(acc[0][i][1], va[i], xa1);
-        cfma(acc[1][i][0], vb[i], xb0);
-        cfma(acc[1][i][1], vb[i], xb1);
+    const int64_t c0 = b_ptr[blk], nu = b_ptr[blk + 1] - c0;
+    const int nch = (int)((nu + NS_CH - 1) / NS_CH);
+    int64_t e = gon ? g_ptr[g] : 0;
+    const int64_t e1 = gon ? g_ptr[g + 1] : 0;
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(xs4);
+    auto stage = [&](int c) {  // chunk c into buffer c & 1
+      for (int t = threadIdx.x; t < NS_CH * 32; t += blockDim.x) {
+        const int j = t >> 5, pc = t & 31;  // column j of the chunk, right-hand sides rb + 2 pc, + 1
+        const int64_t jj = (int64_t)c * NS_CH + j;
+        float4 *dst = xs4 + ((c & 1) * NS_CH + j) * 32 + pc;
+        if (jj < nu && rb + 2 * pc < ldx)
+          ns_cp16(sbase + (uint32_t)((char *)dst - (char *)xs4), xw + (int64_t)b_col[c0 + jj] * ldx + rb + 2 * pc);
+        else
+          *dst = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
       }
+      ns_commit();
+    };
+    if (nch > 0) stage(0);
+    for (int c = 0; c < nch; ++c) {
+      if (c + 1 < nch) {
+        stage(c + 1);
+        ns_wait<1>();
+      } else {
+        ns_wait<0>();
+      }
+      __syncthreads();
+      const float4 *xb = xs4 + (c & 1) * NS_CH * 32 + lane;
+      const int lim = (c + 1) * NS_CH;
+      while (e < e1) {  // warp-uniform
+        const int32_t lc = e + lane < e1 ? g_loc[e + lane] : 0x7fffffff;
+        const int cnt = __popc(__ballot_sync(0xffffffffu, lc < lim));
+#pragma unroll 4
+        for (int u = 0; u < cnt; ++u) {
+          const int j = __shfl_sync(0xffffffffu, lc, u) - c * NS_CH;
+          const float4 x2 = xb[j * 32];
+          const float4 v0 = g_val[2 * (e + u)], v1 = g_val[2 * (e + u) + 1];
+          const cplxf xa = make_float2(x2.x, x2.y), xb2 = make_float2(x2.z, x2.w);
+          const cplxf va[NG_ROWS] = {make_float2(v0.x, v0.y), make_float2(v0.z, v0.w), make_float2(v1.x, v1.y),
+                                     make_float2(v1.z, v1.w)};
+#pragma unroll
+          for (int i = 0; i < NG_ROWS; ++i) {
+            cfma(acc[i][0], va[i], xa);
+            cfma(acc[i][1], va[i], xb2);
+          }
+        }
+        e += cnt;
+        if (cnt < 32) break;
+      }
+      __syncthreads();  // every warp is done with this buffer before it is refilled
     }
   }
+  if (!gon) return;
+  const bool on0 = r0 < nrhs, on1 = r0 + 1 < nrhs;
 #pragma unroll
   for (int i = 0; i < NG_ROWS; ++i) {
     const int32_t m = g_row[NG_ROWS * g + i];
@@ -649,8 +848,7 @@ __global__ void __launch_bounds__(256) k_near_group(cplx *__restrict__ y, const 
     for (int j = 0; j < 2; ++j) {
       const int rr = r0 + j;
       const int rc = rr < nrhs ? rr : 0;
-      double2 v = make_double2((double)acc[0][i][j].x + (double)acc[1][i][j].x,
-                               (double)acc[0][i][j].y + (double)acc[1][i][j].y);
+      double2 v = make_double2((double)acc[i][j].x, (double)acc[i][j].y);
       if (parts & NESA_PART_FAR) {
         double fx = 0.0, fy = 0.0;
         for (int32_t e = rx_ptr[m]; e < rx_ptr[m + 1]; ++e) {
@@ -781,6 +979,13 @@ static void run_product(nesa_ctx *c, const OpView<CT> &op, const cplx *x, cplx *
   const int L = c->L, l0 = c->l0;
   const double B = sizeof(CT);
   const double ncol = (double)c->info.v_columns;
+  if constexpr (std::is_same<CT, cplxf>::value) {
+    if (nrhs >= 32) {  // x permuted to complex64 [n][ldx] for the radiation and the near field
+      const int ldx = (nrhs + 1) & ~1;
+      k_perm_x_wide<<<(unsigned)std::min<int64_t>((c->n * ldx + 255) / 256, 1 << 16), 256, 0, st>>>(
+          c->d_xp, x, c->d_perm, c->n, nrhs, ldx);
+    }
+  }
   if (parts & NESA_PART_FAR) {
     {  // radiation
       DevLevel &d = c->lev[L];
@@ -792,7 +997,13 @@ static void run_product(nesa_ctx *c, const OpView<CT> &op, const cplx *x, cplx *
                     B * (4.0 * ncol * d.q + 4.0 * nrhs * d.nbox * d.q) + 16.0 * nrhs * c->n);
       bool done = false;
       if constexpr (std::is_same<CT, cplxf>::value) {
-        if (d.q % 2 == 0) {  // two rows per thread, 16-byte V loads
+        if (nrhs >= 32) {  // per-leaf product on the permuted complex64 x (made before the far part)
+          k_radiate_leaf<<<dim3((unsigned)d.nbox, (unsigned)((4 * d.q + RL_ROWS - 1) / RL_ROWS),
+                                (unsigned)((nrhs + 63) / 64)),
+                           256, 0, st>>>(op.s[L], op.V, c->d_vc_ptr, c->d_vc_int, c->d_xp, (nrhs + 1) & ~1, nrhs,
+                                         d.q);
+          done = true;
+        } else if (d.q % 2 == 0) {  // two rows per thread, 16-byte V loads
           Tiling t2 = tiling(d.q / 2);
           if (rbk == 1)
             k_radiate2<<<dim3((unsigned)d.nbox, t2.ntile), t2.threads, smem, st>>>(
@@ -835,6 +1046,22 @@ static void run_product(nesa_ctx *c, const OpView<CT> &op, const cplx *x, cplx *
       double by = B * ((double)d.noff * d.q * d.q + (down ? 8.0 * d.q * qp : 0.0) +
                        4.0 * nrhs * (2.0 * d.nbox * d.q + (down ? (double)c->lev[l - 1].nbox * qp : 0.0)));
       StageScope sc(c, 2, fl, by);
+      // FP64: k_translate64 (3M form with the stored sums S); complex64 (the CUDA-core
+      // engine of the mixed product): k_translate
+      auto translate = [&](const CT *Dm, const double *DSm, const int32_t *ptr, const int32_t *src,
+                           const int32_t *slot, bool with_parent, int accum) {
+        if constexpr (std::is_same<CT, cplx>::value) {
+          const size_t smem3 = std::max(sizeof(double2) * 4 * (size_t)std::min(JC, qp),
+                                        (sizeof(double2) + sizeof(double)) * 4 * (size_t)JC3);
+          k_translate64<<<dim3((unsigned)d.nbox, t.ntile), t.threads, smem3, st>>>(
+              op.o[l], op.s[l], Dm, DSm, ptr, src, slot, with_parent ? op.o[l - 1] : nullptr,
+              with_parent ? op.Ct[l] : nullptr, d.parent, d.octant, nrhs, d.q, qp, t.tr, accum);
+        } else {
+          k_translate<CT><<<dim3((unsigned)d.nbox, t.ntile), t.threads, smem, st>>>(
+              op.o[l], op.s[l], Dm, ptr, src, slot, with_parent ? op.o[l - 1] : nullptr,
+              with_parent ? op.Ct[l] : nullptr, d.parent, d.octant, nrhs, d.q, qp, t.tr, accum);
+        }
+      };
       if constexpr (std::is_same<CT, cplxf>::value) {
         if (c->tc_enabled) {
           tc_translate_level(c, l, op.s[l], op.o[l], down ? op.o[l - 1] : nullptr, down ? op.Ct[l] : nullptr, nrhs);
@@ -851,16 +1078,13 @@ static void run_product(nesa_ctx *c, const OpView<CT> &op, const cplx *x, cplx *
         for (int chk = 0; chk < d.nchunk; ++chk) {
           const int64_t slot0 = (int64_t)chk * d.chunk_slots, ns = std::min<int64_t>(d.chunk_slots, d.noff - slot0);
           fill_translations(c, l, slot0, ns, Dw);
-          k_translate<CT><<<dim3((unsigned)d.nbox, t.ntile), t.threads, smem, st>>>(
-              op.o[l], op.s[l], Dw, d.cil_ptr + (int64_t)chk * (d.nbox + 1), d.cil_src, d.cil_slot,
-              (down && chk == 0) ? op.o[l - 1] : nullptr, (down && chk == 0) ? op.Ct[l] : nullptr, d.parent,
-              d.octant, nrhs, d.q, qp, t.tr, chk > 0 ? 1 : 0);
+          if constexpr (std::is_same<CT, cplx>::value) plane_sum(c, d.Dws, Dw, ns * d.q * (int64_t)d.q);
+          translate(Dw, d.Dws, d.cil_ptr + (int64_t)chk * (d.nbox + 1), d.cil_src, d.cil_slot, down && chk == 0,
+                    chk > 0 ? 1 : 0);
         }
         continue;
       }
-      k_translate<CT><<<dim3((unsigned)d.nbox, t.ntile), t.threads, smem, st>>>(
-          op.o[l], op.s[l], op.D[l], d.il_ptr, d.il_src, d.il_slot, down ? op.o[l - 1] : nullptr,
-          down ? op.Ct[l] : nullptr, d.parent, d.octant, nrhs, d.q, qp, t.tr, 0);
+      translate(op.D[l], d.Ds, d.il_ptr, d.il_src, d.il_slot, down, 0);
     }
   }
   const DevLevel &dL = c->lev[L];
@@ -874,17 +1098,16 @@ static void run_product(nesa_ctx *c, const OpView<CT> &op, const cplx *x, cplx *
   if constexpr (std::is_same<CT, cplxf>::value) {
     const unsigned pgrid = (unsigned)std::min<int64_t>((c->n * nrhs + 255) / 256, 1 << 16);
     if (nrhs >= 32) {  // many right-hand sides: groups of four rows, two right-hand sides per lane
-      const int ldx = (nrhs + 1) & ~1;
-      if (parts & NESA_PART_NEAR)
-        k_perm_x_wide<<<(unsigned)std::min<int64_t>((c->n * ldx + 255) / 256, 1 << 16), 256, 0, st>>>(
-            c->d_xp, x, c->d_perm, c->n, nrhs, ldx);
+      const int ldx = (nrhs + 1) & ~1;  // xw was made before the far part
       if (parts & NESA_PART_FAR)
         k_receive_leaf<<<dim3((unsigned)c->nleaf, (unsigned)((nrhs + RC_RHS - 1) / RC_RHS)), 256, 0, st>>>(
             c->d_rcv, op.V, op.o[L], c->d_vc_ptr, nrhs, dL.q, (float)(-1.0 / (c->k * c->k)));
       if (c->n_group > 0)
-        k_near_group<<<grid_for(c->n_group * ((nrhs + 63) / 64) * 32, 256), 256, 0, st>>>(
-            y, c->d_xp, ldx, c->n, nrhs, c->n_group, c->d_ng_ptr, c->d_ng_col, (const float4 *)c->d_ng_val,
-            c->d_ng_row, c->d_rx_ptr, c->d_rx_col, c->d_rcv, c->eta * c->k, parts);
+        k_near_group<<<dim3((unsigned)((c->n_group + NS_GROUPS - 1) / NS_GROUPS), (unsigned)((nrhs + 63) / 64)),
+                       32 * NS_GROUPS, NS_SMEM, st>>>(y, c->d_xp, ldx, c->n, nrhs, c->n_group, c->d_ng_ptr,
+                                                      c->d_ng_loc, (const float4 *)c->d_ng_val, c->d_ng_row,
+                                                      c->d_nb_ptr, c->d_nb_col, c->d_rx_ptr, c->d_rx_col, c->d_rcv,
+                                                      c->eta * c->k, parts);
     } else {
       if (parts & NESA_PART_NEAR) k_perm_x<<<pgrid, 256, 0, st>>>(c->d_xp, x, c->d_perm, c->n, nrhs);
       auto near = nrhs == 1 ? k_near_receive_v<1> : k_near_receive_v<4>;
@@ -1020,9 +1243,11 @@ __global__ void k_gather_c64(cplxf *__restrict__ dst, const int64_t *__restrict_
 // Within the internal rows of one leaf (rows whose first quadrature point lies in it),
 // rows are ordered by their column lists, so that rows with the same list (RWG functions
 // whose quadrature points lie in the same leaves) sit next to each other; then every
-// four consecutive rows form a group over the union of their columns.  The values are
-// the complex64 values of the padded CSR, gathered on the device; the zeros a row gets
-// at columns it lacks change none of its sums.
+// four consecutive rows form a group over the union of their columns, and every eight
+// consecutive groups a block over the union of the groups' columns.  A slot stores the
+// position of its column in the block's union.  The values are the complex64 values of
+// the padded CSR, gathered on the device; the zeros a row gets at columns it lacks
+// change none of its sums.
 static void build_near_groups(nesa_ctx *c) {
   const HostModel &h = c->h;
   const int64_t n = c->n;
@@ -1030,6 +1255,14 @@ static void build_near_groups(nesa_ctx *c) {
   std::vector<int32_t> perm(std::max<int64_t>(n, 1));
   check_cuda(cudaMemcpy(ptr4.data(), c->d_nz_ptr4, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost), "near groups");
   check_cuda(cudaMemcpy(perm.data(), c->d_perm, sizeof(int32_t) * n, cudaMemcpyDeviceToHost), "near groups");
+  {  // internal index of each V column's RWG function (the radiation's x rows)
+    std::vector<int32_t> inv(std::max<int64_t>(n, 1)), vint(std::max<size_t>(h.vc_rwg.size(), 1));
+    for (int64_t r = 0; r < n; ++r) inv[perm[r]] = (int32_t)r;
+    for (size_t g = 0; g < h.vc_rwg.size(); ++g) vint[g] = inv[h.vc_rwg[g]];
+    c->d_vc_int = (int32_t *)dalloc(c, sizeof(int32_t) * vint.size());
+    check_cuda(cudaMemcpy(c->d_vc_int, vint.data(), sizeof(int32_t) * vint.size(), cudaMemcpyHostToDevice),
+               "near groups");
+  }
   const int64_t nnz4 = ptr4[n];
   std::vector<int32_t> col4(std::max<int64_t>(nnz4, 1));
   if (nnz4 > 0)
@@ -1084,14 +1317,41 @@ static void build_near_groups(nesa_ctx *c) {
     std::copy(ucol[g].begin(), ucol[g].end(), gcol.begin() + gptr[g]);
     for (int i = 0; i < NG_ROWS && g * NG_ROWS + i < n; ++i) grow[g * NG_ROWS + i] = perm[order[g * NG_ROWS + i]];
   }
+  // blocks of NS_GROUPS groups: the union of their columns, and every slot's position in it
+  const int64_t nb = (ng + NS_GROUPS - 1) / NS_GROUPS;
+  std::vector<std::vector<int32_t>> bcol(nb);
+  std::vector<int32_t> gloc(std::max<int64_t>(nslot, 1));
+  auto blocks = [&](int64_t b0, int64_t b1) {
+    for (int64_t b = b0; b < b1; ++b) {
+      std::vector<int32_t> &u = bcol[b];
+      const int64_t g0 = b * NS_GROUPS, g1 = std::min<int64_t>(ng, g0 + NS_GROUPS);
+      u.assign(gcol.begin() + gptr[g0], gcol.begin() + gptr[g1]);
+      std::sort(u.begin(), u.end());
+      u.erase(std::unique(u.begin(), u.end()), u.end());
+      for (int64_t sl = gptr[g0]; sl < gptr[g1]; ++sl)
+        gloc[sl] = (int32_t)(std::lower_bound(u.begin(), u.end(), gcol[sl]) - u.begin());
+    }
+  };
+  run_threads(blocks, nb);
+  std::vector<int64_t> bptr(nb + 1, 0);
+  for (int64_t b = 0; b < nb; ++b) bptr[b + 1] = bptr[b] + (int64_t)bcol[b].size();
+  std::vector<int32_t> bflat(std::max<int64_t>(bptr[nb], 1));
+  for (int64_t b = 0; b < nb; ++b) std::copy(bcol[b].begin(), bcol[b].end(), bflat.begin() + bptr[b]);
+  std::vector<std::vector<int32_t>>().swap(bcol);
   std::vector<std::vector<int32_t>>().swap(ucol);
+  c->d_nb_ptr = (int64_t *)dalloc(c, sizeof(int64_t) * (nb + 1));
+  c->d_nb_col = (int32_t *)dalloc(c, sizeof(int32_t) * bflat.size());
+  check_cuda(cudaMemcpy(c->d_nb_ptr, bptr.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice), "near groups");
+  check_cuda(cudaMemcpy(c->d_nb_col, bflat.data(), sizeof(int32_t) * bflat.size(), cudaMemcpyHostToDevice),
+             "near groups");
+  check_cuda(cudaFuncSetAttribute(k_near_group, cudaFuncAttributeMaxDynamicSharedMemorySize, NS_SMEM), "near groups");
   c->d_ng_ptr = (int64_t *)dalloc(c, sizeof(int64_t) * (ng + 1));
-  c->d_ng_col = (int32_t *)dalloc(c, sizeof(int32_t) * std::max<int64_t>(nslot, 1));
+  c->d_ng_loc = (int32_t *)dalloc(c, sizeof(int32_t) * std::max<int64_t>(nslot, 1));
   c->d_ng_row = (int32_t *)dalloc(c, sizeof(int32_t) * std::max<int64_t>(ng * NG_ROWS, 1));
   c->d_ng_val = (cplxf *)dalloc(c, sizeof(cplxf) * std::max<int64_t>(nslot * NG_ROWS, 1));
   check_cuda(cudaMemcpy(c->d_ng_ptr, gptr.data(), sizeof(int64_t) * (ng + 1), cudaMemcpyHostToDevice), "near groups");
   if (nslot > 0)
-    check_cuda(cudaMemcpy(c->d_ng_col, gcol.data(), sizeof(int32_t) * nslot, cudaMemcpyHostToDevice), "near groups");
+    check_cuda(cudaMemcpy(c->d_ng_loc, gloc.data(), sizeof(int32_t) * nslot, cudaMemcpyHostToDevice), "near groups");
   if (ng > 0)
     check_cuda(cudaMemcpy(c->d_ng_row, grow.data(), sizeof(int32_t) * ng * NG_ROWS, cudaMemcpyHostToDevice),
                "near groups");
