@@ -130,6 +130,8 @@ struct nesa_ctx {
   int32_t *d_ng_loc = nullptr;         // [slot] position of the slot's column in its block's union
   nesa::cplxf *d_ng_val = nullptr;     // [slot][4] the four rows' values at that column
   int32_t *d_ng_row = nullptr;         // [n_group][4] ABI row of each group member, -1 past the end
+  int64_t *d_ng_cbp = nullptr;         // [n_group] start of each group's chunk boundaries in d_ng_cb
+  int32_t *d_ng_cb = nullptr;          // per group and chunk of 32 union positions: first slot (relative)
   int64_t *d_nb_ptr = nullptr;         // [n_block + 1] start of each block's union in d_nb_col
   int32_t *d_nb_col = nullptr;         // internal columns of the blocks' unions, ascending per block
   int32_t *d_vc_int = nullptr;         // [ncol] internal index of each V column's RWG function

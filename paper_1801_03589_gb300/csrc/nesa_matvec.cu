@@ -667,19 +667,27 @@ __global__ void __launch_bounds__(256) k_near_receive_v(cplx *__restrict__ y, co
 //   R[g][r] = sum_{ch,i} gamma_ch V[g][ch][i] o_b[r][ch][i]       (Eq. 14, U = V^T)
 // for the leaf's V columns g (an RWG function has one column per leaf that holds one of
 // its triangles; k_near_group adds its columns up).  V and o go through shared memory in
-// chunks of RC_KC of the 4Q values: V as [column][k] (every lane of a warp reads the
-// same two values with one 16-byte load), o as [k][right-hand side] with rows padded to
-// 64 + 2 values (lane l reads right-hand sides 2l and 2l + 1 with one 16-byte load).
-// Thread (warp w, lane l) owns right-hand sides r0 + 2l, r0 + 2l + 1 and the columns
-// w, w + 8, ... of a block of RC_COLS (only those the leaf has): per pair of k values,
-// two o loads and one V load per column feed 16 FMAs per column.  FP32 sums in the
-// order k = 0 .. 4Q-1.
+// stages of RC_COLS columns x RC_KC of the 4Q values, copied asynchronously with the next
+// stage in flight while this one is used: V as [column][k] (every lane of a warp reads
+// the same two values with one 16-byte load), o as [k][right-hand side] with rows padded
+// to 64 + 2 values (lane l reads right-hand sides 2l and 2l + 1 with one 16-byte load;
+// gamma is applied to these o values).  Thread (warp w, lane l) owns right-hand sides
+// r0 + 2l, r0 + 2l + 1 and the columns w, w + 8, ... of a block of RC_COLS (only those
+// the leaf has): per pair of k values, two o loads and one V load per column feed 16
+// FMAs per column.  FP32 sums in the order k = 0 .. 4Q-1.
 constexpr int RC_KC = 32, RC_COLS = 64, RC_RHS = 64, RC_OPAD = RC_RHS + 2;
+constexpr int RC_VS = RC_COLS * RC_KC, RC_OS = RC_KC * RC_OPAD;  // complex64 values per stage
+constexpr int RC_SMEM = 2 * (RC_VS + RC_OS) * 8;
+__device__ __forceinline__ void rc_cp16(uint32_t dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void rc_cp8(uint32_t dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
 __global__ void __launch_bounds__(256) k_receive_leaf(cplxf *__restrict__ R, const cplxf *__restrict__ V,
                                                       const cplxf *__restrict__ oL, const int32_t *__restrict__ vc_ptr,
                                                       int nrhs, int q, float mk2) {
-  __shared__ __align__(16) cplxf Vs[RC_COLS][RC_KC];
-  __shared__ __align__(16) cplxf Os[RC_KC][RC_OPAD];
+  extern __shared__ __align__(16) cplxf rsm[];  // [2][RC_VS + RC_OS]
   const int64_t b = blockIdx.x;
   const int r0 = blockIdx.y * RC_RHS;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -687,55 +695,75 @@ __global__ void __launch_bounds__(256) k_receive_leaf(cplxf *__restrict__ R, con
   const int q4 = 4 * q, q3 = 3 * q;
   const cplxf *ob = oL + b * nrhs * (int64_t)q4;  // o_b[r][ch][i] at ob + r * 4Q + ch * Q + i
   const int ra = r0 + 2 * lane;                   // this lane's right-hand sides ra, ra + 1
-  for (int c0 = 0; c0 < ns; c0 += RC_COLS) {
+  const int nkc = (q4 + RC_KC - 1) / RC_KC, ncb = (ns + RC_COLS - 1) / RC_COLS, nst = ncb * nkc;
+  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(rsm);
+  auto stage = [&](int st) {  // stage st (column block st / nkc, k chunk st % nkc) into buffer st & 1
+    const int c0 = (st / nkc) * RC_COLS, k0 = (st % nkc) * RC_KC;
+    const int nc = min(RC_COLS, ns - c0), kn = min(RC_KC, q4 - k0);  // kn even (q4 and k0 are)
+    cplxf *Vs = rsm + (st & 1) * (RC_VS + RC_OS), *Os = Vs + RC_VS;
+    for (int t = threadIdx.x; t < RC_COLS * (RC_KC / 2); t += blockDim.x) {
+      const int cc = t / (RC_KC / 2), pc = t % (RC_KC / 2);
+      cplxf *dst = Vs + cc * RC_KC + 2 * pc;
+      if (cc < nc && 2 * pc < kn)
+        rc_cp16(sbase + (uint32_t)((dst - rsm) * 8), V + (int64_t)(g0 + c0 + cc) * q4 + k0 + 2 * pc);
+      else
+        *(float4 *)dst = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+    for (int t = threadIdx.x; t < RC_RHS * RC_KC; t += blockDim.x) {  // coalesced along k
+      const int rr = t / RC_KC, kk = t % RC_KC;
+      cplxf *dst = Os + kk * RC_OPAD + rr;
+      if (r0 + rr < nrhs && kk < kn)
+        rc_cp8(sbase + (uint32_t)((dst - rsm) * 8), ob + (int64_t)(r0 + rr) * q4 + k0 + kk);
+      else
+        *dst = make_float2(0.0f, 0.0f);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  cplxf acc[RC_COLS / 8][2];
+  if (nst > 0) stage(0);
+  for (int st = 0; st < nst; ++st) {
+    if (st + 1 < nst) {
+      stage(st + 1);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+    __syncthreads();
+    const int cb = st / nkc, kc = st % nkc;
+    const int c0 = cb * RC_COLS, k0 = kc * RC_KC;
     const int nc = min(RC_COLS, ns - c0);
     const int jn = nc > warp ? (nc - warp + 7) / 8 : 0;  // this warp's columns in the block
-    cplxf acc[RC_COLS / 8][2];
+    if (kc == 0)
 #pragma unroll
-    for (int j = 0; j < RC_COLS / 8; ++j) acc[j][0] = acc[j][1] = make_float2(0.0f, 0.0f);
-    for (int k0 = 0; k0 < q4; k0 += RC_KC) {
-      const int kn = min(RC_KC, q4 - k0);
-      __syncthreads();
-      for (int t = threadIdx.x; t < RC_COLS * RC_KC; t += blockDim.x) {
-        const int cc = t / RC_KC, kk = t % RC_KC;
-        cplxf v = make_float2(0.0f, 0.0f);
-        if (cc < nc && kk < kn) {
-          v = V[(int64_t)(g0 + c0 + cc) * q4 + k0 + kk];
-          const float gm = k0 + kk < q3 ? 1.0f : mk2;
-          v = make_float2(gm * v.x, gm * v.y);
-        }
-        Vs[cc][kk] = v;
-      }
-      for (int t = threadIdx.x; t < RC_RHS * RC_KC; t += blockDim.x) {  // coalesced along k
-        const int rr = t / RC_KC, kk = t % RC_KC;
-        Os[kk][rr] = r0 + rr < nrhs && kk < kn ? ob[(int64_t)(r0 + rr) * q4 + k0 + kk] : make_float2(0.0f, 0.0f);
-      }
-      __syncthreads();
+      for (int j = 0; j < RC_COLS / 8; ++j) acc[j][0] = acc[j][1] = make_float2(0.0f, 0.0f);
+    const cplxf *Vs = rsm + (st & 1) * (RC_VS + RC_OS), *Os = Vs + RC_VS;
 #pragma unroll 2
-      for (int kk = 0; kk < RC_KC; kk += 2) {  // zeros past kn
-        const float4 oa = *(const float4 *)&Os[kk][2 * lane];
-        const float4 obk = *(const float4 *)&Os[kk + 1][2 * lane];
-        const cplxf oa0 = make_float2(oa.x, oa.y), oa1 = make_float2(oa.z, oa.w);
-        const cplxf ob0 = make_float2(obk.x, obk.y), ob1 = make_float2(obk.z, obk.w);
+    for (int kk = 0; kk < RC_KC; kk += 2) {  // zeros past kn
+      const float ga = k0 + kk < q3 ? 1.0f : mk2, gb = k0 + kk + 1 < q3 ? 1.0f : mk2;
+      const float4 oa = *(const float4 *)&Os[kk * RC_OPAD + 2 * lane];
+      const float4 obk = *(const float4 *)&Os[(kk + 1) * RC_OPAD + 2 * lane];
+      const cplxf oa0 = make_float2(ga * oa.x, ga * oa.y), oa1 = make_float2(ga * oa.z, ga * oa.w);
+      const cplxf ob0 = make_float2(gb * obk.x, gb * obk.y), ob1 = make_float2(gb * obk.z, gb * obk.w);
 #pragma unroll
-        for (int j = 0; j < RC_COLS / 8; ++j)
-          if (j < jn) {
-            const float4 v2 = *(const float4 *)&Vs[warp + 8 * j][kk];
-            const cplxf va = make_float2(v2.x, v2.y), vb = make_float2(v2.z, v2.w);
-            cfma(acc[j][0], va, oa0);
-            cfma(acc[j][1], va, oa1);
-            cfma(acc[j][0], vb, ob0);
-            cfma(acc[j][1], vb, ob1);
-          }
-      }
+      for (int j = 0; j < RC_COLS / 8; ++j)
+        if (j < jn) {
+          const float4 v2 = *(const float4 *)&Vs[(warp + 8 * j) * RC_KC + kk];
+          const cplxf va = make_float2(v2.x, v2.y), vb = make_float2(v2.z, v2.w);
+          cfma(acc[j][0], va, oa0);
+          cfma(acc[j][1], va, oa1);
+          cfma(acc[j][0], vb, ob0);
+          cfma(acc[j][1], vb, ob1);
+        }
     }
+    if (kc == nkc - 1)
 #pragma unroll
-    for (int j = 0; j < RC_COLS / 8; ++j)
-      if (j < jn) {
-        cplxf *Rg = R + (int64_t)(g0 + c0 + warp + 8 * j) * nrhs;
-        if (ra < nrhs) Rg[ra] = acc[j][0];
-        if (ra + 1 < nrhs) Rg[ra + 1] = acc[j][1];
-      }
+      for (int j = 0; j < RC_COLS / 8; ++j)
+        if (j < jn) {
+          cplxf *Rg = R + (int64_t)(g0 + c0 + warp + 8 * j) * nrhs;
+          if (ra < nrhs) Rg[ra] = acc[j][0];
+          if (ra + 1 < nrhs) Rg[ra + 1] = acc[j][1];
+        }
+    __syncthreads();  // every warp is done with this buffer before it is refilled
   }
 }
 
@@ -744,26 +772,23 @@ __global__ void __launch_bounds__(256) k_receive_leaf(cplxf *__restrict__ R, con
 // of the four rows' columns (a row's value is 0 at a column it lacks), and the groups in
 // blocks of eight (one CTA, one warp per group) whose x columns are the union of the
 // eight groups' columns.  Lane l of a warp owns right-hand sides r0 + 2l and r0 + 2l + 1
-// of the CTA's 64.  The CTA copies the x rows of its column union into shared memory
-// NS_CH columns at a time (512 contiguous bytes per column, 16-byte asynchronous
-// copies, the next chunk in flight while this one is used), so every x value crosses
-// from L2 once per CTA instead of once per warp, and a warp never waits on a
-// column-then-x chain of global loads.  For each of its slots in the chunk a lane reads
-// its two x values with one conflict-free 16-byte shared load and the four values with
-// two broadcast loads, and does 32 FP32 FMAs.  A group stores its slots' positions in
-// the CTA's union (ascending), so the slots of a chunk are a prefix of the remaining
-// ones: 32 positions are read at a time and a ballot counts those in the chunk.  FP32
-// sums in slot order, converted to FP64; the far part adds the reception values R of
-// the row's V columns (k_receive_leaf) times -i eta k.
-constexpr int NG_ROWS = 4, NS_GROUPS = 8, NS_CH = 64;
-constexpr int NS_SMEM = 2 * NS_CH * 32 * 16;  // two chunks of NS_CH columns x 64 right-hand sides
+// of the CTA's 64.  The CTA works through its column union NS_CH columns at a time; for
+// each chunk it copies into shared memory, asynchronously and one chunk ahead of use,
+// the x rows of the chunk's columns (512 contiguous bytes per column) and, per warp, the
+// values and the in-chunk positions of its group's slots in the chunk (their ranges per
+// chunk are precomputed).  Every operand of the inner loop then comes from shared
+// memory: per slot a broadcast position, a conflict-free 16-byte x load, two broadcast
+// 16-byte value loads and 32 FP32 FMAs.  FP32 sums in slot order, converted to FP64;
+// the far part adds the reception values R of the row's V columns (k_receive_leaf)
+// times -i eta k.
+constexpr int NG_ROWS = 4, NS_GROUPS = 8, NS_CH = 32, NS_VS = NS_CH + 2;
+constexpr int NS_XB = NS_CH * 32 * 16, NS_VB = NS_GROUPS * NS_VS * 32, NS_LB = NS_GROUPS * NS_VS * 4;
+constexpr int NS_SMEM = 2 * (NS_XB + NS_VB + NS_LB);  // two stages: x, values, positions
 __device__ __forceinline__ void ns_cp16(uint32_t dst, const void *src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
-__device__ __forceinline__ void ns_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void ns_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+__device__ __forceinline__ void ns_cp4(uint32_t dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
 }
 __global__ void __launch_bounds__(256) k_near_group(cplx *__restrict__ y, const cplxf *__restrict__ xw, int ldx,
                                                     int64_t n, int nrhs, int64_t n_group,
@@ -771,12 +796,14 @@ __global__ void __launch_bounds__(256) k_near_group(cplx *__restrict__ y, const 
                                                     const int32_t *__restrict__ g_loc,
                                                     const float4 *__restrict__ g_val,
                                                     const int32_t *__restrict__ g_row,
+                                                    const int64_t *__restrict__ g_cbp,
+                                                    const int32_t *__restrict__ g_cb,
                                                     const int64_t *__restrict__ b_ptr,
                                                     const int32_t *__restrict__ b_col,
                                                     const int32_t *__restrict__ rx_ptr,
                                                     const int32_t *__restrict__ rx_col, const cplxf *__restrict__ R,
                                                     double eta_k, int parts) {
-  extern __shared__ __align__(16) float4 xs4[];  // [2][NS_CH][32]: x of 64 right-hand sides per column
+  extern __shared__ __align__(16) unsigned char nsm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t blk = blockIdx.x;
   const int64_t g = blk * NS_GROUPS + warp;
@@ -789,51 +816,67 @@ __global__ void __launch_bounds__(256) k_near_group(cplx *__restrict__ y, const 
   if (parts & NESA_PART_NEAR) {
     const int64_t c0 = b_ptr[blk], nu = b_ptr[blk + 1] - c0;
     const int nch = (int)((nu + NS_CH - 1) / NS_CH);
-    int64_t e = gon ? g_ptr[g] : 0;
-    const int64_t e1 = gon ? g_ptr[g + 1] : 0;
-    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(xs4);
-    auto stage = [&](int c) {  // chunk c into buffer c & 1
+    const int64_t e0 = gon ? g_ptr[g] : 0;
+    const int32_t *cb = g_cb + (gon ? g_cbp[g] : 0);  // slot offsets of the chunks' starts, nch + 1
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(nsm);
+    // stage k: buffer k & 1 holds x at [buf * NS_XB], values at 2 NS_XB + buf * NS_VB,
+    // positions at 2 (NS_XB + NS_VB) + buf * NS_LB
+    int cnt0 = 0, cnt1 = 0;                          // slots of this warp's group in buffers 0 and 1
+    int32_t nb_c = gon ? cb[0] : 0, nb_n = (gon && nch >= 1) ? cb[1] : 0;  // next chunk to stage
+    auto stage = [&](int c) {
+      const int buf = c & 1;
       for (int t = threadIdx.x; t < NS_CH * 32; t += blockDim.x) {
         const int j = t >> 5, pc = t & 31;  // column j of the chunk, right-hand sides rb + 2 pc, + 1
         const int64_t jj = (int64_t)c * NS_CH + j;
-        float4 *dst = xs4 + ((c & 1) * NS_CH + j) * 32 + pc;
+        const uint32_t off = (uint32_t)(buf * NS_XB + (j * 32 + pc) * 16);
         if (jj < nu && rb + 2 * pc < ldx)
-          ns_cp16(sbase + (uint32_t)((char *)dst - (char *)xs4), xw + (int64_t)b_col[c0 + jj] * ldx + rb + 2 * pc);
+          ns_cp16(sbase + off, xw + (int64_t)b_col[c0 + jj] * ldx + rb + 2 * pc);
         else
-          *dst = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+          *(float4 *)(nsm + off) = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
       }
-      ns_commit();
+      if (gon) {
+        const int cnt = nb_n - nb_c;  // at most NS_CH + 1
+        const int64_t sl = e0 + nb_c;
+        const uint32_t voff = (uint32_t)(2 * NS_XB + buf * NS_VB + warp * NS_VS * 32);
+        const uint32_t loff = (uint32_t)(2 * (NS_XB + NS_VB) + buf * NS_LB + warp * NS_VS * 4);
+        for (int t = lane; t < 2 * cnt; t += 32) ns_cp16(sbase + voff + t * 16, g_val + 2 * sl + t);
+        for (int t = lane; t < cnt; t += 32) ns_cp4(sbase + loff + t * 4, g_loc + sl + t);
+        if (buf)
+          cnt1 = cnt;
+        else
+          cnt0 = cnt;
+        nb_c = nb_n;
+        nb_n = c + 2 <= nch ? cb[c + 2] : nb_n;  // used by the next stage
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
     };
     if (nch > 0) stage(0);
     for (int c = 0; c < nch; ++c) {
       if (c + 1 < nch) {
         stage(c + 1);
-        ns_wait<1>();
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
       } else {
-        ns_wait<0>();
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
       }
       __syncthreads();
-      const float4 *xb = xs4 + (c & 1) * NS_CH * 32 + lane;
-      const int lim = (c + 1) * NS_CH;
-      while (e < e1) {  // warp-uniform
-        const int32_t lc = e + lane < e1 ? g_loc[e + lane] : 0x7fffffff;
-        const int cnt = __popc(__ballot_sync(0xffffffffu, lc < lim));
-#pragma unroll 4
-        for (int u = 0; u < cnt; ++u) {
-          const int j = __shfl_sync(0xffffffffu, lc, u) - c * NS_CH;
-          const float4 x2 = xb[j * 32];
-          const float4 v0 = g_val[2 * (e + u)], v1 = g_val[2 * (e + u) + 1];
-          const cplxf xa = make_float2(x2.x, x2.y), xb2 = make_float2(x2.z, x2.w);
-          const cplxf va[NG_ROWS] = {make_float2(v0.x, v0.y), make_float2(v0.z, v0.w), make_float2(v1.x, v1.y),
-                                     make_float2(v1.z, v1.w)};
+      const int buf = c & 1;
+      const int cnt = buf ? cnt1 : cnt0;
+      const float4 *xb = (const float4 *)(nsm + buf * NS_XB) + lane;
+      const float4 *vb = (const float4 *)(nsm + 2 * NS_XB + buf * NS_VB + warp * NS_VS * 32);
+      const int32_t *lb = (const int32_t *)(nsm + 2 * (NS_XB + NS_VB) + buf * NS_LB + warp * NS_VS * 4);
+      const int cbase = c * NS_CH;
+#pragma unroll 2
+      for (int u = 0; u < cnt; ++u) {
+        const float4 x2 = xb[(lb[u] - cbase) * 32];
+        const float4 v0 = vb[2 * u], v1 = vb[2 * u + 1];
+        const cplxf xa = make_float2(x2.x, x2.y), xb2 = make_float2(x2.z, x2.w);
+        const cplxf va[NG_ROWS] = {make_float2(v0.x, v0.y), make_float2(v0.z, v0.w), make_float2(v1.x, v1.y),
+                                   make_float2(v1.z, v1.w)};
 #pragma unroll
-          for (int i = 0; i < NG_ROWS; ++i) {
-            cfma(acc[i][0], va[i], xa);
-            cfma(acc[i][1], va[i], xb2);
-          }
+        for (int i = 0; i < NG_ROWS; ++i) {
+          cfma(acc[i][0], va[i], xa);
+          cfma(acc[i][1], va[i], xb2);
         }
-        e += cnt;
-        if (cnt < 32) break;
       }
       __syncthreads();  // every warp is done with this buffer before it is refilled
     }
@@ -1100,14 +1143,14 @@ static void run_product(nesa_ctx *c, const OpView<CT> &op, const cplx *x, cplx *
     if (nrhs >= 32) {  // many right-hand sides: groups of four rows, two right-hand sides per lane
       const int ldx = (nrhs + 1) & ~1;  // xw was made before the far part
       if (parts & NESA_PART_FAR)
-        k_receive_leaf<<<dim3((unsigned)c->nleaf, (unsigned)((nrhs + RC_RHS - 1) / RC_RHS)), 256, 0, st>>>(
+        k_receive_leaf<<<dim3((unsigned)c->nleaf, (unsigned)((nrhs + RC_RHS - 1) / RC_RHS)), 256, RC_SMEM, st>>>(
             c->d_rcv, op.V, op.o[L], c->d_vc_ptr, nrhs, dL.q, (float)(-1.0 / (c->k * c->k)));
       if (c->n_group > 0)
         k_near_group<<<dim3((unsigned)((c->n_group + NS_GROUPS - 1) / NS_GROUPS), (unsigned)((nrhs + 63) / 64)),
                        32 * NS_GROUPS, NS_SMEM, st>>>(y, c->d_xp, ldx, c->n, nrhs, c->n_group, c->d_ng_ptr,
                                                       c->d_ng_loc, (const float4 *)c->d_ng_val, c->d_ng_row,
-                                                      c->d_nb_ptr, c->d_nb_col, c->d_rx_ptr, c->d_rx_col, c->d_rcv,
-                                                      c->eta * c->k, parts);
+                                                      c->d_ng_cbp, c->d_ng_cb, c->d_nb_ptr, c->d_nb_col,
+                                                      c->d_rx_ptr, c->d_rx_col, c->d_rcv, c->eta * c->k, parts);
     } else {
       if (parts & NESA_PART_NEAR) k_perm_x<<<pgrid, 256, 0, st>>>(c->d_xp, x, c->d_perm, c->n, nrhs);
       auto near = nrhs == 1 ? k_near_receive_v<1> : k_near_receive_v<4>;
@@ -1335,6 +1378,34 @@ static void build_near_groups(nesa_ctx *c) {
   run_threads(blocks, nb);
   std::vector<int64_t> bptr(nb + 1, 0);
   for (int64_t b = 0; b < nb; ++b) bptr[b + 1] = bptr[b] + (int64_t)bcol[b].size();
+  // per group, for each chunk c of NS_CH union positions of its block, the first slot
+  // (relative to the group's first) whose position is >= c NS_CH; the last entry is the
+  // group's slot count
+  std::vector<int64_t> cbp(std::max<int64_t>(ng, 1), 0);
+  for (int64_t g = 0, at = 0; g < ng; ++g) {
+    cbp[g] = at;
+    const int64_t b = g / NS_GROUPS;
+    at += (bptr[b + 1] - bptr[b] + NS_CH - 1) / NS_CH + 1;
+    if (g + 1 == ng) cbp.push_back(at);
+  }
+  std::vector<int32_t> cbv(std::max<int64_t>(ng > 0 ? cbp[ng] : 1, 1), 0);
+  auto bounds = [&](int64_t ga, int64_t gb) {
+    for (int64_t g = ga; g < gb; ++g) {
+      const int64_t b = g / NS_GROUPS, nch = (bptr[b + 1] - bptr[b] + NS_CH - 1) / NS_CH;
+      int64_t sl = gptr[g];
+      for (int64_t c = 0; c <= nch; ++c) {
+        while (sl < gptr[g + 1] && gloc[sl] < c * NS_CH) ++sl;
+        cbv[cbp[g] + c] = (int32_t)(sl - gptr[g]);
+      }
+      cbv[cbp[g] + nch] = (int32_t)(gptr[g + 1] - gptr[g]);
+    }
+  };
+  run_threads(bounds, ng);
+  c->d_ng_cbp = (int64_t *)dalloc(c, sizeof(int64_t) * std::max<int64_t>(ng, 1));
+  c->d_ng_cb = (int32_t *)dalloc(c, sizeof(int32_t) * cbv.size());
+  check_cuda(cudaMemcpy(c->d_ng_cbp, cbp.data(), sizeof(int64_t) * std::max<int64_t>(ng, 1), cudaMemcpyHostToDevice),
+             "near groups");
+  check_cuda(cudaMemcpy(c->d_ng_cb, cbv.data(), sizeof(int32_t) * cbv.size(), cudaMemcpyHostToDevice), "near groups");
   std::vector<int32_t> bflat(std::max<int64_t>(bptr[nb], 1));
   for (int64_t b = 0; b < nb; ++b) std::copy(bcol[b].begin(), bcol[b].end(), bflat.begin() + bptr[b]);
   std::vector<std::vector<int32_t>>().swap(bcol);
@@ -1345,6 +1416,8 @@ static void build_near_groups(nesa_ctx *c) {
   check_cuda(cudaMemcpy(c->d_nb_col, bflat.data(), sizeof(int32_t) * bflat.size(), cudaMemcpyHostToDevice),
              "near groups");
   check_cuda(cudaFuncSetAttribute(k_near_group, cudaFuncAttributeMaxDynamicSharedMemorySize, NS_SMEM), "near groups");
+  check_cuda(cudaFuncSetAttribute(k_receive_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize, RC_SMEM),
+             "near groups");
   c->d_ng_ptr = (int64_t *)dalloc(c, sizeof(int64_t) * (ng + 1));
   c->d_ng_loc = (int32_t *)dalloc(c, sizeof(int32_t) * std::max<int64_t>(nslot, 1));
   c->d_ng_row = (int32_t *)dalloc(c, sizeof(int32_t) * std::max<int64_t>(ng * NG_ROWS, 1));
