@@ -894,7 +894,7 @@ def large_solve(name, max_iters, restart, nrhs=0):
 
 
 PROFILE_RUNS = ("fp64_C2", "fp64_C3a", "tensor_C3a_generated", "tensor_C3a_stored", "tensor_C3a_64rhs",
-                "model2d_N1e5_P300_Q100")
+                "batch_C3", "model2d_N1e5_P300_Q100")
 
 
 def profile_run(name):
@@ -908,6 +908,20 @@ def profile_run(name):
         x = torch.from_numpy(random_coefficients(g.n, 1, seed=5)).cuda()
         for _ in range(2):
             g.matvec(x)
+    elif name == "batch_C3":  # the batched sweep: three meshes x 64 RHS, one graph launch per pass
+        members = []
+        for nm in ("C3a", "C3b", "C3c"):
+            cf = get_config(nm)
+            members.append(nesa.Nesa(cf["vertices"], cf["triangles"], cf["k"], leaf_size=cf["leaf_size"],
+                                     n_levels=cf["n_levels"], precision=nesa.MIXED, translate=nesa.TRANSLATE_TENSOR,
+                                     tile_n=128))
+        bx = [torch.from_numpy(random_coefficients(m.n, 64, seed=300 + i)).cuda() for i, m in enumerate(members)]
+        by = [torch.empty_like(v) for v in bx]
+        bt = nesa.Batch(members, bx, by, parts=nesa.PART_ALL | nesa.PART_MIXED)
+        for _ in range(2):
+            bt.launch()
+        torch.cuda.synchronize()
+        bt.close()
     elif name.startswith("tensor_"):
         c = get_config("C3a")
         tables = nesa.TABLES_GENERATED if name.endswith("generated") else nesa.TABLES_STORED
