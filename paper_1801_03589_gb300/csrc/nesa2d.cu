@@ -536,11 +536,11 @@ __global__ void __launch_bounds__(32 * NEAR_WARPS) k2_near(double *__restrict__ 
 
 // Far-field kernels (Eqs. 10-14 in 2D).  Each output block of Q values (a group's
 // equivalent charges or potentials) is a sum of column-major matrix columns times
-// scalars: a CTA owns the block, its 8 warps split the columns of every matrix between
+// scalars: a CTA owns the block, its 16 warps split the columns of every matrix between
 // them, each lane accumulates the rows k0 + lane + 32 rr (FAR_KR rows, chunks of
-// FAR_TROWS rows for larger Q), and the 8 partial sums are added in warp order
+// FAR_TROWS rows for larger Q), and the 16 partial sums are added in warp order
 // (deterministic).  Every column is one coalesced load per row group.
-constexpr int FAR_WARPS = 8, FAR_KR = 4, FAR_TROWS = 32 * FAR_KR;
+constexpr int FAR_WARPS = 16, FAR_KR = 4, FAR_TROWS = 32 * FAR_KR;
 
 __device__ __forceinline__ void far_col(double (&acc)[FAR_KR], const double *__restrict__ col, double xj, int k0,
                                         int q, int lane) {
