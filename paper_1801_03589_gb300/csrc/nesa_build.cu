@@ -610,6 +610,10 @@ static void build_device(nesa_ctx *c, const nesa_params &p) {
                      "zgemm C");
           k_transpose<<<grid_for((int64_t)qp * q, 256), 256, 0, st>>>(dl.Ct + (size_t)oc * qp * q, Cm, qp, q);
         }
+        dl.Cs = (double *)dalloc(c, sizeof(double) * 8 * (size_t)qp * q);
+        dl.Cts = (double *)dalloc(c, sizeof(double) * 8 * (size_t)qp * q);
+        plane_sum(c, dl.Cs, dl.C, 8LL * qp * q);
+        plane_sum(c, dl.Cts, dl.Ct, 8LL * qp * q);
         check_cuda(cudaStreamSynchronize(st), "transfer fill");
       }
     }

@@ -62,6 +62,7 @@ struct DevLevel {
   double *Ds = nullptr;  // [noff][q][q] Re + Im of D (the FP64 product's 3M sums)
   cplx *C = nullptr;   // [8][q_{l-1}][q] column-major (rows: parent's sources)
   cplx *Ct = nullptr;  // [8][q][q_{l-1}] column-major (transpose of C)
+  double *Cs = nullptr, *Cts = nullptr;  // Re + Im of C and Ct (the FP64 product's 3M sums)
   cplx *K = nullptr;   // [q][2q] column-major
   // generated translations (D == nullptr): equivalent points and offsets on the device,
   // and the pairs grouped in chunks of chunk_slots offset slots: chunk c's pairs by

@@ -422,29 +422,82 @@ __global__ void __launch_bounds__(512) k_translate(CT *__restrict__ o, const CT 
   }
 }
 
-// FP64 translation and potential transfer, the translations in the 3M (Gauss) form.
-// For D = A + iB and a source column u + iv,
-//   Re(D x) = A u - B v,   Im(D x) = (A + B)(u + v) - A u - B v,
-// so with the sums S = A + B stored beside D (one FP64 plane per offset) an entry costs
-// three FMAs per channel instead of the four of the direct form, on a kernel bound by
-// the FP64 pipe.  Thread (channel ch, row i) as in k_translate (4Q threads per box, so
-// nearly every lane works at Q = 100); the source columns pass through shared memory as
-// (u, v) and u + v per channel, JC3 columns at a time.  The potential transfer C^T o_P
-// (Eq. 13) keeps the direct form in its own sum.  The three sums run over the columns in
-// order and are combined once at the end; a later chunk of generated offsets adds its
-// result to o.
+// FP64 source transfer, translation and potential transfer with every complex product
+// in the 3M (Gauss) form.  For a matrix M = A + iB and a source column u + iv,
+//   Re(M x) = A u - B v,   Im(M x) = (A + B)(u + v) - A u - B v,
+// so with the sums S = A + B stored beside M (one FP64 plane per matrix, made at build
+// time) an entry costs three FMAs per channel instead of the four of the direct form,
+// on kernels bound by the FP64 pipe.  Thread (channel ch, row i) as in k_translate (4Q
+// threads per box, so nearly every lane works at Q = 100); the source columns pass
+// through shared memory as (u, v) and u + v per channel, JC3 columns at a time.  The
+// three sums per channel run over the columns in order and are combined once at the end.
 constexpr int JC3 = 256;
+constexpr size_t SMEM3 = (sizeof(double2) + sizeof(double)) * 4 * JC3;
+// (p0, p1, p2) += (A u, B v, S (u + v)) over the kdim columns of M (column j at M + j ld,
+// M and MS already offset to this thread's row) and the 4 channels of src (stride kdim)
+__device__ __forceinline__ void mv3_chunked(double &p0, double &p1, double &p2, unsigned char *smem,
+                                            const double2 *__restrict__ src, const double2 *__restrict__ M,
+                                            const double *__restrict__ MS, int64_t ld, int kdim, int ch, bool active) {
+  double2 *col = (double2 *)smem;                           // [4][JC3] (u, v)
+  double *colw = (double *)(smem + sizeof(double2) * 4 * JC3);  // [4][JC3] u + v
+  for (int j0 = 0; j0 < kdim; j0 += JC3) {
+    const int len = min(JC3, kdim - j0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < 4 * len; t += blockDim.x) {
+      const double2 v = src[(int64_t)(t / len) * kdim + j0 + t % len];
+      col[t] = v;
+      colw[t] = v.x + v.y;
+    }
+    __syncthreads();
+    if (!active) continue;
+    const double2 *cs = col + ch * len;
+    const double *cw = colw + ch * len;
+    const double2 *Mj = M + (int64_t)j0 * ld;
+    const double *Sj = MS + (int64_t)j0 * ld;
+#pragma unroll 4
+    for (int j = 0; j < len; ++j) {
+      const double2 m = Mj[(int64_t)j * ld];
+      const double sm = Sj[(int64_t)j * ld];
+      const double2 x = cs[j];
+      p0 = fma(m.x, x.x, p0);
+      p1 = fma(m.y, x.y, p1);
+      p2 = fma(sm, cw[j], p2);
+    }
+  }
+}
+
+// Eq. 11: parent P at level l-1 (rows qp) gathers its children at level l (rows q)
+__global__ void __launch_bounds__(512) k_upward64(double2 *__restrict__ sp, const double2 *__restrict__ sc,
+                                                  const double2 *__restrict__ C, const double *__restrict__ CS,
+                                                  const int32_t *__restrict__ child_ptr,
+                                                  const int32_t *__restrict__ octant, int nrhs, int qp, int q, int tr) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int32_t P = blockIdx.x;
+  const int ch = threadIdx.x / tr;
+  const int i = blockIdx.y * tr + threadIdx.x % tr;
+  const bool active = ch < 4 && i < qp;
+  const int32_t c0 = child_ptr[P], c1 = child_ptr[P + 1];
+  for (int r = 0; r < nrhs; ++r) {
+    double p0 = 0.0, p1 = 0.0, p2 = 0.0;
+    for (int32_t cb = c0; cb < c1; ++cb)
+      mv3_chunked(p0, p1, p2, smem_raw, sc + ((int64_t)cb * 4 * nrhs + 4 * r) * q,
+                  C + (int64_t)octant[cb] * qp * q + i, CS + (int64_t)octant[cb] * qp * q + i, qp, q, ch, active);
+    if (active) sp[((int64_t)P * 4 * nrhs + 4 * r + ch) * qp + i] = make_double2(p0 - p1, p2 - p0 - p1);
+  }
+}
+
+// Eqs. 13 and 12: o_a = C^T o_P + sum over the interaction list of D(offset) s_b; a later
+// chunk of generated offsets adds its result to o
 __global__ void __launch_bounds__(512) k_translate64(double2 *__restrict__ o, const double2 *__restrict__ s,
                                                      const double2 *__restrict__ D, const double *__restrict__ DS,
                                                      const int32_t *__restrict__ il_ptr,
                                                      const int32_t *__restrict__ il_src,
                                                      const int32_t *__restrict__ il_slot, const double2 *__restrict__ op,
-                                                     const double2 *__restrict__ Ct, const int32_t *__restrict__ parent,
+                                                     const double2 *__restrict__ Ct, const double *__restrict__ CtS,
+                                                     const int32_t *__restrict__ parent,
                                                      const int32_t *__restrict__ octant, int nrhs, int q, int qp, int tr,
                                                      int accum) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double2 *col = (double2 *)smem_raw;                 // [4][JC3] (u, v)
-  double *colw = (double *)(smem_raw + sizeof(double2) * 4 * JC3);  // [4][JC3] u + v
   const int32_t a = blockIdx.x;
   const int ch = threadIdx.x / tr;
   const int i = blockIdx.y * tr + threadIdx.x % tr;
@@ -452,43 +505,16 @@ __global__ void __launch_bounds__(512) k_translate64(double2 *__restrict__ o, co
   const int32_t e0 = il_ptr[a], e1 = il_ptr[a + 1];
   if (accum && e0 == e1) return;  // a later chunk of offsets without pairs of this box
   for (int r = 0; r < nrhs; ++r) {
-    double2 acc = make_double2(0.0, 0.0);
+    double p0 = 0.0, p1 = 0.0, p2 = 0.0;
     if (op)  // potential transfer from the parent (Eq. 13): o_a += C^T o_P
-      matvec_chunked(acc, col, op + ((int64_t)parent[a] * 4 * nrhs + 4 * r) * qp,
-                     Ct + (int64_t)octant[a] * q * qp + i, q, qp, ch, active);
-    double p0 = 0.0, p1 = 0.0, p2 = 0.0;  // A u, B v, S (u + v)
-    for (int32_t e = e0; e < e1; ++e) {  // translations (Eq. 12)
-      const double2 *src = s + ((int64_t)il_src[e] * 4 * nrhs + 4 * r) * q;
-      const double2 *M = D + (int64_t)il_slot[e] * q * q + i;
-      const double *MS = DS + (int64_t)il_slot[e] * q * q + i;
-      for (int j0 = 0; j0 < q; j0 += JC3) {
-        const int len = min(JC3, q - j0);
-        __syncthreads();
-        for (int t = threadIdx.x; t < 4 * len; t += blockDim.x) {
-          const double2 v = src[(int64_t)(t / len) * q + j0 + t % len];
-          col[t] = v;
-          colw[t] = v.x + v.y;
-        }
-        __syncthreads();
-        if (!active) continue;
-        const double2 *cs = col + ch * len;
-        const double *cw = colw + ch * len;
-        const double2 *Mj = M + (int64_t)j0 * q;
-        const double *Sj = MS + (int64_t)j0 * q;
-#pragma unroll 4
-        for (int j = 0; j < len; ++j) {
-          const double2 m = Mj[(int64_t)j * q];
-          const double sm = Sj[(int64_t)j * q];
-          const double2 x = cs[j];
-          p0 = fma(m.x, x.x, p0);
-          p1 = fma(m.y, x.y, p1);
-          p2 = fma(sm, cw[j], p2);
-        }
-      }
-    }
+      mv3_chunked(p0, p1, p2, smem_raw, op + ((int64_t)parent[a] * 4 * nrhs + 4 * r) * qp,
+                  Ct + (int64_t)octant[a] * q * qp + i, CtS + (int64_t)octant[a] * q * qp + i, q, qp, ch, active);
+    for (int32_t e = e0; e < e1; ++e)  // translations (Eq. 12)
+      mv3_chunked(p0, p1, p2, smem_raw, s + ((int64_t)il_src[e] * 4 * nrhs + 4 * r) * q,
+                  D + (int64_t)il_slot[e] * q * q + i, DS + (int64_t)il_slot[e] * q * q + i, q, q, ch, active);
     if (active) {
       double2 *dst = o + ((int64_t)a * 4 * nrhs + 4 * r + ch) * q + i;
-      double2 v = make_double2(acc.x + (p0 - p1), acc.y + (p2 - p0 - p1));
+      double2 v = make_double2(p0 - p1, p2 - p0 - p1);
       if (accum) {  // earlier chunks
         const double2 w = *dst;
         v = make_double2(w.x + v.x, w.y + v.y);
@@ -1075,9 +1101,13 @@ static void run_product(nesa_ctx *c, const OpView<CT> &op, const cplx *x, cplx *
           continue;
         }
       }
-      k_upward<CT><<<dim3((unsigned)p.nbox, t.ntile), t.threads, smem, st>>>(op.s[l - 1], op.s[l], op.C[l],
-                                                                             p.child_ptr, d.octant, nrhs, p.q, d.q,
-                                                                             t.tr);
+      if constexpr (std::is_same<CT, cplx>::value)  // FP64: the 3M form
+        k_upward64<<<dim3((unsigned)p.nbox, t.ntile), t.threads, SMEM3, st>>>(
+            op.s[l - 1], op.s[l], op.C[l], d.Cs, p.child_ptr, d.octant, nrhs, p.q, d.q, t.tr);
+      else
+        k_upward<CT><<<dim3((unsigned)p.nbox, t.ntile), t.threads, smem, st>>>(op.s[l - 1], op.s[l], op.C[l],
+                                                                               p.child_ptr, d.octant, nrhs, p.q, d.q,
+                                                                               t.tr);
     }
     for (int l = l0; l <= L; ++l) {  // translation and potential transfer
       DevLevel &d = c->lev[l];
@@ -1089,16 +1119,15 @@ static void run_product(nesa_ctx *c, const OpView<CT> &op, const cplx *x, cplx *
       double by = B * ((double)d.noff * d.q * d.q + (down ? 8.0 * d.q * qp : 0.0) +
                        4.0 * nrhs * (2.0 * d.nbox * d.q + (down ? (double)c->lev[l - 1].nbox * qp : 0.0)));
       StageScope sc(c, 2, fl, by);
-      // FP64: k_translate64 (3M form with the stored sums S); complex64 (the CUDA-core
+      // FP64: k_translate64 (3M form with the stored sums); complex64 (the CUDA-core
       // engine of the mixed product): k_translate
       auto translate = [&](const CT *Dm, const double *DSm, const int32_t *ptr, const int32_t *src,
                            const int32_t *slot, bool with_parent, int accum) {
         if constexpr (std::is_same<CT, cplx>::value) {
-          const size_t smem3 = std::max(sizeof(double2) * 4 * (size_t)std::min(JC, qp),
-                                        (sizeof(double2) + sizeof(double)) * 4 * (size_t)JC3);
-          k_translate64<<<dim3((unsigned)d.nbox, t.ntile), t.threads, smem3, st>>>(
+          k_translate64<<<dim3((unsigned)d.nbox, t.ntile), t.threads, SMEM3, st>>>(
               op.o[l], op.s[l], Dm, DSm, ptr, src, slot, with_parent ? op.o[l - 1] : nullptr,
-              with_parent ? op.Ct[l] : nullptr, d.parent, d.octant, nrhs, d.q, qp, t.tr, accum);
+              with_parent ? op.Ct[l] : nullptr, with_parent ? d.Cts : nullptr, d.parent, d.octant, nrhs, d.q, qp,
+              t.tr, accum);
         } else {
           k_translate<CT><<<dim3((unsigned)d.nbox, t.ntile), t.threads, smem, st>>>(
               op.o[l], op.s[l], Dm, ptr, src, slot, with_parent ? op.o[l - 1] : nullptr,
