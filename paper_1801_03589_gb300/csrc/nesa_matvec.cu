@@ -103,12 +103,21 @@ __device__ __forceinline__ float2 from64<float2>(double2 v) {
 struct Tiling {
   int ntile, tr, threads;
 };
-static Tiling tiling(int q) {
-  const int maxt = 512;
+static Tiling tiling(int q, int maxt = 512) {
   int ntile = (4 * q + maxt - 1) / maxt;
   int tr = (q + ntile - 1) / ntile;
   int threads = ((4 * tr + 31) / 32) * 32;
   return {ntile, tr, threads};
+}
+// Row tiling of the FP64 transfers and translations: smaller tiles where a level has
+// few boxes, so that the grid holds at least four CTAs per SM (152 SMs); every tile
+// stages the whole source column, which costs little against its Q-long row sums.
+static Tiling tiling_fp64(int q, int64_t nbox) {
+  for (int maxt : {512, 256}) {
+    const Tiling t = tiling(q, maxt);
+    if (nbox * t.ntile >= 4 * 152) return t;
+  }
+  return tiling(q, 128);
 }
 
 // Source columns pass through shared memory in chunks of JC values per channel, so any
@@ -1101,10 +1110,11 @@ static void run_product(nesa_ctx *c, const OpView<CT> &op, const cplx *x, cplx *
           continue;
         }
       }
-      if constexpr (std::is_same<CT, cplx>::value)  // FP64: the 3M form
-        k_upward64<<<dim3((unsigned)p.nbox, t.ntile), t.threads, SMEM3, st>>>(
-            op.s[l - 1], op.s[l], op.C[l], d.Cs, p.child_ptr, d.octant, nrhs, p.q, d.q, t.tr);
-      else
+      if constexpr (std::is_same<CT, cplx>::value) {  // FP64: the 3M form
+        const Tiling t3 = tiling_fp64(p.q, p.nbox);
+        k_upward64<<<dim3((unsigned)p.nbox, t3.ntile), t3.threads, SMEM3, st>>>(
+            op.s[l - 1], op.s[l], op.C[l], d.Cs, p.child_ptr, d.octant, nrhs, p.q, d.q, t3.tr);
+      } else
         k_upward<CT><<<dim3((unsigned)p.nbox, t.ntile), t.threads, smem, st>>>(op.s[l - 1], op.s[l], op.C[l],
                                                                                p.child_ptr, d.octant, nrhs, p.q, d.q,
                                                                                t.tr);
@@ -1124,10 +1134,11 @@ static void run_product(nesa_ctx *c, const OpView<CT> &op, const cplx *x, cplx *
       auto translate = [&](const CT *Dm, const double *DSm, const int32_t *ptr, const int32_t *src,
                            const int32_t *slot, bool with_parent, int accum) {
         if constexpr (std::is_same<CT, cplx>::value) {
-          k_translate64<<<dim3((unsigned)d.nbox, t.ntile), t.threads, SMEM3, st>>>(
+          const Tiling t3 = tiling_fp64(d.q, d.nbox);
+          k_translate64<<<dim3((unsigned)d.nbox, t3.ntile), t3.threads, SMEM3, st>>>(
               op.o[l], op.s[l], Dm, DSm, ptr, src, slot, with_parent ? op.o[l - 1] : nullptr,
               with_parent ? op.Ct[l] : nullptr, with_parent ? d.Cts : nullptr, d.parent, d.octant, nrhs, d.q, qp,
-              t.tr, accum);
+              t3.tr, accum);
         } else {
           k_translate<CT><<<dim3((unsigned)d.nbox, t.ntile), t.threads, smem, st>>>(
               op.o[l], op.s[l], Dm, ptr, src, slot, with_parent ? op.o[l - 1] : nullptr,
