@@ -53,7 +53,7 @@ GEMM_DRAM_BYTES_C2 = 1.5083e9
 # DRAM traffic of the FP64 translation launches (k_translate64) of one product of
 # the r = 3 sphere (ncu: dram__bytes_read.sum + dram__bytes_write.sum of the 4 launches of one
 # product, captured on the current kernel with `--profile-run fp64_C2`)
-K_TRANSLATE64_DRAM_BYTES_C2 = 22.5584e9
+K_TRANSLATE64_DRAM_BYTES_C2 = 21.7700e9
 SPEC = ("PEC sphere r=3 wavelengths, icosphere subdiv 6 (81,920 triangles, 122,880 RWG), "
         "6-level octree, leaf 0.25 wavelength, 1 RHS")
 
