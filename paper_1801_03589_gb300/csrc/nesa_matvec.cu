@@ -67,8 +67,25 @@ int ensure_workspace(nesa_ctx *c, int nrhs) {
 
 static void build_near_groups(nesa_ctx *c);
 
+static void free_near_groups(nesa_ctx *c) {
+  for (void **p : {(void **)&c->d_ng_ptr, (void **)&c->d_ng_loc, (void **)&c->d_ng_val, (void **)&c->d_ng_row,
+                   (void **)&c->d_ng_cbp, (void **)&c->d_ng_cb, (void **)&c->d_nb_ptr, (void **)&c->d_nb_col,
+                   (void **)&c->d_vc_int}) {
+    dfree(c, *p);
+    *p = nullptr;
+  }
+  c->n_group = 0;
+}
+
 static void ensure_workspace32(nesa_ctx *c, int nrhs) {
-  if (nrhs >= 32 && !c->d_ng_ptr) build_near_groups(c);
+  if (nrhs >= 32 && c->n_group == 0 && c->n > 0) {  // n_group is set last: a failed build leaves it 0
+    try {
+      build_near_groups(c);
+    } catch (...) {
+      free_near_groups(c);
+      throw;
+    }
+  }
   if (nrhs <= c->nrhs_cap32) return;
   dfree(c, c->d_xp);
   dfree(c, c->d_rcv);
