@@ -66,6 +66,9 @@ int ensure_workspace(nesa_ctx *c, int nrhs) {
 }
 
 static void build_near_groups(nesa_ctx *c);
+// from this many right-hand sides the mixed product's near field and reception run in
+// the grouped and per-leaf forms (k_near_group, k_receive_leaf; 16 per CTA below 32)
+constexpr int WIDE_MIN_RHS = 16;
 
 static void free_near_groups(nesa_ctx *c) {
   for (void **p : {(void **)&c->d_ng_ptr, (void **)&c->d_ng_loc, (void **)&c->d_ng_val, (void **)&c->d_ng_row,
@@ -78,7 +81,7 @@ static void free_near_groups(nesa_ctx *c) {
 }
 
 static void ensure_workspace32(nesa_ctx *c, int nrhs) {
-  if (nrhs >= 32 && c->n_group == 0 && c->n > 0) {  // n_group is set last: a failed build leaves it 0
+  if (nrhs >= WIDE_MIN_RHS && c->n_group == 0 && c->n > 0) {  // n_group is set last: a failed build leaves it 0
     try {
       build_near_groups(c);
     } catch (...) {
@@ -92,7 +95,7 @@ static void ensure_workspace32(nesa_ctx *c, int nrhs) {
   c->d_rcv = nullptr;
   // (nrhs + 1) & ~1: the row stride of the wide layout
   c->d_xp = (cplxf *)dalloc(c, sizeof(cplxf) * (size_t)std::max<int64_t>(1, c->n * ((nrhs + 1) & ~1)));
-  if (nrhs >= 32) c->d_rcv = (cplxf *)dalloc(c, sizeof(cplxf) * (size_t)c->info.v_columns * nrhs);
+  if (nrhs >= WIDE_MIN_RHS) c->d_rcv = (cplxf *)dalloc(c, sizeof(cplxf) * (size_t)c->info.v_columns * nrhs);
   for (int l = c->l0; l <= c->L; ++l) {
     DevLevel &d = c->lev[l];
     dfree(c, d.s32);
@@ -714,56 +717,68 @@ __global__ void __launch_bounds__(256) k_near_receive_v(cplx *__restrict__ y, co
   }
 }
 
-// Reception of the mixed product for many right-hand sides (nrhs >= 32), one leaf b and
-// one group of 64 right-hand sides per block, as a small complex product per leaf:
+// Reception of the mixed product for many right-hand sides (nrhs >= 16), one leaf b and
+// one group of RW right-hand sides per block, as a small complex product per leaf:
 //   R[g][r] = sum_{ch,i} gamma_ch V[g][ch][i] o_b[r][ch][i]       (Eq. 14, U = V^T)
 // for the leaf's V columns g (an RWG function has one column per leaf that holds one of
 // its triangles; k_near_group adds its columns up).  V and o go through shared memory in
 // stages of RC_COLS columns x RC_KC of the 4Q values, copied asynchronously with the next
-// stage in flight while this one is used: V as [column][k] (every lane of a warp reads
-// the same two values with one 16-byte load), o as [k][right-hand side] with rows padded
-// to 64 + 2 values (lane l reads right-hand sides 2l and 2l + 1 with one 16-byte load;
-// gamma is applied to these o values).  Thread (warp w, lane l) owns right-hand sides
-// r0 + 2l, r0 + 2l + 1 and the columns w, w + 8, ... of a block of RC_COLS (only those
-// the leaf has): per pair of k values, two o loads and one V load per column feed 16
-// FMAs per column.  FP32 sums in the order k = 0 .. 4Q-1.
-constexpr int RC_KC = 32, RC_COLS = 64, RC_RHS = 64, RC_OPAD = RC_RHS + 2;
-constexpr int RC_VS = RC_COLS * RC_KC, RC_OS = RC_KC * RC_OPAD;  // complex64 values per stage
-constexpr int RC_SMEM = 2 * (RC_VS + RC_OS) * 8;
+// stage in flight while this one is used: V as [column][k] (16-byte loads of two k
+// values), o as [k][right-hand side] with rows padded by two values (a lane reads its
+// two right-hand sides with one 16-byte load; gamma is applied to these o values).
+// RW = 64 (32 or more right-hand sides): lane l owns right-hand sides 2l, 2l + 1 and
+// warp w the columns w, w + 8, ... (every lane of a warp reads the same V values).
+// RW = 16: lane l owns right-hand sides 2 (l mod 8), + 1 and, with the warp, the columns
+// 4w + l / 8 + 32 j (four columns per warp at a time; V rows padded by two values so
+// that they fall in different banks).  Per pair of k values a lane does 16 FMAs per
+// column (RW = 64) or 8 (RW = 16).  FP32 sums in the order k = 0 .. 4Q-1.
+constexpr int RC_KC = 32, RC_COLS = 64;
+template <int RW>
+struct RcShape {
+  static constexpr int OPAD = RW + 2, VLD = RW == 64 ? RC_KC : RC_KC + 2;  // row strides of o and V
+  static constexpr int VS = RC_COLS * VLD, OS = RC_KC * OPAD;              // complex64 values per stage
+  static constexpr int SMEM = 2 * (VS + OS) * 8;
+  static constexpr int CPW = RW == 64 ? RC_COLS / 8 : RC_COLS / 32;        // columns per lane per block
+};
 __device__ __forceinline__ void rc_cp16(uint32_t dst, const void *src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
 __device__ __forceinline__ void rc_cp8(uint32_t dst, const void *src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
 }
+template <int RW>
 __global__ void __launch_bounds__(256) k_receive_leaf(cplxf *__restrict__ R, const cplxf *__restrict__ V,
                                                       const cplxf *__restrict__ oL, const int32_t *__restrict__ vc_ptr,
                                                       int nrhs, int q, float mk2) {
-  extern __shared__ __align__(16) cplxf rsm[];  // [2][RC_VS + RC_OS]
+  using SH = RcShape<RW>;
+  extern __shared__ __align__(16) cplxf rsm[];  // [2][SH::VS + SH::OS]
   const int64_t b = blockIdx.x;
-  const int r0 = blockIdx.y * RC_RHS;
+  const int r0 = blockIdx.y * RW;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int32_t g0 = vc_ptr[b], ns = vc_ptr[b + 1] - g0;
   const int q4 = 4 * q, q3 = 3 * q;
   const cplxf *ob = oL + b * nrhs * (int64_t)q4;  // o_b[r][ch][i] at ob + r * 4Q + ch * Q + i
-  const int ra = r0 + 2 * lane;                   // this lane's right-hand sides ra, ra + 1
+  const int pl = RW == 64 ? lane : (lane & 7);    // this lane's right-hand-side pair
+  const int ra = r0 + 2 * pl;                     // this lane's right-hand sides ra, ra + 1
+  // this lane's first column in a block and the step between its columns
+  const int cfirst = RW == 64 ? warp : 4 * warp + (lane >> 3), cstep = RW == 64 ? 8 : 32;
   const int nkc = (q4 + RC_KC - 1) / RC_KC, ncb = (ns + RC_COLS - 1) / RC_COLS, nst = ncb * nkc;
   const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(rsm);
   auto stage = [&](int st) {  // stage st (column block st / nkc, k chunk st % nkc) into buffer st & 1
     const int c0 = (st / nkc) * RC_COLS, k0 = (st % nkc) * RC_KC;
     const int nc = min(RC_COLS, ns - c0), kn = min(RC_KC, q4 - k0);  // kn even (q4 and k0 are)
-    cplxf *Vs = rsm + (st & 1) * (RC_VS + RC_OS), *Os = Vs + RC_VS;
+    cplxf *Vs = rsm + (st & 1) * (SH::VS + SH::OS), *Os = Vs + SH::VS;
     for (int t = threadIdx.x; t < RC_COLS * (RC_KC / 2); t += blockDim.x) {
       const int cc = t / (RC_KC / 2), pc = t % (RC_KC / 2);
-      cplxf *dst = Vs + cc * RC_KC + 2 * pc;
+      cplxf *dst = Vs + cc * SH::VLD + 2 * pc;
       if (cc < nc && 2 * pc < kn)
         rc_cp16(sbase + (uint32_t)((dst - rsm) * 8), V + (int64_t)(g0 + c0 + cc) * q4 + k0 + 2 * pc);
       else
         *(float4 *)dst = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
-    for (int t = threadIdx.x; t < RC_RHS * RC_KC; t += blockDim.x) {  // coalesced along k
+    for (int t = threadIdx.x; t < RW * RC_KC; t += blockDim.x) {  // coalesced along k
       const int rr = t / RC_KC, kk = t % RC_KC;
-      cplxf *dst = Os + kk * RC_OPAD + rr;
+      cplxf *dst = Os + kk * SH::OPAD + rr;
       if (r0 + rr < nrhs && kk < kn)
         rc_cp8(sbase + (uint32_t)((dst - rsm) * 8), ob + (int64_t)(r0 + rr) * q4 + k0 + kk);
       else
@@ -771,7 +786,7 @@ __global__ void __launch_bounds__(256) k_receive_leaf(cplxf *__restrict__ R, con
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
-  cplxf acc[RC_COLS / 8][2];
+  cplxf acc[SH::CPW][2];
   if (nst > 0) stage(0);
   for (int st = 0; st < nst; ++st) {
     if (st + 1 < nst) {
@@ -784,22 +799,22 @@ __global__ void __launch_bounds__(256) k_receive_leaf(cplxf *__restrict__ R, con
     const int cb = st / nkc, kc = st % nkc;
     const int c0 = cb * RC_COLS, k0 = kc * RC_KC;
     const int nc = min(RC_COLS, ns - c0);
-    const int jn = nc > warp ? (nc - warp + 7) / 8 : 0;  // this warp's columns in the block
+    const int jn = nc > cfirst ? (nc - cfirst + cstep - 1) / cstep : 0;  // this lane's columns in the block
     if (kc == 0)
 #pragma unroll
-      for (int j = 0; j < RC_COLS / 8; ++j) acc[j][0] = acc[j][1] = make_float2(0.0f, 0.0f);
-    const cplxf *Vs = rsm + (st & 1) * (RC_VS + RC_OS), *Os = Vs + RC_VS;
+      for (int j = 0; j < SH::CPW; ++j) acc[j][0] = acc[j][1] = make_float2(0.0f, 0.0f);
+    const cplxf *Vs = rsm + (st & 1) * (SH::VS + SH::OS), *Os = Vs + SH::VS;
 #pragma unroll 2
     for (int kk = 0; kk < RC_KC; kk += 2) {  // zeros past kn
       const float ga = k0 + kk < q3 ? 1.0f : mk2, gb = k0 + kk + 1 < q3 ? 1.0f : mk2;
-      const float4 oa = *(const float4 *)&Os[kk * RC_OPAD + 2 * lane];
-      const float4 obk = *(const float4 *)&Os[(kk + 1) * RC_OPAD + 2 * lane];
+      const float4 oa = *(const float4 *)&Os[kk * SH::OPAD + 2 * pl];
+      const float4 obk = *(const float4 *)&Os[(kk + 1) * SH::OPAD + 2 * pl];
       const cplxf oa0 = make_float2(ga * oa.x, ga * oa.y), oa1 = make_float2(ga * oa.z, ga * oa.w);
       const cplxf ob0 = make_float2(gb * obk.x, gb * obk.y), ob1 = make_float2(gb * obk.z, gb * obk.w);
 #pragma unroll
-      for (int j = 0; j < RC_COLS / 8; ++j)
+      for (int j = 0; j < SH::CPW; ++j)
         if (j < jn) {
-          const float4 v2 = *(const float4 *)&Vs[(warp + 8 * j) * RC_KC + kk];
+          const float4 v2 = *(const float4 *)&Vs[(cfirst + cstep * j) * SH::VLD + kk];
           const cplxf va = make_float2(v2.x, v2.y), vb = make_float2(v2.z, v2.w);
           cfma(acc[j][0], va, oa0);
           cfma(acc[j][1], va, oa1);
@@ -809,9 +824,9 @@ __global__ void __launch_bounds__(256) k_receive_leaf(cplxf *__restrict__ R, con
     }
     if (kc == nkc - 1)
 #pragma unroll
-      for (int j = 0; j < RC_COLS / 8; ++j)
+      for (int j = 0; j < SH::CPW; ++j)
         if (j < jn) {
-          cplxf *Rg = R + (int64_t)(g0 + c0 + warp + 8 * j) * nrhs;
+          cplxf *Rg = R + (int64_t)(g0 + c0 + cfirst + cstep * j) * nrhs;
           if (ra < nrhs) Rg[ra] = acc[j][0];
           if (ra + 1 < nrhs) Rg[ra + 1] = acc[j][1];
         }
@@ -820,28 +835,36 @@ __global__ void __launch_bounds__(256) k_receive_leaf(cplxf *__restrict__ R, con
 }
 
 // Near field and reception sum of the mixed product for many right-hand sides
-// (nrhs >= 32).  The internal rows come in groups of four whose columns are the union
+// (nrhs >= 16).  The internal rows come in groups of four whose columns are the union
 // of the four rows' columns (a row's value is 0 at a column it lacks), and the groups in
 // blocks of eight (one CTA, one warp per group) whose x columns are the union of the
-// eight groups' columns.  Lane l of a warp owns right-hand sides r0 + 2l and r0 + 2l + 1
-// of the CTA's 64.  The CTA works through its column union NS_CH columns at a time; for
-// each chunk it copies into shared memory, asynchronously and one chunk ahead of use,
-// the x rows of the chunk's columns (512 contiguous bytes per column) and, per warp, the
-// values and the in-chunk positions of its group's slots in the chunk (their ranges per
-// chunk are precomputed).  Every operand of the inner loop then comes from shared
-// memory: per slot a broadcast position, a conflict-free 16-byte x load, two broadcast
-// 16-byte value loads and 32 FP32 FMAs.  FP32 sums in slot order, converted to FP64;
-// the far part adds the reception values R of the row's V columns (k_receive_leaf)
-// times -i eta k.
+// eight groups' columns.  A CTA serves RW right-hand sides: with RW = 64 (32 or more)
+// lane l owns right-hand sides 2l, 2l + 1 and all four rows; with RW = 16 lane l owns
+// row l / 8 and right-hand sides 2 (l mod 8), + 1.  The CTA works through its column
+// union NS_CH columns at a time; for each chunk it copies into shared memory,
+// asynchronously and one chunk ahead of use, the x rows of the chunk's columns (8 RW
+// contiguous bytes per column) and, per warp, the values and the in-chunk positions of
+// its group's slots in the chunk (their ranges per chunk are precomputed).  Every
+// operand of the inner loop then comes from shared memory: per slot a broadcast
+// position, a 16-byte x load, the values (two broadcast 16-byte loads, or one 8-byte
+// load of the lane's row) and 32 (RW = 64) or 8 (RW = 16) FP32 FMAs.  FP32 sums in slot
+// order, converted to FP64; the far part adds the reception values R of the row's V
+// columns (k_receive_leaf) times -i eta k.
 constexpr int NG_ROWS = 4, NS_GROUPS = 8, NS_CH = 32, NS_VS = NS_CH + 2;
-constexpr int NS_XB = NS_CH * 32 * 16, NS_VB = NS_GROUPS * NS_VS * 32, NS_LB = NS_GROUPS * NS_VS * 4;
-constexpr int NS_SMEM = 2 * (NS_XB + NS_VB + NS_LB);  // two stages: x, values, positions
+constexpr int NS_VB = NS_GROUPS * NS_VS * 32, NS_LB = NS_GROUPS * NS_VS * 4;
+template <int RW>
+struct NsShape {
+  static constexpr int XB = NS_CH * (RW / 2) * 16;  // x bytes per stage
+  static constexpr int SMEM = 2 * (XB + NS_VB + NS_LB);
+  static constexpr int RPL = RW == 64 ? NG_ROWS : 1;  // rows per lane
+};
 __device__ __forceinline__ void ns_cp16(uint32_t dst, const void *src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
 __device__ __forceinline__ void ns_cp4(uint32_t dst, const void *src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
 }
+template <int RW>
 __global__ void __launch_bounds__(256) k_near_group(cplx *__restrict__ y, const cplxf *__restrict__ xw, int ldx,
                                                     int64_t n, int nrhs, int64_t n_group,
                                                     const int64_t *__restrict__ g_ptr,
@@ -855,32 +878,36 @@ __global__ void __launch_bounds__(256) k_near_group(cplx *__restrict__ y, const 
                                                     const int32_t *__restrict__ rx_ptr,
                                                     const int32_t *__restrict__ rx_col, const cplxf *__restrict__ R,
                                                     double eta_k, int parts) {
+  using SH = NsShape<RW>;
+  constexpr int PCS = RW / 2;  // 16-byte pieces of x per column
   extern __shared__ __align__(16) unsigned char nsm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t blk = blockIdx.x;
   const int64_t g = blk * NS_GROUPS + warp;
   const bool gon = g < n_group;
-  const int rb = blockIdx.y * 64;
-  const int r0 = rb + 2 * lane;  // this lane's right-hand sides r0, r0 + 1
-  cplxf acc[NG_ROWS][2];
+  const int rb = blockIdx.y * RW;
+  const int pl = RW == 64 ? lane : (lane & 7);  // this lane's right-hand-side pair
+  const int il = RW == 64 ? 0 : (lane >> 3);    // this lane's first row in the group
+  const int r0 = rb + 2 * pl;                   // this lane's right-hand sides r0, r0 + 1
+  cplxf acc[SH::RPL][2];
 #pragma unroll
-  for (int i = 0; i < NG_ROWS; ++i) acc[i][0] = acc[i][1] = make_float2(0.0f, 0.0f);
+  for (int i = 0; i < SH::RPL; ++i) acc[i][0] = acc[i][1] = make_float2(0.0f, 0.0f);
   if (parts & NESA_PART_NEAR) {
     const int64_t c0 = b_ptr[blk], nu = b_ptr[blk + 1] - c0;
     const int nch = (int)((nu + NS_CH - 1) / NS_CH);
     const int64_t e0 = gon ? g_ptr[g] : 0;
     const int32_t *cb = g_cb + (gon ? g_cbp[g] : 0);  // slot offsets of the chunks' starts, nch + 1
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(nsm);
-    // stage k: buffer k & 1 holds x at [buf * NS_XB], values at 2 NS_XB + buf * NS_VB,
-    // positions at 2 (NS_XB + NS_VB) + buf * NS_LB
+    // stage k: buffer k & 1 holds x at [buf * XB], values at 2 XB + buf * NS_VB,
+    // positions at 2 (XB + NS_VB) + buf * NS_LB
     int cnt0 = 0, cnt1 = 0;                          // slots of this warp's group in buffers 0 and 1
     int32_t nb_c = gon ? cb[0] : 0, nb_n = (gon && nch >= 1) ? cb[1] : 0;  // next chunk to stage
     auto stage = [&](int c) {
       const int buf = c & 1;
-      for (int t = threadIdx.x; t < NS_CH * 32; t += blockDim.x) {
-        const int j = t >> 5, pc = t & 31;  // column j of the chunk, right-hand sides rb + 2 pc, + 1
+      for (int t = threadIdx.x; t < NS_CH * PCS; t += blockDim.x) {
+        const int j = t / PCS, pc = t % PCS;  // column j of the chunk, right-hand sides rb + 2 pc, + 1
         const int64_t jj = (int64_t)c * NS_CH + j;
-        const uint32_t off = (uint32_t)(buf * NS_XB + (j * 32 + pc) * 16);
+        const uint32_t off = (uint32_t)(buf * SH::XB + (j * PCS + pc) * 16);
         if (jj < nu && rb + 2 * pc < ldx)
           ns_cp16(sbase + off, xw + (int64_t)b_col[c0 + jj] * ldx + rb + 2 * pc);
         else
@@ -889,8 +916,8 @@ __global__ void __launch_bounds__(256) k_near_group(cplx *__restrict__ y, const 
       if (gon) {
         const int cnt = nb_n - nb_c;  // at most NS_CH + 1
         const int64_t sl = e0 + nb_c;
-        const uint32_t voff = (uint32_t)(2 * NS_XB + buf * NS_VB + warp * NS_VS * 32);
-        const uint32_t loff = (uint32_t)(2 * (NS_XB + NS_VB) + buf * NS_LB + warp * NS_VS * 4);
+        const uint32_t voff = (uint32_t)(2 * SH::XB + buf * NS_VB + warp * NS_VS * 32);
+        const uint32_t loff = (uint32_t)(2 * (SH::XB + NS_VB) + buf * NS_LB + warp * NS_VS * 4);
         for (int t = lane; t < 2 * cnt; t += 32) ns_cp16(sbase + voff + t * 16, g_val + 2 * sl + t);
         for (int t = lane; t < cnt; t += 32) ns_cp4(sbase + loff + t * 4, g_loc + sl + t);
         if (buf)
@@ -913,21 +940,27 @@ __global__ void __launch_bounds__(256) k_near_group(cplx *__restrict__ y, const 
       __syncthreads();
       const int buf = c & 1;
       const int cnt = buf ? cnt1 : cnt0;
-      const float4 *xb = (const float4 *)(nsm + buf * NS_XB) + lane;
-      const float4 *vb = (const float4 *)(nsm + 2 * NS_XB + buf * NS_VB + warp * NS_VS * 32);
-      const int32_t *lb = (const int32_t *)(nsm + 2 * (NS_XB + NS_VB) + buf * NS_LB + warp * NS_VS * 4);
+      const float4 *xb = (const float4 *)(nsm + buf * SH::XB) + pl;
+      const float4 *vb = (const float4 *)(nsm + 2 * SH::XB + buf * NS_VB + warp * NS_VS * 32);
+      const int32_t *lb = (const int32_t *)(nsm + 2 * (SH::XB + NS_VB) + buf * NS_LB + warp * NS_VS * 4);
       const int cbase = c * NS_CH;
 #pragma unroll 2
       for (int u = 0; u < cnt; ++u) {
-        const float4 x2 = xb[(lb[u] - cbase) * 32];
-        const float4 v0 = vb[2 * u], v1 = vb[2 * u + 1];
+        const float4 x2 = xb[(lb[u] - cbase) * PCS];
         const cplxf xa = make_float2(x2.x, x2.y), xb2 = make_float2(x2.z, x2.w);
-        const cplxf va[NG_ROWS] = {make_float2(v0.x, v0.y), make_float2(v0.z, v0.w), make_float2(v1.x, v1.y),
-                                   make_float2(v1.z, v1.w)};
+        if constexpr (RW == 64) {
+          const float4 v0 = vb[2 * u], v1 = vb[2 * u + 1];
+          const cplxf va[NG_ROWS] = {make_float2(v0.x, v0.y), make_float2(v0.z, v0.w), make_float2(v1.x, v1.y),
+                                     make_float2(v1.z, v1.w)};
 #pragma unroll
-        for (int i = 0; i < NG_ROWS; ++i) {
-          cfma(acc[i][0], va[i], xa);
-          cfma(acc[i][1], va[i], xb2);
+          for (int i = 0; i < NG_ROWS; ++i) {
+            cfma(acc[i][0], va[i], xa);
+            cfma(acc[i][1], va[i], xb2);
+          }
+        } else {
+          const cplxf v = ((const cplxf *)vb)[NG_ROWS * u + il];
+          cfma(acc[0][0], v, xa);
+          cfma(acc[0][1], v, xb2);
         }
       }
       __syncthreads();  // every warp is done with this buffer before it is refilled
@@ -936,8 +969,8 @@ __global__ void __launch_bounds__(256) k_near_group(cplx *__restrict__ y, const 
   if (!gon) return;
   const bool on0 = r0 < nrhs, on1 = r0 + 1 < nrhs;
 #pragma unroll
-  for (int i = 0; i < NG_ROWS; ++i) {
-    const int32_t m = g_row[NG_ROWS * g + i];
+  for (int i = 0; i < SH::RPL; ++i) {
+    const int32_t m = g_row[NG_ROWS * g + il + i];
     if (m < 0) continue;
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
@@ -1075,7 +1108,7 @@ static void run_product(nesa_ctx *c, const OpView<CT> &op, const cplx *x, cplx *
   const double B = sizeof(CT);
   const double ncol = (double)c->info.v_columns;
   if constexpr (std::is_same<CT, cplxf>::value) {
-    if (nrhs >= 32) {  // x permuted to complex64 [n][ldx] for the radiation and the near field
+    if (nrhs >= WIDE_MIN_RHS) {  // x permuted to complex64 [n][ldx] for the near field (and radiation)
       const int ldx = (nrhs + 1) & ~1;
       k_perm_x_wide<<<(unsigned)std::min<int64_t>((c->n * ldx + 255) / 256, 1 << 16), 256, 0, st>>>(
           c->d_xp, x, c->d_perm, c->n, nrhs, ldx);
@@ -1197,17 +1230,26 @@ static void run_product(nesa_ctx *c, const OpView<CT> &op, const cplx *x, cplx *
   StageScope sc(c, 3, fl, by);
   if constexpr (std::is_same<CT, cplxf>::value) {
     const unsigned pgrid = (unsigned)std::min<int64_t>((c->n * nrhs + 255) / 256, 1 << 16);
-    if (nrhs >= 32) {  // many right-hand sides: groups of four rows, two right-hand sides per lane
+    if (nrhs >= WIDE_MIN_RHS) {  // many right-hand sides: groups of four rows, two right-hand sides per lane
       const int ldx = (nrhs + 1) & ~1;  // xw was made before the far part
-      if (parts & NESA_PART_FAR)
-        k_receive_leaf<<<dim3((unsigned)c->nleaf, (unsigned)((nrhs + RC_RHS - 1) / RC_RHS)), 256, RC_SMEM, st>>>(
-            c->d_rcv, op.V, op.o[L], c->d_vc_ptr, nrhs, dL.q, (float)(-1.0 / (c->k * c->k)));
-      if (c->n_group > 0)
-        k_near_group<<<dim3((unsigned)((c->n_group + NS_GROUPS - 1) / NS_GROUPS), (unsigned)((nrhs + 63) / 64)),
-                       32 * NS_GROUPS, NS_SMEM, st>>>(y, c->d_xp, ldx, c->n, nrhs, c->n_group, c->d_ng_ptr,
-                                                      c->d_ng_loc, (const float4 *)c->d_ng_val, c->d_ng_row,
-                                                      c->d_ng_cbp, c->d_ng_cb, c->d_nb_ptr, c->d_nb_col,
-                                                      c->d_rx_ptr, c->d_rx_col, c->d_rcv, c->eta * c->k, parts);
+      const float mk2 = (float)(-1.0 / (c->k * c->k));
+      if (parts & NESA_PART_FAR) {
+        if (nrhs >= 32)
+          k_receive_leaf<64><<<dim3((unsigned)c->nleaf, (unsigned)((nrhs + 63) / 64)), 256, RcShape<64>::SMEM, st>>>(
+              c->d_rcv, op.V, op.o[L], c->d_vc_ptr, nrhs, dL.q, mk2);
+        else
+          k_receive_leaf<16><<<dim3((unsigned)c->nleaf, (unsigned)((nrhs + 15) / 16)), 256, RcShape<16>::SMEM, st>>>(
+              c->d_rcv, op.V, op.o[L], c->d_vc_ptr, nrhs, dL.q, mk2);
+      }
+      if (c->n_group > 0) {
+        const int rw = nrhs >= 32 ? 64 : 16;
+        const dim3 grid((unsigned)((c->n_group + NS_GROUPS - 1) / NS_GROUPS), (unsigned)((nrhs + rw - 1) / rw));
+        auto kern = nrhs >= 32 ? k_near_group<64> : k_near_group<16>;
+        kern<<<grid, 32 * NS_GROUPS, nrhs >= 32 ? NsShape<64>::SMEM : NsShape<16>::SMEM, st>>>(
+            y, c->d_xp, ldx, c->n, nrhs, c->n_group, c->d_ng_ptr, c->d_ng_loc, (const float4 *)c->d_ng_val,
+            c->d_ng_row, c->d_ng_cbp, c->d_ng_cb, c->d_nb_ptr, c->d_nb_col, c->d_rx_ptr, c->d_rx_col, c->d_rcv,
+            c->eta * c->k, parts);
+      }
     } else {
       if (parts & NESA_PART_NEAR) k_perm_x<<<pgrid, 256, 0, st>>>(c->d_xp, x, c->d_perm, c->n, nrhs);
       auto near = nrhs == 1 ? k_near_receive_v<1> : k_near_receive_v<4>;
@@ -1472,8 +1514,13 @@ static void build_near_groups(nesa_ctx *c) {
   check_cuda(cudaMemcpy(c->d_nb_ptr, bptr.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice), "near groups");
   check_cuda(cudaMemcpy(c->d_nb_col, bflat.data(), sizeof(int32_t) * bflat.size(), cudaMemcpyHostToDevice),
              "near groups");
-  check_cuda(cudaFuncSetAttribute(k_near_group, cudaFuncAttributeMaxDynamicSharedMemorySize, NS_SMEM), "near groups");
-  check_cuda(cudaFuncSetAttribute(k_receive_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize, RC_SMEM),
+  check_cuda(cudaFuncSetAttribute(k_near_group<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, NsShape<64>::SMEM),
+             "near groups");
+  check_cuda(cudaFuncSetAttribute(k_near_group<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, NsShape<16>::SMEM),
+             "near groups");
+  check_cuda(cudaFuncSetAttribute(k_receive_leaf<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, RcShape<64>::SMEM),
+             "near groups");
+  check_cuda(cudaFuncSetAttribute(k_receive_leaf<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, RcShape<16>::SMEM),
              "near groups");
   c->d_ng_ptr = (int64_t *)dalloc(c, sizeof(int64_t) * (ng + 1));
   c->d_ng_loc = (int32_t *)dalloc(c, sizeof(int32_t) * std::max<int64_t>(nslot, 1));

@@ -124,11 +124,13 @@ def test_many_rhs_reception_large_leaves():
     assert e < TOL_TC
 
 
-@pytest.mark.parametrize("nrhs", [33, 64])
+@pytest.mark.parametrize("nrhs", [16, 21, 33, 64])
 def test_many_rhs_grouped_near_field(nrhs):
-    # 32 or more right-hand sides: the near field runs four rows at a time over the union
+    # 16 or more right-hand sides: the near field runs four rows at a time over the union
     # of their columns (a row's value 0 where it lacks a column), two right-hand sides
-    # per lane; an odd count pads the x rows to an even stride with zeros.  Every column
+    # per lane (all four rows per lane from 32 right-hand sides, one row per lane below,
+    # where a CTA serves 16 and 21 needs a second, partly filled one); an odd count pads
+    # the x rows to an even stride with zeros.  Every column
     # of the near part against the FP64 near part (complex64 values and x, FP32 sums:
     # 1e-5 as for one right-hand side), every column of the whole product against the
     # FP64 product (the mixed tolerance), and sampled rows of the last column against the
