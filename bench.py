@@ -747,16 +747,16 @@ def run_ours(args, world, rank, local):
 
     # roofline of the headline (FP64) product: its dominant kernel is the translation
     # (k_translate64, Eqs. 12-13), bound by the FP64 pipe.  Achieved counts the
-    # algorithmic 8 flops per complex multiply-add; the kernel's 3M form issues 13 FP64
-    # operations per matrix entry and right-hand side where that count has 16 (4 complex
-    # multiply-adds), so "issued_frac" is frac x 13/16
+    # algorithmic 8 flops per complex multiply-add; the kernel's 3M form issues 12 FP64
+    # FMAs per matrix entry and right-hand side (3 per channel, with the sums Re + Im of
+    # the matrix stored) where that count has 16, so "issued_frac" is frac x 12/16
     tr64 = prof64["translation"]
     ach64 = tr64["flops"] / (tr64["ms"] * 1e-3) / 1e12
     roof = {"kernel": "k_translate64", "bound": "alu", "achieved": ach64, "peak": FP64_PEAK_TFLOPS,
-            "unit": "TFLOP/s", "frac": ach64 / FP64_PEAK_TFLOPS, "issued_frac": ach64 / FP64_PEAK_TFLOPS * 13 / 16,
+            "unit": "TFLOP/s", "frac": ach64 / FP64_PEAK_TFLOPS, "issued_frac": ach64 / FP64_PEAK_TFLOPS * 12 / 16,
             "peak_note": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (derived from unit counts and the "
                          "maximum clock); achieved counts 8 flops per complex multiply-add, the 3M form issues "
-                         "13/16 of them",
+                         "12/16 of them",
             "traffic": (K_TRANSLATE64_DRAM_BYTES_C2 if (args.workload == CONFIG and nrhs == 1) else None),
             "traffic_unit": "bytes per product (all launches of the kernel in one product)",
             "share_of_product": tr64["ms"] / sum(v["ms"] for k, v in prof64.items() if k != "translation_tensor_gemm"),
